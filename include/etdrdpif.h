@@ -1,0 +1,182 @@
+/*
+ * etdrdpif.h -- C ABI of libetdrdpif, a GB300 (sm_103a) implementation of the
+ * second-order L-stable ETD-RDP-IF scheme of Asante-Asamani, Kleefeld and
+ * Wade, "A second-order exponential time differencing scheme for non-linear
+ * reaction-diffusion systems with dimensional splitting" (arXiv 2001.11220).
+ *
+ * Problem (Section 2, Eq. model): u_t = D Lap u + F(u) for s species on a
+ * d-dimensional box (d = 2, 3), diagonal D, homogeneous Dirichlet, Neumann or
+ * periodic boundaries, second-order central differences (Section 3, Example 1
+ * and Eq. Ai).  One time step is the framed ETD-RDP-IF scheme of Section 6
+ * (Eq. donedone and its d-dimensional frame):
+ *     U*      = P_d ... P_1 (U_n + k F(U_n, t_n))
+ *     U_{n+1} = T_d [R_{d-1}..R_1 (9 U_n + 2k F(U_n)) + k F(U*, t_{n+1})]
+ *             - S_d [R_{d-1}..R_1 (8 U_n + 3k/2 F(U_n)) + k/2 F(U*, t_{n+1})]
+ * with P_a = (I + k A_a)^{-1}, T_a = (I + k/3 A_a)^{-1}, S_a = (I + k/4 A_a)^{-1},
+ * R_a = 9 T_a - 8 S_a.  Every inverse is a set of independent line solves
+ * along one axis (Section 7); periodic lines are cyclic and are solved with a
+ * per-line Sherman-Morrison correction whose scalar is formed in FP64.
+ *
+ * Conventions shared by every entry point
+ *   - State layout: species-major, x fastest: U[s][z][y][x] (2D: U[s][y][x]),
+ *     contiguous, element type double (ETD_FP64) or float (ETD_FP32).
+ *     Axis 0 = x is the B_p factor at the last spatial Kronecker slot of
+ *     Eq. (Ai); the last axis carries T_d / S_d and F(U*).
+ *   - Grid nodes per axis follow Section 3, Example 1: Dirichlet n interior
+ *     nodes, h = L/(n+1); Neumann n nodes including both ends, h = L/(n-1);
+ *     periodic n nodes, h = L/n.  n >= 3 on every axis.
+ *   - Device pointers are CUDA device (or managed) memory owned by the
+ *     caller; the library never frees them.  Host pointers are plain host
+ *     memory.  The context owns its coefficient tables and scratch.
+ *   - All device work is ordered on the context's stream; entry points
+ *     return without synchronising unless stated otherwise.
+ *   - Every entry point returns an etd_status and never aborts the process;
+ *     on failure etd_last_error(ctx) describes the cause.
+ */
+#ifndef ETDRDPIF_H
+#define ETDRDPIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ETD_OK = 0,
+  ETD_ERR_INVALID_ARG = 1, /* bad pointer, size, boundary, coefficient, step or reaction */
+  ETD_ERR_UNSUPPORTED = 2, /* valid problem outside what the kernels implement */
+  ETD_ERR_OOM = 3,         /* device or host allocation failed */
+  ETD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  ETD_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  ETD_ERR_NONFINITE = 6    /* a non-finite value was detected where checked */
+} etd_status;
+
+typedef enum { ETD_BC_DIRICHLET = 0, ETD_BC_NEUMANN = 1, ETD_BC_PERIODIC = 2 } etd_bc;
+typedef enum { ETD_FP64 = 0, ETD_FP32 = 1 } etd_precision;
+
+/* Reactions F(u) evaluated pointwise (Section 2; systems of Section 8 and the
+ * benchmark problems).  params[] per kind:
+ *   ZERO          F = 0
+ *   LINEAR        F_i = p0 u_i + p1                                 (any s)
+ *   BRUSSELATOR   F_u = p0 + u^2 v - (p1+1) u, F_v = p1 u - u^2 v    (s = 2;
+ *                 Section 8.2 with B = p0, A = p1)
+ *   SCHNAKENBERG  F_u = p2 (p0 - u + u^2 v), F_v = p2 (p1 - u^2 v)  (s = 2)
+ *   GRAY_SCOTT    F_u = -u v^2 + p0 (1-u), F_v = u v^2 - (p0+p1) v   (s = 2)
+ *   ENZYME        F = -u/(1+u) + p0 src(x,t), src the manufactured source
+ *                 (p1 Sum_a (pi/L_a)^2 - 1) q + q/(1+q),
+ *                 q = e^{-t} Prod_a sin(pi x_a/L_a)                 (s = 1;
+ *                 Section 8.1; p0 = 0 gives the paper's enzyme model) */
+typedef enum {
+  ETD_REACTION_ZERO = 0,
+  ETD_REACTION_LINEAR = 1,
+  ETD_REACTION_BRUSSELATOR = 2,
+  ETD_REACTION_SCHNAKENBERG = 3,
+  ETD_REACTION_GRAY_SCOTT = 4,
+  ETD_REACTION_ENZYME = 5
+} etd_reaction_kind;
+
+typedef struct {
+  int32_t dim;       /* 2 or 3 */
+  int32_t bc[3];     /* etd_bc per axis (axis 0 = x) */
+  int64_t n[3];      /* nodes per axis, 3 <= n <= 16384 */
+  double length[3];  /* domain length per axis, > 0 */
+} etd_grid;
+
+typedef struct {
+  int32_t kind;      /* etd_reaction_kind */
+  int32_t nspecies;  /* s: 1 or 2 */
+  double params[8];  /* see etd_reaction_kind */
+} etd_reaction;
+
+typedef struct etd_ctx etd_ctx;
+
+/* Static facts about a context (for measurement and tuning). */
+typedef struct {
+  int32_t dim, nspecies, precision;
+  int64_t npoints;               /* points per species */
+  int64_t state_bytes;           /* bytes of one state U */
+  int64_t scratch_bytes;         /* device scratch the context owns */
+  int64_t algorithmic_bytes;     /* HBM bytes one step must move (sweep floor: (4d-2) fields
+                                    read or written per species per point) */
+  int32_t launches_per_step;     /* kernels one etd_step enqueues */
+  int32_t chunk[3];              /* chunk length per axis (elements per thread) */
+  int32_t lines_per_block[3];
+} etd_info;
+
+/* Create a context for one problem.  Validates every argument
+ * (ETD_ERR_INVALID_ARG on dim not 2/3, n < 3, bad bc, length <= 0, D < 0 or
+ * non-finite, k <= 0 or non-finite, reaction kind / species mismatch),
+ * factorises the line matrices I + (k/gamma) D_s B_p for gamma in {1,3,4} in
+ * FP64 on the host (LU without pivoting, Section 7; the matrices are
+ * diagonally dominant for every k > 0, D >= 0), uploads the tables in the
+ * context's precision and allocates 3 s N elements of device scratch.
+ * D points to nspecies host doubles.  stream is a cudaStream_t (NULL = legacy
+ * default stream).  On success *out owns everything; free with etd_destroy. */
+etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction *reaction,
+                      double k, int32_t precision, void *stream, etd_ctx **out);
+
+/* One ETD-RDP-IF step in place: U (device, layout above) holds U_n at time
+ * t_n on entry and U_{n+1} on return (stream-ordered). */
+etd_status etd_step(etd_ctx *ctx, void *U, double t_n);
+
+/* nsteps steps from time t0, in place on device U. */
+etd_status etd_run(etd_ctx *ctx, void *U, double t0, int64_t nsteps);
+
+/* Same as etd_run for a HOST buffer U_host: copies it to a device state the
+ * context owns, runs, copies back and synchronises the stream before
+ * returning.  Pinned host memory gives the fastest copies. */
+etd_status etd_run_host(etd_ctx *ctx, void *U_host, double t0, int64_t nsteps);
+
+/* Reverse mode of one step (the discrete adjoint of the frame above): given
+ * U_n (device) at t_n and Ubar_next = dL/dU_{n+1} (device), writes
+ * Ubar_n = dL/dU_n (device, may alias Ubar_next) and ADDS dL/dD_s into dD[s]
+ * and dL/dparams_j into dparams[j] (host arrays of nspecies and 8 doubles;
+ * either may be NULL).  Synchronises the stream. */
+etd_status etd_step_adjoint(etd_ctx *ctx, const void *Un, double t_n, const void *Ubar_next,
+                            void *Ubar_n, double *dD, double *dparams);
+
+/* Loss L = 1/2 sum (U_N - target)^2 after nsteps from U0 (device) at t0 and
+ * its gradients: dU0 (device), dD[nspecies], dparams[8] (host), with the
+ * forward states checkpointed every ckpt_every steps and recomputed segment
+ * by segment in the reverse sweep.  loss is a host double.  Synchronises. */
+etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target, int64_t nsteps,
+                    int64_t ckpt_every, double *loss, void *dU0, double *dD, double *dparams);
+
+/* Batched ensemble: ninst independent problems (grids[i], D[i*nspecies ..],
+ * reactions[i]; all instances share nspecies, dim and precision; k is
+ * common) advanced together, one launch per sweep kind covering every
+ * instance.  etd_batch_run takes an array of ninst device state pointers
+ * (host array).  Other entry points reject batched contexts. */
+etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *D,
+                            const etd_reaction *reactions, double k, int32_t precision,
+                            void *stream, etd_ctx **out);
+etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps);
+
+/* Re-tune the per-axis chunk lengths by timing every candidate on the
+ * context's stream with CUDA events (work buffer: a device state of the
+ * context's shape, overwritten).  Synchronises. */
+etd_status etd_autotune(etd_ctx *ctx, void *U_work);
+
+etd_status etd_set_stream(etd_ctx *ctx, void *stream);
+
+/* Per-sweep timing for measurement.  While enabled, runs launch kernels
+ * directly (no graph) and bracket every sweep launch with CUDA events on the
+ * context's stream; etd_profile_read synchronises, adds the elapsed device
+ * time of each sweep kind (0 = first axis, 1 = middle axis, 2 = last axis)
+ * to ms[3] and the launch counts to launches[3], and clears the record. */
+etd_status etd_profile(etd_ctx *ctx, int32_t enable);
+etd_status etd_profile_read(etd_ctx *ctx, double *ms, int64_t *launches);
+etd_status etd_get_info(const etd_ctx *ctx, etd_info *info);
+
+/* Description of the last failure on ctx (or of the last failed etd_create /
+ * etd_batch_create when ctx is NULL).  Never NULL. */
+const char *etd_last_error(const etd_ctx *ctx);
+
+/* Frees everything the context owns; NULL is accepted. */
+void etd_destroy(etd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,146 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from
+PyTorch, every step of the scheme runs in libetdrdpif's kernels.
+
+    ctx = EtdRdpIf.from_workload(workload, precision="fp32")
+    U = torch.tensor(initial_state, device="cuda", dtype=ctx.dtype)
+    ctx.run(U, t0=0.0, nsteps=100)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _binding as B
+from .workloads import REACTIONS, Workload
+
+
+def _stream_handle(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_grid(n, bc, length=None) -> B.etd_grid:
+    g = B.etd_grid()
+    g.dim = len(n)
+    bc = (bc,) * len(n) if isinstance(bc, int) else tuple(bc)
+    length = length or (1.0,) * len(n)
+    for a in range(3):
+        g.n[a] = int(n[a]) if a < len(n) else 1
+        g.bc[a] = int(bc[a]) if a < len(n) else 0
+        g.length[a] = float(length[a]) if a < len(n) else 1.0
+    return g
+
+
+def make_reaction(kind, nspecies, params=()) -> B.etd_reaction:
+    r = B.etd_reaction()
+    r.kind = REACTIONS[kind] if isinstance(kind, str) else int(kind)
+    r.nspecies = int(nspecies)
+    for j in range(8):
+        r.params[j] = float(params[j]) if j < len(params) else 0.0
+    return r
+
+
+class EtdRdpIf:
+    """One ETD-RDP-IF problem on the current CUDA device."""
+
+    def __init__(self, n, bc, D, reaction="zero", params=(), k=0.01, precision="fp64", length=None, stream=None):
+        self.lib = B.load()
+        self.n = tuple(int(v) for v in n)
+        self.D = tuple(float(d) for d in D)
+        self.k = float(k)
+        self.precision = B.ETD_FP64 if precision in ("fp64", B.ETD_FP64) else B.ETD_FP32
+        self.dtype = torch.float64 if self.precision == B.ETD_FP64 else torch.float32
+        self.shape = (len(self.D),) + tuple(reversed(self.n))
+        grid = make_grid(self.n, bc, length)
+        rx = make_reaction(reaction, len(self.D), params)
+        Darr = (ctypes.c_double * len(self.D))(*self.D)
+        ctx = ctypes.c_void_p()
+        st = self.lib.etd_create(ctypes.byref(grid), Darr, ctypes.byref(rx), self.k, self.precision,
+                                 _stream_handle(stream), ctypes.byref(ctx))
+        B.check(st, None)
+        self.ctx = ctx
+
+    @classmethod
+    def from_workload(cls, w: Workload, precision="fp64", stream=None) -> "EtdRdpIf":
+        return cls(w.n, w.bc, w.D, w.reaction, w.params, w.k, precision, w.length, stream)
+
+    def _check_state(self, U: torch.Tensor):
+        if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous() and tuple(U.shape) == self.shape):
+            raise ValueError(f"state must be a contiguous CUDA {self.dtype} tensor of shape {self.shape}")
+
+    def set_stream(self, stream=None):
+        B.check(self.lib.etd_set_stream(self.ctx, _stream_handle(stream)), self.ctx)
+
+    def step(self, U: torch.Tensor, t: float):
+        self._check_state(U)
+        B.check(self.lib.etd_step(self.ctx, ctypes.c_void_p(U.data_ptr()), float(t)), self.ctx)
+        return U
+
+    def run(self, U: torch.Tensor, t0: float, nsteps: int):
+        self._check_state(U)
+        B.check(self.lib.etd_run(self.ctx, ctypes.c_void_p(U.data_ptr()), float(t0), int(nsteps)), self.ctx)
+        return U
+
+    def run_host(self, U: torch.Tensor, t0: float, nsteps: int):
+        """U: contiguous CPU tensor (pinned for speed); copies in/out inside the call."""
+        if U.is_cuda or U.dtype != self.dtype or not U.is_contiguous() or tuple(U.shape) != self.shape:
+            raise ValueError("run_host needs a contiguous CPU tensor of the state's dtype and shape")
+        B.check(self.lib.etd_run_host(self.ctx, ctypes.c_void_p(U.data_ptr()), float(t0), int(nsteps)), self.ctx)
+        return U
+
+    def step_adjoint(self, Un: torch.Tensor, t: float, Ubar_next: torch.Tensor, Ubar_n: torch.Tensor = None):
+        self._check_state(Un)
+        self._check_state(Ubar_next)
+        if Ubar_n is None:
+            Ubar_n = torch.empty_like(Un)
+        dD = (ctypes.c_double * len(self.D))()
+        dp = (ctypes.c_double * 8)()
+        B.check(self.lib.etd_step_adjoint(self.ctx, ctypes.c_void_p(Un.data_ptr()), float(t),
+                                          ctypes.c_void_p(Ubar_next.data_ptr()), ctypes.c_void_p(Ubar_n.data_ptr()),
+                                          dD, dp), self.ctx)
+        return Ubar_n, np.array(dD[:]), np.array(dp[:])
+
+    def grad(self, U0: torch.Tensor, t0: float, target: torch.Tensor, nsteps: int, ckpt_every: int = 20):
+        self._check_state(U0)
+        self._check_state(target)
+        dU0 = torch.empty_like(U0)
+        loss = ctypes.c_double()
+        dD = (ctypes.c_double * len(self.D))()
+        dp = (ctypes.c_double * 8)()
+        B.check(self.lib.etd_grad(self.ctx, ctypes.c_void_p(U0.data_ptr()), float(t0),
+                                  ctypes.c_void_p(target.data_ptr()), int(nsteps), int(ckpt_every),
+                                  ctypes.byref(loss), ctypes.c_void_p(dU0.data_ptr()), dD, dp), self.ctx)
+        return loss.value, dU0, np.array(dD[:]), np.array(dp[:])
+
+    def autotune(self, U_work: torch.Tensor):
+        self._check_state(U_work)
+        B.check(self.lib.etd_autotune(self.ctx, ctypes.c_void_p(U_work.data_ptr())), self.ctx)
+
+    def profile(self, enable: bool):
+        B.check(self.lib.etd_profile(self.ctx, int(bool(enable))), self.ctx)
+
+    def profile_read(self):
+        """(ms[3], launches[3]) per sweep kind since the last read (synchronises)."""
+        ms = (ctypes.c_double * 3)()
+        ln = (ctypes.c_int64 * 3)()
+        B.check(self.lib.etd_profile_read(self.ctx, ms, ln), self.ctx)
+        return list(ms), list(ln)
+
+    def info(self) -> dict:
+        inf = B.etd_info()
+        B.check(self.lib.etd_get_info(self.ctx, ctypes.byref(inf)), self.ctx)
+        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block") else getattr(inf, f))
+                for f, _ in inf._fields_}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.etd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

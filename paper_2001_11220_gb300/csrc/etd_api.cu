@@ -1,0 +1,462 @@
+// etd_api.cu -- C ABI of libetdrdpif: contexts, FP64 pre-factorisation,
+// launch planning and the forward step.  See include/etdrdpif.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/etdrdpif.h"
+#include "etd_context.h"
+#include "etd_internal.h"
+#include "etd_tables.h"
+
+using namespace etd;
+
+static thread_local std::string g_create_error = "no error";
+
+const char *etd_last_error(const etd_ctx *ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+namespace etd {
+
+etd_status fail(etd_ctx *ctx, etd_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf; else g_create_error = buf;
+  return st;
+}
+
+etd_status cuda_fail(etd_ctx *ctx, cudaError_t e, const char *what) {
+  return fail(ctx, ETD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ validation
+
+etd_status validate_problem(const etd_grid *grid, const double *D, const etd_reaction *rx, double k,
+                            int32_t precision) {
+  if (!grid || !D || !rx) return fail(nullptr, ETD_ERR_INVALID_ARG, "null grid, D or reaction");
+  if (grid->dim != 2 && grid->dim != 3) return fail(nullptr, ETD_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", grid->dim);
+  for (int a = 0; a < grid->dim; ++a) {
+    if (grid->n[a] < 3 || grid->n[a] > 16384)
+      return fail(nullptr, ETD_ERR_INVALID_ARG, "n[%d] = %lld outside [3, 16384]", a, (long long)grid->n[a]);
+    if (grid->bc[a] < 0 || grid->bc[a] > 2) return fail(nullptr, ETD_ERR_INVALID_ARG, "bc[%d] = %d invalid", a, grid->bc[a]);
+    if (!(grid->length[a] > 0) || !std::isfinite(grid->length[a]))
+      return fail(nullptr, ETD_ERR_INVALID_ARG, "length[%d] must be finite and > 0", a);
+  }
+  if (!(k > 0) || !std::isfinite(k)) return fail(nullptr, ETD_ERR_INVALID_ARG, "k must be finite and > 0");
+  if (precision != ETD_FP64 && precision != ETD_FP32) return fail(nullptr, ETD_ERR_INVALID_ARG, "precision %d invalid", precision);
+  const int S = rx->nspecies;
+  if (S < 1) return fail(nullptr, ETD_ERR_INVALID_ARG, "nspecies must be >= 1");
+  if (S > MAX_SPECIES) return fail(nullptr, ETD_ERR_UNSUPPORTED, "nspecies %d > %d", S, MAX_SPECIES);
+  for (int s = 0; s < S; ++s)
+    if (!(D[s] >= 0) || !std::isfinite(D[s])) return fail(nullptr, ETD_ERR_INVALID_ARG, "D[%d] must be finite and >= 0", s);
+  switch (rx->kind) {
+    case ETD_REACTION_ZERO:
+    case ETD_REACTION_LINEAR: break;
+    case ETD_REACTION_BRUSSELATOR:
+    case ETD_REACTION_SCHNAKENBERG:
+    case ETD_REACTION_GRAY_SCOTT:
+      if (S != 2) return fail(nullptr, ETD_ERR_INVALID_ARG, "reaction %d needs 2 species", rx->kind);
+      break;
+    case ETD_REACTION_ENZYME:
+      if (S != 1) return fail(nullptr, ETD_ERR_INVALID_ARG, "enzyme reaction needs 1 species");
+      break;
+    default: return fail(nullptr, ETD_ERR_INVALID_ARG, "unknown reaction kind %d", rx->kind);
+  }
+  for (int j = 0; j < 8; ++j)
+    if (!std::isfinite(rx->params[j])) return fail(nullptr, ETD_ERR_INVALID_ARG, "params[%d] not finite", j);
+  return ETD_OK;
+}
+
+// ------------------------------------------------------------ planning
+
+static int pick_pitch(int m) { return (m % 2 == 0) ? m + 1 : m; }
+
+// lines-per-block and chunk count for one axis and chunk length L
+bool plan_axis(Instance &I, int a, int L, int max_threads) {
+  AxisPlan &P = I.plan[a];
+  const long long n = I.n[a];
+  P.L = L;
+  P.m = (int)((n + L - 1) / L);
+  if (P.m > max_threads) return false;
+  P.kind = (a == 0) ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  P.st = st;
+  P.nlines = I.N / n;
+  if (a == 0) {
+    int nlb = std::max(1, 256 / P.m);
+    nlb = (int)std::min<long long>(nlb, P.nlines);
+    P.nlb = nlb;
+    P.nlo_blocks = 1;
+    P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
+  } else {
+    int nlb = std::max(1, max_threads / P.m);
+    if (nlb >= 32) nlb = (nlb / 32) * 32;
+    nlb = (int)std::min<long long>(nlb, ((st + 31) / 32) * 32);
+    nlb = std::max(1, nlb);
+    P.nlb = nlb;
+    P.nlo_blocks = (int)((st + nlb - 1) / nlb);
+    const long long nhi = I.N / (st * n);
+    P.nblocks = (int)(P.nlo_blocks * nhi);
+  }
+  P.pitch = pick_pitch(P.m);
+  P.nthreads = P.nlb * P.m;
+  P.smem = sweep_smem_bytes(P.kind, I.S, P.nlb, P.pitch, I.real_bytes);
+  return P.smem <= 200 * 1024;
+}
+
+int default_chunk(const Instance &I, int a) {
+  // contiguous axis: short chunks (lanes walk the line); strided axes: longer
+  // chunks so a block covers 32 neighbouring lines
+  if (I.real_bytes == 4) return a == 0 ? 8 : 16;
+  return a == 0 ? 4 : 8;
+}
+
+// ------------------------------------------------------------ tables
+
+template <typename R>
+static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::vector<void *> &owned,
+                       cudaError_t &err) {
+  std::vector<R> pos(T.pos.begin(), T.pos.end()), sum(T.sum.begin(), T.sum.end()),
+      chunk(T.chunk.begin(), T.chunk.end());
+  M.pos = (const typename V4T<R>::T *)arena.put(pos.data(), pos.size() * sizeof(R), err);
+  M.sum = (const typename V2T<R>::T *)arena.put(sum.data(), sum.size() * sizeof(R), err);
+  M.chunk = (const typename V4T<R>::T *)arena.put(chunk.data(), chunk.size() * sizeof(R), err);
+  M.sm_c = T.sm_c;
+  M.sm_inv = T.sm_inv;
+  (void)owned;
+}
+
+// factorise every (axis, species, gamma) line matrix of one instance, forward
+// (and transposed for the adjoint), and upload in the instance's precision
+etd_status build_instance_tables(etd_ctx *ctx, Instance &I) {
+  cudaError_t err = cudaSuccess;
+  static const double gammas[3] = {1.0, 3.0, 4.0};
+  for (int a = 0; a < I.dim; ++a) {
+    const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+    for (int s = 0; s < I.S; ++s)
+      for (int g = 0; g < 3; ++g)
+        for (int tr = 0; tr < 2; ++tr) {
+          const double r = (I.k / gammas[g]) * I.D[s] / (h * h);
+          HostTab T;
+          build_tab((int)I.n[a], I.bc[a], r, tr != 0, I.plan[a].L, T);
+          if (I.real_bytes == 8)
+            upload_tab<double>(I.arena, T, I.tab64[tr][a][s][g], I.owned, err);
+          else
+            upload_tab<float>(I.arena, T, I.tab32[tr][a][s][g], I.owned, err);
+          if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
+        }
+  }
+  // manufactured-source coordinate tables
+  I.has_source = (I.rkind == ETD_REACTION_ENZYME && I.rp[0] != 0.0);
+  I.src_lf = 0.0;
+  for (int a = 0; a < 3; ++a) I.phi[a] = nullptr;
+  if (I.has_source) {
+    for (int a = 0; a < I.dim; ++a) {
+      const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+      std::vector<double> ph(I.n[a]);
+      for (long long i = 0; i < I.n[a]; ++i) {
+        const double x = (I.bc[a] == BC_DIRICHLET) ? (i + 1) * h : i * h;
+        ph[i] = std::sin(M_PI * x / I.length[a]);
+      }
+      I.src_lf += (M_PI / I.length[a]) * (M_PI / I.length[a]);
+      if (I.real_bytes == 8) {
+        I.phi[a] = I.arena.put(ph.data(), ph.size() * 8, err);
+      } else {
+        std::vector<float> pf(ph.begin(), ph.end());
+        I.phi[a] = I.arena.put(pf.data(), pf.size() * 4, err);
+      }
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading source tables");
+    }
+  }
+  return ETD_OK;
+}
+
+// ------------------------------------------------------------ sweep args
+
+template <typename R>
+void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
+  const AxisPlan &P = I.plan[a];
+  memset(&A, 0, sizeof(A));
+  A.N = I.N;
+  A.st = P.st;
+  A.nlines = P.nlines;
+  A.n = (int)I.n[a];
+  A.nlo_blocks = P.nlo_blocks;
+  A.m = P.m;
+  A.nlb = P.nlb;
+  A.pitch = P.pitch;
+  A.nblocks = P.nblocks;
+  for (int s = 0; s < I.S; ++s)
+    for (int g = 0; g < 3; ++g) {
+      if constexpr (sizeof(R) == 8) A.mat[s][g] = I.tab64[transpose][a][s][g];
+      else A.mat[s][g] = I.tab32[transpose][a][s][g];
+    }
+  A.k = I.k;
+  A.rkind = I.rkind;
+  for (int j = 0; j < 8; ++j) A.rp[j] = I.rp[j];
+  for (int b = 0; b < 3; ++b) A.phi[b] = (const R *)I.phi[b];
+  A.nx = (int)I.n[0];
+  A.ny = (int)I.n[1];
+  A.src_lf = I.src_lf;
+}
+template void fill_args<float>(const Instance &, int, int, SweepArgs<float> &);
+template void fill_args<double>(const Instance &, int, int, SweepArgs<double> &);
+
+// forward step of one instance on stream s: U holds U_n at t_n, gets U_{n+1}
+cudaError_t prof_begin(etd_ctx *ctx, cudaStream_t s, cudaEvent_t &ev) {
+  ev = nullptr;
+  if (!ctx || !ctx->profiling) return cudaSuccess;
+  if (ctx->prof_pool.empty()) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+  } else {
+    ev = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+  }
+  return cudaEventRecord(ev, s);
+}
+
+cudaError_t prof_end(etd_ctx *ctx, cudaStream_t s, int kind, cudaEvent_t ev0) {
+  if (!ctx || !ctx->profiling || !ev0) return cudaSuccess;
+  cudaEvent_t ev1;
+  cudaError_t e = prof_begin(ctx, s, ev1);
+  if (e != cudaSuccess) return e;
+  ctx->prof_events.push_back({kind, {ev0, ev1}});
+  return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t s, etd_ctx *prof) {
+  R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
+  for (int a = 0; a < I.dim; ++a) {
+    const AxisPlan &P = I.plan[a];
+    SweepArgs<R> A;
+    fill_args<R>(I, a, 0, A);
+    if (P.kind == SWEEP_FIRST) {
+      A.in[0] = U;
+      A.out[0] = cu; A.out[1] = cf; A.out[2] = w;
+      A.t_eval = t;
+    } else if (P.kind == SWEEP_MIDDLE) {
+      A.in[0] = cu; A.in[1] = cf; A.in[2] = w;
+      A.out[0] = cu; A.out[1] = cf; A.out[2] = w;
+      A.t_eval = t;
+    } else {
+      A.in[0] = cu; A.in[1] = cf; A.in[2] = w;
+      A.out[0] = U;
+      A.t_eval = t + I.k;
+    }
+    A.exp_mt = std::exp(-A.t_eval);
+    cudaEvent_t ev0;
+    cudaError_t e = prof_begin(prof, s, ev0);
+    if (e != cudaSuccess) return e;
+    e = launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+    if (e != cudaSuccess) return e;
+    e = prof_end(prof, s, P.kind, ev0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t forward_step(const Instance &I, void *U, double t, cudaStream_t s, etd_ctx *prof) {
+  if (I.real_bytes == 8) return step_instance<double>(I, (double *)U, t, s, prof);
+  return step_instance<float>(I, (float *)U, t, s, prof);
+}
+
+// ------------------------------------------------------------ instances
+
+etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const double *D, const etd_reaction *rx,
+                         double k, int32_t precision, bool with_scratch) {
+  I.dim = grid->dim;
+  I.N = 1;
+  for (int a = 0; a < 3; ++a) {
+    I.n[a] = a < I.dim ? grid->n[a] : 1;
+    I.bc[a] = a < I.dim ? grid->bc[a] : 0;
+    I.length[a] = a < I.dim ? grid->length[a] : 1.0;
+    I.N *= I.n[a];
+  }
+  I.S = rx->nspecies;
+  for (int s = 0; s < I.S; ++s) I.D[s] = D[s];
+  I.k = k;
+  I.rkind = rx->kind;
+  for (int j = 0; j < 8; ++j) I.rp[j] = rx->params[j];
+  I.real_bytes = precision == ETD_FP64 ? 8 : 4;
+  for (int a = 0; a < I.dim; ++a) {
+    int L = default_chunk(I, a);
+    while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
+    if (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
+      return fail(ctx, ETD_ERR_UNSUPPORTED, "axis %d with n = %lld does not fit one block", a, (long long)I.n[a]);
+  }
+  etd_status st = build_instance_tables(ctx, I);
+  if (st != ETD_OK) return st;
+  if (with_scratch) {
+    const size_t bytes = (size_t)I.S * I.N * I.real_bytes;
+    for (int f = 0; f < 3; ++f) {
+      cudaError_t e = cudaMalloc(&I.scratch[f], bytes);
+      if (e != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "scratch allocation of %zu bytes failed", bytes);
+      I.owned.push_back(I.scratch[f]);
+    }
+  }
+  return ETD_OK;
+}
+
+}  // namespace etd
+
+// ================================================================= C ABI
+
+extern "C" {
+
+etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction *reaction, double k,
+                      int32_t precision, void *stream, etd_ctx **out) {
+  if (!out) return fail(nullptr, ETD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  etd_status st = validate_problem(grid, D, reaction, k, precision);
+  if (st != ETD_OK) return st;
+  etd_ctx *ctx = new (std::nothrow) etd_ctx();
+  if (!ctx) return fail(nullptr, ETD_ERR_OOM, "host allocation failed");
+  ctx->stream = (cudaStream_t)stream;
+  ctx->precision = precision;
+  ctx->batched = false;
+  ctx->inst.resize(1);
+  st = init_instance(ctx, ctx->inst[0], grid, D, reaction, k, precision, true);
+  if (st != ETD_OK) {
+    g_create_error = ctx->err;
+    etd_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return ETD_OK;
+}
+
+etd_status etd_set_stream(etd_ctx *ctx, void *stream) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->stream = (cudaStream_t)stream;
+  ctx->graphs.clear();
+  return ETD_OK;
+}
+
+etd_status etd_step(etd_ctx *ctx, void *U, double t_n) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_step on a batched context");
+  if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
+  if (!std::isfinite(t_n)) return fail(ctx, ETD_ERR_INVALID_ARG, "t_n not finite");
+  cudaError_t e = forward_step(ctx->inst[0], U, t_n, ctx->stream, ctx);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etd_step launch");
+  return ETD_OK;
+}
+
+etd_status etd_run(etd_ctx *ctx, void *U, double t0, int64_t nsteps) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_run on a batched context");
+  if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
+  if (nsteps < 0) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0");
+  if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
+  const Instance &I = ctx->inst[0];
+  return run_steps(ctx, [&](cudaStream_t s, int64_t n) -> cudaError_t {
+    return forward_step(I, U, t0 + (double)n * I.k, s, ctx);
+  }, GraphKey{U, nullptr, t0, nsteps}, nsteps);
+}
+
+etd_status etd_run_host(etd_ctx *ctx, void *U_host, double t0, int64_t nsteps) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_run_host on a batched context");
+  if (!U_host) return fail(ctx, ETD_ERR_INVALID_ARG, "U_host is NULL");
+  const Instance &I = ctx->inst[0];
+  const size_t bytes = (size_t)I.S * I.N * I.real_bytes;
+  if (!ctx->host_state) {
+    cudaError_t e = cudaMalloc(&ctx->host_state, bytes);
+    if (e != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "device state allocation of %zu bytes failed", bytes);
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->host_state, U_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+  etd_status st = etd_run(ctx, ctx->host_state, t0, nsteps);
+  if (st != ETD_OK) return st;
+  e = cudaMemcpyAsync(U_host, ctx->host_state, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  return ETD_OK;
+}
+
+etd_status etd_profile(etd_ctx *ctx, int32_t enable) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->profiling = enable != 0;
+  return ETD_OK;
+}
+
+etd_status etd_profile_read(etd_ctx *ctx, double *ms, int64_t *launches) {
+  if (!ctx || !ms || !launches) return fail(ctx, ETD_ERR_INVALID_ARG, "null argument");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  for (auto &rec : ctx->prof_events) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, rec.second.first, rec.second.second);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed time");
+    const int kd = rec.first < 0 ? 0 : (rec.first > 2 ? 2 : rec.first);
+    ms[kd] += t;
+    launches[kd] += 1;
+    ctx->prof_pool.push_back(rec.second.first);
+    ctx->prof_pool.push_back(rec.second.second);
+  }
+  ctx->prof_events.clear();
+  return ETD_OK;
+}
+
+etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
+  if (!ctx || !info) return fail(nullptr, ETD_ERR_INVALID_ARG, "null ctx or info");
+  memset(info, 0, sizeof(*info));
+  const Instance &I = ctx->inst[0];
+  info->dim = I.dim;
+  info->nspecies = I.S;
+  info->precision = ctx->precision;
+  long long N = 0, scratch = 0;
+  int launches = 0;
+  for (const Instance &J : ctx->inst) {
+    N += J.N;
+    scratch += 3LL * J.S * J.N * J.real_bytes;
+  }
+  launches = ctx->batched ? I.dim : I.dim;
+  info->npoints = N;
+  info->state_bytes = (int64_t)I.S * N * I.real_bytes;
+  info->scratch_bytes = scratch;
+  info->algorithmic_bytes = (int64_t)(4 * I.dim - 2) * I.S * N * I.real_bytes;
+  info->launches_per_step = launches;
+  for (int a = 0; a < I.dim; ++a) {
+    info->chunk[a] = I.plan[a].L;
+    info->lines_per_block[a] = I.plan[a].nlb;
+  }
+  return ETD_OK;
+}
+
+void etd_destroy(etd_ctx *ctx) {
+  if (!ctx) return;
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  for (Instance &I : ctx->inst) {
+    for (void *p : I.owned) cudaFree(p);
+    I.owned.clear();
+    I.arena.release();
+  }
+  if (ctx->host_state) cudaFree(ctx->host_state);
+  for (auto &rec : ctx->prof_events) {
+    cudaEventDestroy(rec.second.first);
+    cudaEventDestroy(rec.second.second);
+  }
+  for (cudaEvent_t ev : ctx->prof_pool) cudaEventDestroy(ev);
+  for (void *p : ctx->owned) cudaFree(p);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// etd_context.h -- the opaque etd_ctx and per-instance state of libetdrdpif.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/etdrdpif.h"
+#include "etd_internal.h"
+
+#define ETD_MAX_BLOCK_THREADS 512
+
+namespace etd {
+
+// device allocations of one instance's tables (one cudaMalloc each)
+struct DeviceArena {
+  std::vector<void *> blocks;
+  void *put(const void *host, size_t bytes, cudaError_t &err) {
+    if (err != cudaSuccess) return nullptr;
+    void *d = nullptr;
+    err = cudaMalloc(&d, bytes < 16 ? 16 : bytes);
+    if (err != cudaSuccess) return nullptr;
+    blocks.push_back(d);
+    err = cudaMemcpy(d, host, bytes, cudaMemcpyHostToDevice);
+    return d;
+  }
+  void release() {
+    for (void *p : blocks) cudaFree(p);
+    blocks.clear();
+  }
+};
+
+// launch plan of one axis sweep
+struct AxisPlan {
+  int kind = 0;        // SweepKind
+  int L = 8;           // chunk length (elements per thread)
+  int m = 1;           // chunks per line
+  int nlb = 1;         // lines per block
+  int pitch = 1;       // shared-memory pitch
+  int nthreads = 1;    // nlb * m
+  int nlo_blocks = 1;  // strided sweeps: blocks along the contiguous line index
+  int nblocks = 1;
+  long long st = 1;    // element stride of the axis
+  long long nlines = 1;
+  size_t smem = 0;
+};
+
+// one problem: grid, coefficients, tables, plans and scratch
+struct Instance {
+  int dim = 2, S = 1, real_bytes = 8;
+  long long n[3] = {1, 1, 1};
+  int bc[3] = {0, 0, 0};
+  double length[3] = {1, 1, 1};
+  long long N = 1;
+  double D[MAX_SPECIES] = {0, 0};
+  double k = 0;
+  int rkind = 0;
+  double rp[8] = {0};
+  bool has_source = false;
+  double src_lf = 0;
+  void *phi[3] = {nullptr, nullptr, nullptr};
+  AxisPlan plan[3];
+  // [transpose][axis][species][gamma index: 0 -> 1, 1 -> 3, 2 -> 4]
+  MatTab<float> tab32[2][3][MAX_SPECIES][3];
+  MatTab<double> tab64[2][3][MAX_SPECIES][3];
+  void *scratch[3] = {nullptr, nullptr, nullptr};  // c_U, c_f, w
+  DeviceArena arena;
+  std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
+};
+
+struct GraphKey {
+  const void *U;
+  const void *U2;
+  double t0;
+  int64_t nsteps;
+  bool operator==(const GraphKey &o) const {
+    return U == o.U && U2 == o.U2 && t0 == o.t0 && nsteps == o.nsteps;
+  }
+};
+
+}  // namespace etd
+
+struct etd_ctx {
+  cudaStream_t stream = nullptr;
+  int32_t precision = 0;
+  bool batched = false;
+  std::vector<etd::Instance> inst;
+  std::string err = "no error";
+  void *host_state = nullptr;           // device copy used by etd_run_host
+  std::vector<void *> owned;            // context-level device buffers
+  std::list<std::pair<etd::GraphKey, cudaGraphExec_t>> graphs;  // captured multi-step runs
+  // batched launch data (device)
+  void *batch_args[3] = {nullptr, nullptr, nullptr};  // SweepArgs<R>[ninst] per axis
+  int *batch_block_start[3] = {nullptr, nullptr, nullptr};
+  int batch_total_blocks[3] = {0, 0, 0};
+  int batch_threads[3] = {0, 0, 0};
+  size_t batch_smem[3] = {0, 0, 0};
+  int batch_L[3] = {0, 0, 0};
+  // per-sweep profiling (etd_profile)
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+  std::vector<cudaEvent_t> prof_pool;
+  // adjoint / gradient workspace (allocated on first use)
+  void *adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
+};
+
+namespace etd {
+
+etd_status fail(etd_ctx *ctx, etd_status st, const char *fmt, ...);
+etd_status cuda_fail(etd_ctx *ctx, cudaError_t e, const char *what);
+cudaError_t forward_step(const Instance &I, void *U, double t, cudaStream_t s, etd_ctx *prof = nullptr);
+cudaError_t prof_begin(etd_ctx *ctx, cudaStream_t s, cudaEvent_t &ev);
+cudaError_t prof_end(etd_ctx *ctx, cudaStream_t s, int kind, cudaEvent_t ev0);
+template <typename R> void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A);
+
+// Enqueue nsteps steps with enqueue(stream, step_index).  Runs of two or more
+// steps on a non-legacy stream are captured once into a CUDA graph (cached
+// by key) and replayed; otherwise kernels are launched directly.
+template <typename F>
+etd_status run_steps(etd_ctx *ctx, F enqueue, GraphKey key, int64_t nsteps) {
+  cudaStream_t s = ctx->stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  bool graphs = nsteps >= 2 && s != nullptr && !ctx->profiling && std::getenv("ETD_NO_GRAPHS") == nullptr;
+  if (graphs && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) graphs = false;
+  if (!graphs) {
+    for (int64_t n = 0; n < nsteps; ++n) {
+      cudaError_t e = enqueue(s, n);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+    }
+    return ETD_OK;
+  }
+  for (auto it = ctx->graphs.begin(); it != ctx->graphs.end(); ++it)
+    if (it->first == key) {
+      cudaError_t e = cudaGraphLaunch(it->second, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+      ctx->graphs.splice(ctx->graphs.begin(), ctx->graphs, it);
+      return ETD_OK;
+    }
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+  cudaError_t le = cudaSuccess;
+  for (int64_t n = 0; n < nsteps && le == cudaSuccess; ++n) le = enqueue(s, n);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(ctx, le, "step launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+  ctx->graphs.emplace_front(key, ex);
+  while (ctx->graphs.size() > 4) {
+    cudaGraphExecDestroy(ctx->graphs.back().second);
+    ctx->graphs.pop_back();
+  }
+  e = cudaGraphLaunch(ex, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+  return ETD_OK;
+}
+
+}  // namespace etd

@@ -1,0 +1,95 @@
+// etd_internal.h -- types shared by the host side and the sweep kernels of
+// libetdrdpif.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etd {
+
+// The three fused sweeps of one step (Section 7, Figs. flow2d / flow3d):
+//  FIRST  (axis 0, contiguous lines): F(U_n, t_n), the five solves
+//         T,S on U_n; T,S on F(U_n); P on U_n + k F(U_n)  -> c_U, c_f, w
+//  MIDDLE (axis 1 of a 3D grid, strided lines): the same five solves applied
+//         to (c_U, c_f, w) in place (R_2 on c_U and c_f, P_2 on w)
+//  LAST   (axis d-1, strided lines): U* = P_d w, F(U*, t_{n+1}),
+//         f1 = 9 c_U + 2k c_f + k F*, f2 = 8 c_U + 3k/2 c_f + k/2 F*,
+//         U_{n+1} = T_d f1 - S_d f2
+enum SweepKind { SWEEP_FIRST = 0, SWEEP_MIDDLE = 1, SWEEP_LAST = 2 };
+
+constexpr int MAX_SPECIES = 2;
+
+template <typename R> struct V4T;
+template <> struct V4T<float> { using T = float4; };
+template <> struct V4T<double> { using T = double4; };
+template <typename R> struct V2T;
+template <> struct V2T<float> { using T = float2; };
+template <> struct V2T<double> { using T = double2; };
+
+// Tables of one line matrix M = I + (k/gamma) D_s B_p (or its modified
+// tridiagonal part M' for periodic lines), chunked into m chunks of L
+// positions, stored position-major: entry (t, j) at index t*m + j, i.e. the
+// t-th position of chunk j.  Positions past the end of the line are identity
+// rows (a = 0, e = 1, alpha = 0, z = 0, v = w = 0).
+//   pos[t*m+j]   = (a, e, alpha, z):  forward g_i = a_i g_{i-1} + e_i b_i,
+//                  backward x_i = g_i - alpha_i x_{i+1}, Sherman-Morrison
+//                  vector z (periodic only)
+//   sum[t*m+j]   = (v, w): chunk summaries F_j = sum v b (zero-carry forward
+//                  value at the chunk end) and Y_j = sum w b (zero-carry
+//                  backward value at the chunk start)
+//   chunk[j]     = (Aend, kappa, Bst, 0): G_in[j+1] = Aend G_in[j] + F_j;
+//                  X[j] = Y_j + kappa G_in[j] + Bst X[j+1]
+template <typename R> struct MatTab {
+  const typename V4T<R>::T *pos;
+  const typename V2T<R>::T *sum;
+  const typename V4T<R>::T *chunk;
+  double sm_c;    // v_{p-1} of the Sherman-Morrison rank-one term (periodic)
+  double sm_inv;  // 1 / (1 + v.z)                                  (periodic)
+};
+
+// Everything one sweep launch needs for one problem instance.
+template <typename R> struct SweepArgs {
+  const R *in[3];  // FIRST: in[0] = U_n.  MIDDLE/LAST: c_U, c_f, w
+  R *out[3];       // FIRST/MIDDLE: c_U, c_f, w.  LAST: out[0] = U_{n+1}
+  long long N;     // points per species (species stride in elements)
+  long long st;    // element stride of the swept axis
+  long long nlines;  // lines of the swept axis = N / n
+  int n;           // nodes on the swept axis
+  int nlo_blocks;  // strided sweeps: blocks along the low (contiguous) line index
+  int m;           // chunks per line
+  int nlb;         // lines per block (blockDim.x = nlb * m)
+  int pitch;       // shared-memory pitch of one line's chunk summaries
+  int nblocks;     // blocks of this instance
+  MatTab<R> mat[MAX_SPECIES][3];  // [species][0: P (gamma 1), 1: T (gamma 3), 2: S (gamma 4)]
+  double k;        // time step
+  double t_eval;   // time at which F is evaluated in this sweep
+  double exp_mt;   // e^{-t_eval} (manufactured source)
+  int rkind;       // etd_reaction_kind
+  double rp[8];    // reaction parameters
+  const R *phi[3]; // sin(pi x_a / L_a) per axis (manufactured source), NULL otherwise
+  int nx, ny;      // grid extents of axes 0 and 1 (point -> coordinates)
+  double src_lf;   // Sum_a (pi / L_a)^2
+};
+
+// host-side launchers (one translation unit per element type)
+cudaError_t launch_sweep(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads,
+                         size_t smem, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads,
+                         size_t smem, cudaStream_t s);
+// batched: args[] in device memory, block_start[i] = first block of instance i (prefix, ninst+1)
+cudaError_t launch_sweep_batched(const SweepArgs<float> *args_dev, const int *block_start_dev, int ninst,
+                                 int total_blocks, int nspecies, int L, int kind, int nthreads,
+                                 size_t smem, cudaStream_t s);
+cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *block_start_dev, int ninst,
+                                 int total_blocks, int nspecies, int L, int kind, int nthreads,
+                                 size_t smem, cudaStream_t s);
+
+// shared-memory bytes of one sweep block
+inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes) {
+  int nq = (kind == SWEEP_LAST) ? 3 * nspecies : 5 * nspecies;
+  size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes;
+  sums = (sums + 15) & ~(size_t)15;
+  return sums + (size_t)nq * nlb * sizeof(double);
+}
+
+}  // namespace etd

@@ -1,0 +1,20 @@
+// etd_sweep_f64.cu -- sweep kernels and launchers for double.
+#include "etd_sweep_launch.cuh"
+
+namespace etd {
+
+cudaError_t launch_sweep(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                         cudaStream_t s) {
+#define CALL(S_, L_, K_) launch_one<double, S_, L_, K_>(a, nthreads, smem, s)
+  ETD_DISPATCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_sweep_batched(const SweepArgs<double> *args, const int *bs, int ninst, int total, int nspecies,
+                                 int L, int kind, int nthreads, size_t smem, cudaStream_t s) {
+#define CALL(S_, L_, K_) launch_one_batched<double, S_, L_, K_>(args, bs, ninst, total, nthreads, smem, s)
+  ETD_DISPATCH(CALL)
+#undef CALL
+}
+
+}  // namespace etd

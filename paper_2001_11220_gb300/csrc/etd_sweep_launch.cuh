@@ -1,0 +1,69 @@
+// etd_sweep_launch.cuh -- host launchers for the sweep kernels of one element
+// type; included once per element type by etd_sweep_f32.cu / etd_sweep_f64.cu.
+#pragma once
+
+#include <mutex>
+#include <unordered_map>
+
+#include "etd_sweep.cuh"
+
+namespace etd {
+
+// raise the dynamic shared-memory limit of a kernel once per requested size
+inline cudaError_t ensure_smem(const void *fn, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> done;
+  if (smem <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= smem) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done[fn] = smem;
+  return e;
+}
+
+template <typename R, int S, int L, int KIND>
+cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStream_t s) {
+  constexpr bool CONTIG = (KIND == SWEEP_FIRST);
+  auto fn = sweep_kernel<R, S, L, CONTIG, KIND>;
+  cudaError_t e = ensure_smem((const void *)fn, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<a.nblocks, nthreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int S, int L, int KIND>
+cudaError_t launch_one_batched(const SweepArgs<R> *args, const int *bs, int ninst, int total, int nthreads,
+                               size_t smem, cudaStream_t s) {
+  constexpr bool CONTIG = (KIND == SWEEP_FIRST);
+  auto fn = sweep_kernel_batched<R, S, L, CONTIG, KIND>;
+  cudaError_t e = ensure_smem((const void *)fn, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<total, nthreads, smem, s>>>(args, bs, ninst);
+  return cudaGetLastError();
+}
+
+#define ETD_DISPATCH(CALL)                                                        \
+  switch (nspecies * 1000 + L * 10 + kind) {                                      \
+    case 1040: return CALL(1, 4, SWEEP_FIRST);                                    \
+    case 1041: return CALL(1, 4, SWEEP_MIDDLE);                                   \
+    case 1042: return CALL(1, 4, SWEEP_LAST);                                     \
+    case 1080: return CALL(1, 8, SWEEP_FIRST);                                    \
+    case 1081: return CALL(1, 8, SWEEP_MIDDLE);                                   \
+    case 1082: return CALL(1, 8, SWEEP_LAST);                                     \
+    case 1160: return CALL(1, 16, SWEEP_FIRST);                                   \
+    case 1161: return CALL(1, 16, SWEEP_MIDDLE);                                  \
+    case 1162: return CALL(1, 16, SWEEP_LAST);                                    \
+    case 2040: return CALL(2, 4, SWEEP_FIRST);                                    \
+    case 2041: return CALL(2, 4, SWEEP_MIDDLE);                                   \
+    case 2042: return CALL(2, 4, SWEEP_LAST);                                     \
+    case 2080: return CALL(2, 8, SWEEP_FIRST);                                    \
+    case 2081: return CALL(2, 8, SWEEP_MIDDLE);                                   \
+    case 2082: return CALL(2, 8, SWEEP_LAST);                                     \
+    case 2160: return CALL(2, 16, SWEEP_FIRST);                                   \
+    case 2161: return CALL(2, 16, SWEEP_MIDDLE);                                  \
+    case 2162: return CALL(2, 16, SWEEP_LAST);                                    \
+    default: return cudaErrorInvalidValue;                                        \
+  }
+
+}  // namespace etd

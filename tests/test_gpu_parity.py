@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances: FP64 <= 1e-12 relative (max over species of
+max|U_gpu - U_oracle| / max|U_oracle|), after one step and at the end of a
+run.  FP32: the error against the FP64 oracle is measured and bounded by the
+per-case figure below (printed with -s).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2001_11220_gb300 import workloads as W  # noqa: E402
+from tests.dense_reference import oracle_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def _api():
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    return EtdRdpIf
+
+
+def rel_err(a, ref):
+    return max(float(np.max(np.abs(a[s] - ref[s])) / max(np.max(np.abs(ref[s])), 1e-300)) for s in range(ref.shape[0]))
+
+
+def gpu_run(w, U0, nsteps, precision="fp64", t0=0.0):
+    ctx = _api().from_workload(w, precision)
+    U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+    ctx.run(U, t0, nsteps)
+    torch.cuda.synchronize()
+    out = U.double().cpu().numpy()
+    ctx.close()
+    return out
+
+
+def oracle_run(w, U0, nsteps, t0=0.0):
+    return oracle.run(oracle_problem(w), U0, t0, nsteps)
+
+
+def case(name, n, bc, reaction, D, params=(), k=0.05, ic="normal", ic_args=None, length=None):
+    S = len(D)
+    if ic_args is None and ic == "normal":
+        ic_args = ((0.8, 1.2)[:S], 0.1)
+    return W.Workload(name, n, bc, D, reaction, params, k, 1, length=length, ic=ic, ic_args=ic_args or ())
+
+
+ONE_STEP_CASES = [
+    case("bru2d_neu_64", (64, 64), W.NEUMANN, (2e-3, 2e-3), "brusselator", (1.0, 3.4), k=0.01),
+    case("bru2d_neu_ragged", (37, 23), W.NEUMANN, (0.02, 0.05), "brusselator", (1.0, 3.4)),
+    case("enz2d_dir_src", (45, 31), W.DIRICHLET, (0.2,), "enzyme", (1.0, 0.2), ic="sine"),
+    case("enz2d_dir_plain", (19, 40), W.DIRICHLET, (0.2,), "enzyme", (0.0, 0.0)),
+    case("sch2d_per", (41, 29), W.PERIODIC, (0.01, 0.1), "schnakenberg", (0.1, 0.9, 10.0)),
+    case("gs2d_mixed", (33, 47), (W.PERIODIC, W.NEUMANN), (0.02, 0.01), "gray_scott", (0.04, 0.06), k=0.5),
+    case("lin2d_dir_stiff", (130, 67), W.DIRICHLET, (3.0,), "linear", (-0.7, 0.2), k=0.5),
+    case("min2d_dir", (3, 3), W.DIRICHLET, (0.3, 0.1), "linear", (0.5, 0.0)),
+    case("min2d_neu", (3, 3), W.NEUMANN, (0.3, 0.1), "brusselator", (1.0, 3.4)),
+    case("min2d_per", (3, 3), W.PERIODIC, (0.3, 0.1), "gray_scott", (0.04, 0.06)),
+    case("long_x", (517, 5), (W.NEUMANN, W.PERIODIC), (0.5, 0.1), "brusselator", (1.0, 3.4)),
+    case("long_y", (5, 517), (W.PERIODIC, W.DIRICHLET), (0.5, 0.1), "brusselator", (1.0, 3.4)),
+    case("heun_D0", (21, 13), W.NEUMANN, (0.0, 0.0), "brusselator", (1.0, 3.4)),
+    case("gs3d_mixed", (19, 17, 23), (W.PERIODIC, W.NEUMANN, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+         (0.04, 0.06), k=0.5),
+    case("mms3d_16", (16, 16, 16), W.DIRICHLET, (1.0,), "enzyme", (1.0, 1.0), k=1 / 17, ic="sine"),
+    case("bru3d_per", (33, 20, 9), W.PERIODIC, (0.05, 0.02), "brusselator", (1.0, 3.4)),
+    case("min3d", (3, 3, 3), (W.DIRICHLET, W.NEUMANN, W.PERIODIC), (0.3, 0.1), "brusselator", (1.0, 3.4)),
+    case("sch3d_stiff", (24, 24, 24), W.PERIODIC, (1.0, 10.0), "schnakenberg", (0.1, 0.9, 1000.0), k=1e-3,
+         ic="uniform", ic_args=((1.0, 0.9), 1e-3)),
+]
+
+
+@pytest.mark.parametrize("w", ONE_STEP_CASES, ids=lambda w: w.name)
+def test_one_step_fp64_matches_oracle(w):
+    U0 = W.initial_state(w)
+    got = gpu_run(w, U0, 1, "fp64", t0=0.3)
+    ref = oracle_run(w, U0, 1, t0=0.3)
+    err = rel_err(got, ref)
+    assert err <= FP64_TOL, err
+
+
+@pytest.mark.parametrize("w", ONE_STEP_CASES[:6] + ONE_STEP_CASES[13:16], ids=lambda w: w.name)
+def test_one_step_fp32_error_bounded(w):
+    U0 = W.initial_state(w)
+    got = gpu_run(w, U0, 1, "fp32", t0=0.3)
+    ref = oracle_run(w, U0, 1, t0=0.3)
+    err = rel_err(got, ref)
+    print(f"FP32 one-step error {w.name}: {err:.3e}")
+    assert err <= 2e-5, err
+
+
+def test_brusselator_64_full_run_fp64_and_fp32():
+    """2D Brusselator 64x64 Neumann, k = 0.01, 100 steps (T = 1)."""
+    w = W.brusselator_2d()
+    U0 = W.initial_state(w)
+    ref = oracle_run(w, U0, w.steps)
+    e64 = rel_err(gpu_run(w, U0, w.steps, "fp64"), ref)
+    e32 = rel_err(gpu_run(w, U0, w.steps, "fp32"), ref)
+    print(f"brusselator2d_64 100 steps: FP64 err {e64:.3e}  FP32 err {e32:.3e}")
+    assert e64 <= FP64_TOL
+    assert e32 <= 1e-4
+
+
+@pytest.mark.parametrize("p", [32])
+def test_mms3d_full_run(p):
+    w = W.mms_3d(p)
+    U0 = W.initial_state(w)
+    ref = oracle_run(w, U0, w.steps)
+    e64 = rel_err(gpu_run(w, U0, w.steps, "fp64"), ref)
+    e32 = rel_err(gpu_run(w, U0, w.steps, "fp32"), ref)
+    exact = W.exact_mms(w, w.steps * w.k)
+    print(f"mms3d_{p}: FP64 err vs oracle {e64:.3e}, FP32 {e32:.3e}, oracle vs exact {rel_err(ref, exact):.3e}")
+    assert e64 <= FP64_TOL
+    assert e32 <= 1e-5
+
+
+def test_mms3d_256_one_step_full_size():
+    """3D Dirichlet manufactured problem at the benchmark size 256^3, one step, FP64 and FP32."""
+    w = W.mms_3d(256)
+    U0 = W.initial_state(w)
+    ref = oracle_run(w, U0, 1)
+    e64 = rel_err(gpu_run(w, U0, 1, "fp64"), ref)
+    e32 = rel_err(gpu_run(w, U0, 1, "fp32"), ref)
+    print(f"mms3d_256 one step: FP64 err {e64:.3e}, FP32 err {e32:.3e}")
+    assert e64 <= FP64_TOL
+    assert e32 <= 1e-5
+
+
+def test_schnakenberg_4096_one_step_fp32():
+    """2D periodic Schnakenberg 4096^2 (cyclic lines, Sherman-Morrison), FP32 state, one step."""
+    w = W.schnakenberg_2d(4096)
+    U0 = W.initial_state(w)
+    ref = oracle_run(w, U0, 1)
+    e32 = rel_err(gpu_run(w, U0, 1, "fp32"), ref)
+    print(f"schnakenberg2d_4096 one step FP32 err {e32:.3e}")
+    assert e32 <= 1e-5
+
+
+def test_run_host_matches_device_run():
+    w = W.brusselator_2d(p=40, steps=7)
+    U0 = W.initial_state(w)
+    EtdRdpIf = _api()
+    ctx = EtdRdpIf.from_workload(w, "fp64")
+    U = torch.tensor(U0, device="cuda")
+    ctx.run(U, 0.0, w.steps)
+    H = torch.tensor(U0).pin_memory()
+    ctx.run_host(H, 0.0, w.steps)
+    torch.cuda.synchronize()
+    assert torch.equal(U.cpu(), H)
+    ctx.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    w = W.brusselator_2d(p=48, steps=9)
+    U0 = W.initial_state(w)
+    EtdRdpIf = _api()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = EtdRdpIf.from_workload(w, "fp32")
+        A = torch.tensor(U0, device="cuda", dtype=torch.float32)
+        B = A.clone()
+        ctx.run(A, 0.0, w.steps)          # captured into a CUDA graph
+        ctx.run(B, 0.0, w.steps)          # different buffer: captured again
+        C = torch.tensor(U0, device="cuda", dtype=torch.float32)
+        os.environ["ETD_NO_GRAPHS"] = "1"
+        try:
+            ctx.run(C, 0.0, w.steps)      # direct launches
+        finally:
+            del os.environ["ETD_NO_GRAPHS"]
+    s.synchronize()
+    assert torch.equal(A, B) and torch.equal(A, C)
+    ctx.close()
+
+
+def test_step_sequence_equals_run():
+    w = W.brusselator_2d(p=30, steps=4)
+    U0 = W.initial_state(w)
+    EtdRdpIf = _api()
+    ctx = EtdRdpIf.from_workload(w, "fp64")
+    A = torch.tensor(U0, device="cuda")
+    B = A.clone()
+    ctx.run(A, 0.0, 4)
+    for n in range(4):
+        ctx.step(B, n * w.k)
+    torch.cuda.synchronize()
+    assert torch.equal(A, B)
+    ctx.close()
+
+
+def test_bad_state_rejected():
+    w = W.brusselator_2d(p=16, steps=1)
+    ctx = _api().from_workload(w, "fp64")
+    with pytest.raises(ValueError):
+        ctx.step(torch.zeros((2, 16, 16), device="cuda", dtype=torch.float32), 0.0)
+    ctx.close()
