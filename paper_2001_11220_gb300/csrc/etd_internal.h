@@ -30,14 +30,16 @@ template <> struct V2T<double> { using T = double2; };
 // tridiagonal part M' for periodic lines), chunked into m chunks of L
 // positions, stored position-major: entry (t, j) at index t*m + j, i.e. the
 // t-th position of chunk j.  Positions past the end of the line are identity
-// rows (a = 0, e = 1, alpha = 0, z = 0, v = w = 0).
-//   pos[t*m+j]   = (a, e, alpha, z):  forward g_i = a_i g_{i-1} + e_i b_i,
-//                  backward x_i = g_i - alpha_i x_{i+1}, Sherman-Morrison
-//                  vector z (periodic only)
+// rows (nl = 0, e = 1, alpha = 0, z = 0, v = w = 0).
+//   pos[t*m+j]   = (nl, e, alpha, z): forward g_i = (b_i + nl_i g_{i-1}) e_i
+//                  (nl = minus the sub-diagonal, e = 1 / pivot), backward
+//                  x_i = g_i - alpha_i x_{i+1}, Sherman-Morrison vector z
+//                  (periodic only)
 //   sum[t*m+j]   = (v, w): chunk summaries F_j = sum v b (zero-carry forward
 //                  value at the chunk end) and Y_j = sum w b (zero-carry
 //                  backward value at the chunk start)
-//   chunk[j]     = (Aend, kappa, Bst, 0): G_in[j+1] = Aend G_in[j] + F_j;
+//   chunk[j]     = (Aend, kappa, Bst, 0): with a_i = -l_i e_i,
+//                  G_in[j+1] = Aend G_in[j] + F_j;
 //                  X[j] = Y_j + kappa G_in[j] + Bst X[j+1]
 template <typename R> struct MatTab {
   const typename V4T<R>::T *pos;

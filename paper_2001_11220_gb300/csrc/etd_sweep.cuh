@@ -188,7 +188,7 @@ __device__ __forceinline__ void pass2(const MatTab<R> &M, int m, int j, const R 
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const typename V4T<R>::T q = M.pos[t * m + j];
-    g = fma(q.x, g, q.y * b[t]);
+    g = fma(q.x, g, b[t]) * q.y;
     x[t] = g;
   }
   R xn = Xr;

@@ -57,21 +57,25 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
     u[0] = g;
     u[p - 1] = bl;
   }
-  // LU without pivoting (Section 7): pivot_i = d_i - l_i u_{i-1} / pivot_{i-1}
-  std::vector<double> a(p), e(p), al(p), z(p, 0.0);
-  double piv = di[0];
+  // LU without pivoting, in the operation order of the Thomas variant of
+  // Section 7: alpha_0 = u_0/d_0, den_i = d_i - alpha_{i-1} l_i,
+  // alpha_i = u_i / den_i.  The kernels run beta_i = (b_i - l_i beta_{i-1}) / den_i
+  // as (b_i + nl_i beta_{i-1}) * e_i with nl = -l and e = 1/den.
+  std::vector<double> a(p), e(p), al(p), nl(p), z(p, 0.0);
+  double den = di[0];
   for (int i = 0; i < p; ++i) {
-    if (i > 0) piv = di[i] - lo[i] * up[i - 1] / piv;
-    e[i] = 1.0 / piv;
+    if (i > 0) den = di[i] - al[i - 1] * lo[i];
+    e[i] = 1.0 / den;
+    al[i] = up[i] / den;
+    nl[i] = -lo[i];
     a[i] = -lo[i] * e[i];
-    al[i] = up[i] * e[i];
   }
   T.sm_c = 0.0;
   T.sm_inv = 0.0;
   if (bc == BC_PERIODIC) {
     double gg = 0.0;
     for (int i = 0; i < p; ++i) {
-      gg = a[i] * gg + e[i] * u[i];
+      gg = (u[i] + nl[i] * gg) * e[i];
       z[i] = gg;
     }
     for (int i = p - 2; i >= 0; --i) z[i] -= al[i] * z[i + 1];
@@ -86,7 +90,7 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
   T.pos.assign((size_t)4 * L * m, 0.0);
   T.sum.assign((size_t)2 * L * m, 0.0);
   T.chunk.assign((size_t)4 * m, 0.0);
-  std::vector<double> ca(L), ce(L), cal(L), A(L), V(L), Wt(L), Sx(L);
+  std::vector<double> ca(L), ce(L), cal(L), cnl(L), A(L), V(L), Wt(L), Sx(L);
   for (int j = 0; j < m; ++j) {
     const int tl = std::min(L, p - j * L) - 1;  // last real position of the chunk
     for (int t = 0; t < L; ++t) {
@@ -95,8 +99,9 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
       ca[t] = real ? a[i] : 0.0;
       ce[t] = real ? e[i] : 1.0;
       cal[t] = real ? al[i] : 0.0;
+      cnl[t] = real ? nl[i] : 0.0;
       const size_t q = (size_t)t * m + j;
-      T.pos[4 * q + 0] = ca[t];
+      T.pos[4 * q + 0] = cnl[t];
       T.pos[4 * q + 1] = ce[t];
       T.pos[4 * q + 2] = cal[t];
       T.pos[4 * q + 3] = real ? z[i] : 0.0;

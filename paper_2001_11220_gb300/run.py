@@ -1,0 +1,57 @@
+"""Run a named synthetic workload for a number of steps on cuda:0 (used for
+profiling captures).
+
+    python -m paper_2001_11220_gb300.run --workload mms3d --p 256 --precision fp32 --steps 4
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def workload(name: str, p: int):
+    from paper_2001_11220_gb300 import workloads as W
+    if name == "mms3d":
+        return W.mms_3d(p)
+    if name == "brusselator2d":
+        return W.brusselator_2d(p)
+    if name == "schnakenberg2d":
+        return W.schnakenberg_2d(p)
+    if name == "grayscott3d":
+        return W.gray_scott_3d(p)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="mms3d")
+    ap.add_argument("--p", type=int, default=256)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--steps", type=int, default=4)
+    args = ap.parse_args()
+    import torch
+
+    from paper_2001_11220_gb300 import workloads as W
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    w = workload(args.workload, args.p)
+    ctx = EtdRdpIf.from_workload(w, args.precision)          # default stream: direct launches
+    U = torch.tensor(W.initial_state(w), device="cuda", dtype=ctx.dtype)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for n in range(args.steps):
+        ctx.step(U, n * w.k)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    print(f"{w.name} {args.precision}: {args.steps} steps in {dt * 1e3:.2f} ms, info {ctx.info()}, "
+          f"finite={bool(torch.isfinite(U).all())}")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
