@@ -91,6 +91,9 @@ typedef struct {
 
 typedef struct etd_ctx etd_ctx;
 
+/* Bytes of the static device scratch array behind etd_step_noalloc. */
+#define ETD_NOALLOC_BYTES (64u * 1024u * 1024u)
+
 /* Static facts about a context (for measurement and tuning). */
 typedef struct {
   int32_t dim, nspecies, precision;
@@ -168,6 +171,25 @@ etd_status etd_set_stream(etd_ctx *ctx, void *stream);
 etd_status etd_profile(etd_ctx *ctx, int32_t enable);
 etd_status etd_profile_read(etd_ctx *ctx, double *ms, int64_t *launches);
 etd_status etd_get_info(const etd_ctx *ctx, etd_info *info);
+
+/* One step without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- plugins whose host
+ * application owns every device allocation through its own pool, and
+ * real-time loops that must not touch the allocator after start-up.  Same arguments as etd_create plus the
+ * state: U (device, layout above) holds U_n at t_n on entry and U_{n+1} on
+ * return.  Scratch (the three carried fields and the line tables) lives in
+ * one static __device__ array of ETD_NOALLOC_BYTES (64 MiB) that every GPU
+ * loading the library keeps until exit; problems with 3 s N elements (plus
+ * tables) beyond it are rejected with ETD_ERR_INVALID_ARG before any device
+ * work.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Each call recomputes the line tables on the
+ * host, copies them into the array on `stream` and synchronises that stream
+ * once before launching the sweeps.  All calls share the one array and keep
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race. */
+etd_status etd_step_noalloc(const etd_grid *grid, const double *D, const etd_reaction *reaction, double k,
+                            int32_t precision, void *U, double t_n, void *stream);
 
 /* Description of the last failure on ctx (or of the last failed etd_create /
  * etd_batch_create when ctx is NULL).  Never NULL. */

@@ -20,7 +20,7 @@ ETD_FP64, ETD_FP32 = 0, 1
 # every symbol include/etdrdpif.h declares
 EXPORTS = ["etd_create", "etd_step", "etd_run", "etd_run_host", "etd_step_adjoint", "etd_grad",
            "etd_batch_create", "etd_batch_run", "etd_autotune", "etd_set_stream", "etd_profile",
-           "etd_profile_read", "etd_get_info",
+           "etd_profile_read", "etd_get_info", "etd_step_noalloc",
            "etd_last_error", "etd_destroy"]
 
 
@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
         "etd_profile": ([vp, i32], i32),
         "etd_profile_read": ([vp, dptr, ctypes.POINTER(ctypes.c_int64)], i32),
         "etd_get_info": ([vp, ctypes.POINTER(etd_info)], i32),
+        "etd_step_noalloc": ([ctypes.POINTER(etd_grid), dptr, ctypes.POINTER(etd_reaction), dbl, i32, vp, dbl, vp], i32),
         "etd_last_error": ([vp], ctypes.c_char_p),
         "etd_destroy": ([vp], None),
     }
