@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -251,6 +252,11 @@ def main():
 
     # ---- main measurement: FP32 (or --precision) with per-sweep events
     ctx, U = make(args.precision)
+    if not args.no_autotune:
+        with torch.cuda.stream(stream):
+            Wk = U.clone()
+        ctx.autotune(Wk)                      # tile shapes timed per axis on a scratch state
+        del Wk
     info = ctx.info()
     with ClockSampler(local) as clk:
         ms, per = timed(ctx, U, K, profile=True)
@@ -283,6 +289,11 @@ def main():
     extra = {}
     if args.precision == "fp32":
         ctx64, U64 = make("fp64")
+        if not args.no_autotune:
+            with torch.cuda.stream(stream):
+                Wk = U64.clone()
+            ctx64.autotune(Wk)
+            del Wk
         K64 = max(3, K // 5)
         ms64, _ = timed(ctx64, U64, K64, profile=False)
         v64 = units_per_step * K64 / (ms64 / 1e3)
@@ -325,7 +336,8 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": dict(workload_desc(w, args.precision), parallelism="replicas" if world > 1 else "single",
-                               chunk=info["chunk"][:3], lines_per_block=info["lines_per_block"][:3]),
+                               chunk=info["chunk"][:3], lines_per_block=info["lines_per_block"][:3],
+                               staged=info["staged"][:3], autotuned=not args.no_autotune),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes},

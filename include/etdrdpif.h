@@ -104,7 +104,8 @@ typedef struct {
                                     read or written per species per point) */
   int32_t launches_per_step;     /* kernels one etd_step enqueues */
   int32_t chunk[3];              /* chunk length per axis (elements per thread) */
-  int32_t lines_per_block[3];
+  int32_t lines_per_block[3];    /* lines per tile / block per axis */
+  int32_t staged[3];             /* 1: persistent shared-memory-staged kernel, 0: register kernel */
 } etd_info;
 
 /* Create a context for one problem.  Validates every argument

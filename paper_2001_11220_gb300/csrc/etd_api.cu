@@ -83,8 +83,56 @@ etd_status validate_problem(const etd_grid *grid, const double *D, const etd_rea
 
 static int pick_pitch(int m) { return (m % 2 == 0) ? m + 1 : m; }
 
-// lines-per-block and chunk count for one axis and chunk length L
-bool plan_axis(Instance &I, int a, int L, int max_threads) {
+static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+static int pow2_floor(long long v) {
+  int p = 1;
+  while ((long long)p * 2 <= v) p *= 2;
+  return p;
+}
+
+// shared-memory plan of the staged kernel for nlb lines per tile and nbuf buffers
+static StagePlan stage_plan(const Instance &I, const AxisPlan &P, int nlb, int nbuf) {
+  StagePlan sp{};
+  const bool contig = P.kind == SWEEP_FIRST;
+  const int S = I.S, rb = I.real_bytes;
+  const long long n = P.nlines > 0 ? I.N / P.nlines : 1;
+  const int nin = contig ? S : 3 * S;
+  const int nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
+  const int pitch = pick_pitch(P.m);
+  const long long mL = (long long)P.m * P.L;  // positions per line incl. zero padding
+  long long te = contig ? (long long)nlb * (mL + 1) : mL * nlb;
+  te = (te + 3) & ~3LL;
+  sp.staged = 1;
+  sp.tile_elems = (int)te;
+  sp.nin = nin;
+  sp.nbuf = nbuf;
+  const int VW = 16 / rb;
+  sp.vec = (!contig && P.st % VW == 0 && nlb % VW == 0) ? 1 : 0;
+  sp.off_buf = 0;
+  size_t off = align16((size_t)nbuf * nin * te * rb);
+  sp.off_f0 = (unsigned)off;
+  if (P.kind == SWEEP_FIRST) off = align16(off + (size_t)S * te * rb);
+  sp.off_out = (unsigned)off;
+  if (contig) off = align16(off + (size_t)3 * S * te * rb);
+  sp.off_sum = (unsigned)off;
+  off = align16(off + (size_t)2 * nq * nlb * pitch * rb);
+  sp.off_sig = (unsigned)off;
+  off += (size_t)nq * nlb * sizeof(double);
+  sp.bytes = (unsigned)off;
+  if (contig) sp.ntiles = (int)((P.nlines + nlb - 1) / nlb);
+  else sp.ntiles = (int)(((P.st + nlb - 1) / nlb) * (I.N / (P.st * n)));
+  return sp;
+}
+
+static const size_t kStageSmemCap = 220 * 1024;      // one block per SM
+static const size_t kStageSmemHalf = 110 * 1024;     // two blocks per SM
+
+// lines-per-block and chunk count for one axis and chunk length L.  Lines
+// short enough to stage go to the persistent double-buffered kernel; longer
+// ones to the register kernel.  nlb_force > 0 asks for the staged kernel with
+// that many lines per tile, reg_force for the register kernel (autotuning).
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force) {
   AxisPlan &P = I.plan[a];
   const long long n = I.n[a];
   P.L = L;
@@ -95,6 +143,34 @@ bool plan_axis(Instance &I, int a, int L, int max_threads) {
   for (int b = 0; b < a; ++b) st *= I.n[b];
   P.st = st;
   P.nlines = I.N / n;
+  P.pitch = pick_pitch(P.m);
+  // staged plan: largest power-of-two lines per tile that fits with double buffering
+  P.sp = StagePlan{};
+  {
+    const int cap = (a == 0) ? 64 : (I.real_bytes == 4 ? 32 : 16);
+    const long long avail = (a == 0) ? P.nlines : st;
+    int top = pow2_floor(std::min<long long>(std::min(cap, max_threads / P.m), std::max<long long>(1, avail)));
+    if (top < avail && top * 2 <= std::min(cap, max_threads / P.m)) top *= 2;
+    // prefer two resident blocks per SM (their exchange phases overlap), then one
+    int chosen = 0;
+    if (nlb_force > 0) {
+      if (nlb_force * P.m > max_threads || stage_plan(I, P, nlb_force, 2).bytes > kStageSmemCap) return false;
+      chosen = nlb_force;
+    }
+    for (int nlb = top; nlb >= 8 && !chosen && !reg_force; nlb /= 2)
+      if (stage_plan(I, P, nlb, 2).bytes <= kStageSmemHalf) chosen = nlb;
+    for (int nlb = top; nlb >= 4 && !chosen && !reg_force; nlb /= 2)
+      if (stage_plan(I, P, nlb, 2).bytes <= kStageSmemCap) chosen = nlb;
+    if (chosen) {
+      P.sp = stage_plan(I, P, chosen, 2);
+      P.nlb = chosen;
+      P.nthreads = chosen * P.m;
+      P.nlo_blocks = (a == 0) ? 1 : (int)((st + chosen - 1) / chosen);
+      P.nblocks = P.sp.ntiles;
+      P.smem = P.sp.bytes;
+      return true;
+    }
+  }
   if (a == 0) {
     int nlb = std::max(1, 256 / P.m);
     nlb = (int)std::min<long long>(nlb, P.nlines);
@@ -111,17 +187,19 @@ bool plan_axis(Instance &I, int a, int L, int max_threads) {
     const long long nhi = I.N / (st * n);
     P.nblocks = (int)(P.nlo_blocks * nhi);
   }
-  P.pitch = pick_pitch(P.m);
   P.nthreads = P.nlb * P.m;
   P.smem = sweep_smem_bytes(P.kind, I.S, P.nlb, P.pitch, I.real_bytes);
   return P.smem <= 200 * 1024;
 }
 
+bool plan_axis(Instance &I, int a, int L, int max_threads) { return plan_axis_ex(I, a, L, max_threads, 0, false); }
+
 int default_chunk(const Instance &I, int a) {
-  // contiguous axis: short chunks (lanes walk the line); strided axes: longer
-  // chunks so a block covers 32 neighbouring lines
-  if (I.real_bytes == 4) return a == 0 ? 8 : 16;
-  return a == 0 ? 4 : 8;
+  // staged kernels: 16 positions per thread (FP32) keeps the per-line chain of
+  // chunk carries short; the register kernel for long x lines uses 8
+  const long long n = I.n[a];
+  if (I.real_bytes == 4) return (a == 0 && n > 1024) ? 8 : 16;
+  return (a == 0 && n > 1024) ? 4 : 8;
 }
 
 // ------------------------------------------------------------ tables
@@ -141,10 +219,10 @@ static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::
 
 // factorise every (axis, species, gamma) line matrix of one instance, forward
 // (and transposed for the adjoint), and upload in the instance's precision
-etd_status build_instance_tables(etd_ctx *ctx, Instance &I) {
+etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
   cudaError_t err = cudaSuccess;
   static const double gammas[3] = {1.0, 3.0, 4.0};
-  for (int a = 0; a < I.dim; ++a) {
+  {
     const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
     for (int s = 0; s < I.S; ++s)
       for (int g = 0; g < 3; ++g)
@@ -158,6 +236,15 @@ etd_status build_instance_tables(etd_ctx *ctx, Instance &I) {
             upload_tab<float>(I.arena, T, I.tab32[tr][a][s][g], I.owned, err);
           if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
         }
+  }
+  return ETD_OK;
+}
+
+etd_status build_instance_tables(etd_ctx *ctx, Instance &I) {
+  cudaError_t err = cudaSuccess;
+  for (int a = 0; a < I.dim; ++a) {
+    etd_status st = build_axis_tables(ctx, I, a);
+    if (st != ETD_OK) return st;
   }
   // manufactured-source coordinate tables
   I.has_source = (I.rkind == ETD_REACTION_ENZYME && I.rp[0] != 0.0);
@@ -211,6 +298,8 @@ void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
   A.nx = (int)I.n[0];
   A.ny = (int)I.n[1];
   A.src_lf = I.src_lf;
+  A.axis = a;
+  A.sp = P.sp;
 }
 template void fill_args<float>(const Instance &, int, int, SweepArgs<float> &);
 template void fill_args<double>(const Instance &, int, int, SweepArgs<double> &);
@@ -436,6 +525,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   for (int a = 0; a < I.dim; ++a) {
     info->chunk[a] = I.plan[a].L;
     info->lines_per_block[a] = I.plan[a].nlb;
+    info->staged[a] = I.plan[a].sp.staged;
   }
   return ETD_OK;
 }

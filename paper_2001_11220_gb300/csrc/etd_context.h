@@ -47,7 +47,8 @@ struct AxisPlan {
   int nblocks = 1;
   long long st = 1;    // element stride of the axis
   long long nlines = 1;
-  size_t smem = 0;
+  size_t smem = 0;     // register kernel: shared memory bytes
+  StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel
 };
 
 // one problem: grid, coefficients, tables, plans and scratch

@@ -28,14 +28,14 @@ template <> struct V2T<double> { using T = double2; };
 
 // Tables of one line matrix M = I + (k/gamma) D_s B_p (or its modified
 // tridiagonal part M' for periodic lines), chunked into m chunks of L
-// positions, stored position-major: entry (t, j) at index t*m + j, i.e. the
-// t-th position of chunk j.  Positions past the end of the line are identity
+// positions, stored chunk-major: entry (t, j) at index j*L + t, i.e. the
+// t-th position of chunk j (a thread's L entries are contiguous).  Positions past the end of the line are identity
 // rows (nl = 0, e = 1, alpha = 0, z = 0, v = w = 0).
-//   pos[t*m+j]   = (nl, e, alpha, z): forward g_i = (b_i + nl_i g_{i-1}) e_i
+//   pos[j*L+t]   = (nl, e, alpha, z): forward g_i = (b_i + nl_i g_{i-1}) e_i
 //                  (nl = minus the sub-diagonal, e = 1 / pivot), backward
 //                  x_i = g_i - alpha_i x_{i+1}, Sherman-Morrison vector z
 //                  (periodic only)
-//   sum[t*m+j]   = (v, w): chunk summaries F_j = sum v b (zero-carry forward
+//   sum[j*L+t]   = (v, w): chunk summaries F_j = sum v b (zero-carry forward
 //                  value at the chunk end) and Y_j = sum w b (zero-carry
 //                  backward value at the chunk start)
 //   chunk[j]     = (Aend, kappa, Bst, 0): with a_i = -l_i e_i,
@@ -47,6 +47,18 @@ template <typename R> struct MatTab {
   const typename V4T<R>::T *chunk;
   double sm_c;    // v_{p-1} of the Sherman-Morrison rank-one term (periodic)
   double sm_inv;  // 1 / (1 + v.z)                                  (periodic)
+};
+
+// Shared-memory staging plan of the persistent sweep kernels (byte offsets
+// into dynamic shared memory; every region 16-byte aligned).
+struct StagePlan {
+  int staged;       // 1: persistent shared-memory-staged kernel, 0: register kernel
+  int tile_elems;   // elements of one staged field tile
+  int nin;          // staged input fields per tile
+  int nbuf;         // 1 or 2 tile buffers (2 = next tile prefetched during compute)
+  int vec;          // strided tiles: 1 = 16-byte async copies per row segment
+  int ntiles;       // tiles of this instance
+  unsigned off_buf, off_f0, off_out, off_sum, off_sig, bytes;
 };
 
 // Everything one sweep launch needs for one problem instance.
@@ -71,6 +83,8 @@ template <typename R> struct SweepArgs {
   const R *phi[3]; // sin(pi x_a / L_a) per axis (manufactured source), NULL otherwise
   int nx, ny;      // grid extents of axes 0 and 1 (point -> coordinates)
   double src_lf;   // Sum_a (pi / L_a)^2
+  int axis;        // swept axis
+  StagePlan sp;    // staged-kernel plan
 };
 
 // host-side launchers (one translation unit per element type)

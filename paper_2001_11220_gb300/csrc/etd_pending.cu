@@ -26,6 +26,5 @@ etd_status etd_batch_run(etd_ctx *ctx, void *const *, double, int64_t) {
   return fail(ctx, ETD_ERR_UNSUPPORTED, "etd_batch_run not implemented");
 }
 
-etd_status etd_autotune(etd_ctx *ctx, void *) { return fail(ctx, ETD_ERR_UNSUPPORTED, "etd_autotune not implemented"); }
 
 }  // extern "C"

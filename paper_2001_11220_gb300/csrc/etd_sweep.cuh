@@ -154,7 +154,7 @@ __device__ __forceinline__ void pass1(const MatTab<R> &M, int m, int j, const R 
   R f = R(0), y = R(0);
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const typename V2T<R>::T vw = M.sum[t * m + j];
+    const typename V2T<R>::T vw = M.sum[j * L + t];
     f = fma(vw.x, b[t], f);
     y = fma(vw.y, b[t], y);
   }
@@ -169,7 +169,7 @@ __device__ __forceinline__ void pass1x2(const MatTab<R> &M, int m, int j, const 
   R f0 = R(0), y0 = R(0), f1 = R(0), y1 = R(0);
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const typename V2T<R>::T vw = M.sum[t * m + j];
+    const typename V2T<R>::T vw = M.sum[j * L + t];
     f0 = fma(vw.x, b0[t], f0);
     y0 = fma(vw.y, b0[t], y0);
     f1 = fma(vw.x, b1[t], f1);
@@ -187,14 +187,14 @@ __device__ __forceinline__ void pass2(const MatTab<R> &M, int m, int j, const R 
   R g = Gin;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const typename V4T<R>::T q = M.pos[t * m + j];
+    const typename V4T<R>::T q = M.pos[j * L + t];
     g = fma(q.x, g, b[t]) * q.y;
     x[t] = g;
   }
   R xn = Xr;
 #pragma unroll
   for (int t = L - 1; t >= 0; --t) {
-    const typename V4T<R>::T q = M.pos[t * m + j];
+    const typename V4T<R>::T q = M.pos[j * L + t];
     xn = fma(-q.z, xn, x[t]);
     x[t] = fma(-sig, q.w, xn);
   }

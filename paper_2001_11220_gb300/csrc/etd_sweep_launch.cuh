@@ -2,10 +2,13 @@
 // type; included once per element type by etd_sweep_f32.cu / etd_sweep_f64.cu.
 #pragma once
 
+#include <algorithm>
+#include <cstdio>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 
-#include "etd_sweep.cuh"
+#include "etd_sweep_smem.cuh"
 
 namespace etd {
 
@@ -22,9 +25,50 @@ inline cudaError_t ensure_smem(const void *fn, size_t smem) {
   return e;
 }
 
+// resident blocks per SM of a kernel configuration times the SM count (cached)
+inline cudaError_t persistent_grid(const void *fn, int nthreads, size_t smem, int ntiles, int &grid) {
+  static std::mutex mu;
+  static std::unordered_map<std::string, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  char key[96];
+  snprintf(key, sizeof(key), "%p/%d/%zu/%d", fn, nthreads, smem, dev);
+  int per_sm = 0, nsm = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      grid = std::min(ntiles, it->second);
+      return cudaSuccess;
+    }
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nthreads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int resident = std::max(1, per_sm) * nsm;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = resident;
+  }
+  grid = std::min(ntiles, resident);
+  return cudaSuccess;
+}
+
 template <typename R, int S, int L, int KIND>
 cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStream_t s) {
   constexpr bool CONTIG = (KIND == SWEEP_FIRST);
+  if (a.sp.staged) {
+    auto fn = sweep_staged_kernel<R, S, L, CONTIG, KIND>;
+    cudaError_t e = ensure_smem((const void *)fn, a.sp.bytes);
+    if (e != cudaSuccess) return e;
+    int grid = 0;
+    e = persistent_grid((const void *)fn, nthreads, a.sp.bytes, a.sp.ntiles, grid);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, nthreads, a.sp.bytes, s>>>(a);
+    return cudaGetLastError();
+  }
   auto fn = sweep_kernel<R, S, L, CONTIG, KIND>;
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;

@@ -100,7 +100,7 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
       ce[t] = real ? e[i] : 1.0;
       cal[t] = real ? al[i] : 0.0;
       cnl[t] = real ? nl[i] : 0.0;
-      const size_t q = (size_t)t * m + j;
+      const size_t q = (size_t)j * L + t;
       T.pos[4 * q + 0] = cnl[t];
       T.pos[4 * q + 1] = ce[t];
       T.pos[4 * q + 2] = cal[t];
@@ -123,7 +123,7 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
     for (int t = 0; t <= tl; ++t) {
       kap += Wt[t] * A[t];
       bst *= -cal[t];
-      const size_t q = (size_t)t * m + j;
+      const size_t q = (size_t)j * L + t;
       T.sum[2 * q + 0] = ce[t] * V[t];
       T.sum[2 * q + 1] = ce[t] * Sx[t];
     }

@@ -1,0 +1,100 @@
+// etd_tune.cu -- tile-shape autotuner: for every axis, time each candidate
+// (chunk length L, lines per tile, staged or register kernel) on the
+// context's stream with CUDA events and keep the fastest.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../include/etdrdpif.h"
+#include "etd_context.h"
+
+namespace etd {
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force);
+etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
+}  // namespace etd
+
+using namespace etd;
+
+namespace {
+
+struct Cand {
+  int L, nlb;
+  bool reg;
+};
+
+// device time of axis a's sweep, averaged over `reps` steps
+etd_status time_axis(etd_ctx *ctx, Instance &I, int a, void *U, int reps, double &ms) {
+  const bool was = ctx->profiling;
+  ctx->profiling = false;
+  for (int r = 0; r < 2; ++r) {
+    cudaError_t e = forward_step(I, U, 0.0, ctx->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune warm-up");
+  }
+  ctx->profiling = true;
+  double acc[3] = {0, 0, 0};
+  int64_t cnt[3] = {0, 0, 0};
+  etd_profile_read(ctx, acc, cnt);  // drop stale records
+  acc[0] = acc[1] = acc[2] = 0;
+  cnt[0] = cnt[1] = cnt[2] = 0;
+  for (int r = 0; r < reps; ++r) {
+    cudaError_t e = forward_step(I, U, 0.0, ctx->stream, ctx);
+    if (e != cudaSuccess) {
+      ctx->profiling = was;
+      return cuda_fail(ctx, e, "autotune step");
+    }
+  }
+  etd_status st = etd_profile_read(ctx, acc, cnt);
+  ctx->profiling = was;
+  if (st != ETD_OK) return st;
+  const int kind = I.plan[a].kind;
+  ms = cnt[kind] ? acc[kind] / cnt[kind] : 1e30;
+  return ETD_OK;
+}
+
+}  // namespace
+
+extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_autotune on a batched context");
+  if (!U_work) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work is NULL");
+  Instance &I = ctx->inst[0];
+  ctx->graphs.clear();
+  const int Ls32[] = {8, 16}, Ls64[] = {4, 8};
+  const int nlbs[] = {4, 8, 16, 32, 64};
+  for (int a = 0; a < I.dim; ++a) {
+    std::vector<Cand> cands;
+    for (int li = 0; li < 2; ++li) {
+      const int L = I.real_bytes == 4 ? Ls32[li] : Ls64[li];
+      for (int nlb : nlbs) cands.push_back({L, nlb, false});
+      cands.push_back({L, 0, true});
+    }
+    const AxisPlan keep = I.plan[a];
+    double best = 1e30;
+    Cand pick{keep.L, keep.sp.staged ? keep.nlb : 0, !keep.sp.staged};
+    for (const Cand &c : cands) {
+      if (!plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.reg ? 0 : c.nlb, c.reg)) continue;
+      if (c.reg && I.plan[a].sp.staged) continue;
+      etd_status st = build_axis_tables(ctx, I, a);
+      if (st != ETD_OK) return st;
+      double ms = 0;
+      st = time_axis(ctx, I, a, U_work, 5, ms);
+      if (st != ETD_OK) return st;
+      if (std::getenv("ETD_TUNE_VERBOSE"))
+        fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d %s -> %.4f ms\n", a, c.L, I.plan[a].nlb,
+                I.plan[a].sp.staged ? "staged" : "register", ms);
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    if (!plan_axis_ex(I, a, pick.L, ETD_MAX_BLOCK_THREADS, pick.reg ? 0 : pick.nlb, pick.reg))
+      return fail(ctx, ETD_ERR_CUDA, "autotune: best candidate of axis %d no longer plans", a);
+    etd_status st = build_axis_tables(ctx, I, a);
+    if (st != ETD_OK) return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune synchronize");
+  return ETD_OK;
+}

@@ -203,3 +203,21 @@ def test_bad_state_rejected():
     with pytest.raises(ValueError):
         ctx.step(torch.zeros((2, 16, 16), device="cuda", dtype=torch.float32), 0.0)
     ctx.close()
+
+
+def test_autotuned_tiles_keep_parity():
+    """Every tile shape the autotuner may pick computes the same step: after
+    tuning, one FP64 step still matches the oracle."""
+    w = case("gs3d_tune", (40, 36, 33), (W.PERIODIC, W.NEUMANN, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+             (0.04, 0.06), k=0.5)
+    U0 = W.initial_state(w)
+    EtdRdpIf = _api()
+    ctx = EtdRdpIf.from_workload(w, "fp64")
+    work = torch.tensor(U0, device="cuda")
+    ctx.autotune(work)
+    U = torch.tensor(U0, device="cuda")
+    ctx.step(U, 0.3)
+    torch.cuda.synchronize()
+    err = rel_err(U.cpu().numpy(), oracle_run(w, U0, 1, t0=0.3))
+    ctx.close()
+    assert err <= FP64_TOL, err
