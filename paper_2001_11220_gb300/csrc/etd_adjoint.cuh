@@ -1,0 +1,478 @@
+// etd_adjoint.cuh -- reverse-mode (discrete adjoint) sweeps of one ETD-RDP-IF
+// step and the misfit kernel.
+//
+// The forward step is a composition of line solves x = M^{-1} b with
+// M = I + (k/gamma) D_s B (Section 7) and pointwise operations (Section 6
+// frame).  Its adjoint, axis by axis in reverse order:
+//   x = M^{-1} b         ->  bbar += M^{-T} xbar              (transposed tables)
+//                            Dbar_s -= <M^{-T} xbar, b - x> / D_s
+//                            (since (k/gamma) B x = (b - x) / D_s)
+//   f = F(u)             ->  ubar += J_F(u)^T fbar, pbar += (dF/dp)^T fbar
+//   linear combinations  ->  transposed combinations
+// Each adjoint sweep recomputes the forward solves of its axis from the
+// forward inputs of that sweep (kept by the caller), so every line solve of
+// the step appears twice: forward (for the D-gradient) and transposed.
+//
+// Block layout: one block owns nlb complete lines; thread (l = tid % nlb,
+// j = tid / nlb) owns chunk j of line l for every species in registers; all
+// solves of a phase share one shared-memory exchange (etd_sweep.cuh).
+#pragma once
+
+#include "etd_sweep.cuh"
+
+namespace etd {
+
+// J_F(u)^T yb and (dF/dparams)^T yb at one point (q: manufactured-source
+// factor e^{-t} prod sin(pi x/L) at the point, 0 if the source is off)
+template <typename R, int S>
+__device__ __forceinline__ void reaction_vjp(const SweepArgs<R> &A, const R (&u)[S], const R (&yb)[S], R (&out)[S],
+                                             R (&pg)[8], R q) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[s] = R(0);
+  switch (A.rkind) {
+    case 1: {  // F_i = p0 u_i + p1
+      const R p0 = (R)A.rp[0];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        out[s] = p0 * yb[s];
+        pg[0] = fma(u[s], yb[s], pg[0]);
+        pg[1] += yb[s];
+      }
+      return;
+    }
+    case 2:
+      if constexpr (S == 2) {  // Brusselator
+        const R b = (R)A.rp[1], U = u[0], V = u[1];
+        const R uv2 = R(2) * U * V, uu = U * U;
+        out[0] = (uv2 - (b + R(1))) * yb[0] + (b - uv2) * yb[1];
+        out[1] = uu * (yb[0] - yb[1]);
+        pg[0] += yb[0];
+        pg[1] = fma(U, yb[1] - yb[0], pg[1]);
+      }
+      return;
+    case 3:
+      if constexpr (S == 2) {  // Schnakenberg
+        const R a = (R)A.rp[0], b = (R)A.rp[1], g = (R)A.rp[2], U = u[0], V = u[1];
+        const R uv2 = R(2) * U * V, uu = U * U, uuv = uu * V;
+        out[0] = g * ((uv2 - R(1)) * yb[0] - uv2 * yb[1]);
+        out[1] = g * uu * (yb[0] - yb[1]);
+        pg[0] = fma(g, yb[0], pg[0]);
+        pg[1] = fma(g, yb[1], pg[1]);
+        pg[2] += (a - U + uuv) * yb[0] + (b - uuv) * yb[1];
+      }
+      return;
+    case 4:
+      if constexpr (S == 2) {  // Gray-Scott
+        const R F = (R)A.rp[0], kap = (R)A.rp[1], U = u[0], V = u[1];
+        const R vv = V * V, uv2 = R(2) * U * V;
+        out[0] = (-vv - F) * yb[0] + vv * yb[1];
+        out[1] = -uv2 * yb[0] + (uv2 - (F + kap)) * yb[1];
+        pg[0] += (R(1) - U) * yb[0] - V * yb[1];
+        pg[1] -= V * yb[1];
+      }
+      return;
+    case 5: {  // enzyme kinetics + manufactured source
+      const R d = R(1) + u[0];
+      out[0] = -yb[0] / (d * d);
+      if (q != R(0)) {
+        const R lf = (R)A.src_lf;
+        pg[0] += (((R)A.rp[1] * lf - R(1)) * q + q / (R(1) + q)) * yb[0];
+        pg[1] += (R)A.rp[0] * lf * q * yb[0];
+      }
+      return;
+    }
+    default:
+      return;
+  }
+}
+
+// manufactured-source factor q at grid point pidx
+template <typename R>
+__device__ __forceinline__ R mms_q(const SweepArgs<R> &A, long long pidx) {
+  const long long x = pidx % A.nx;
+  const long long r = pidx / A.nx;
+  const long long y = r % A.ny;
+  const long long z = r / A.ny;
+  R q = (R)A.exp_mt * A.phi[0][x] * A.phi[1][y];
+  if (A.phi[2]) q *= A.phi[2][z];
+  return q;
+}
+
+// chain the chunk summaries of solves q0 .. q0+nq-1; mat(q) gives the solve's tables
+template <typename R, typename GetMat>
+__device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
+                                            GetMat mat) {
+  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    const MatTab<R> &M = mat(q);
+    R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    R G = R(0);
+    for (int j = 0; j < m; ++j) {
+      const R f = F[j];
+      F[j] = G;
+      G = fma(M.chunk[j].x, G, f);
+    }
+    R X = R(0);
+    for (int j = m - 1; j >= 0; --j) {
+      const typename V4T<R>::T c = M.chunk[j];
+      const R y = fma(c.y, F[j], Y[j]);
+      Y[j] = X;
+      X = fma(c.z, X, y);
+    }
+    sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X + M.sm_c * (double)G) * M.sm_inv : 0.0;
+  }
+}
+
+// block-wide sum of nv per-thread values added atomically to acc[0..nv)
+template <int NV>
+__device__ __forceinline__ void block_accumulate(double (&v)[NV], double *acc, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[warp * NV + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * NV + threadIdx.x];
+    if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+  }
+}
+
+template <typename R, int S, int L, bool CONTIG, int KIND>
+__global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_constant__ SweepArgs<R> A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NQ = (KIND == ADJ_LAST) ? 6 * S : 10 * S;
+  const int m = A.m, nlb = A.nlb, pitch = A.pitch, n = A.n;
+  const int tid = threadIdx.x;
+  const int l = tid % nlb, j = tid / nlb;
+  long long base;
+  bool line_ok;
+  if constexpr (CONTIG) {
+    const long long line = (long long)blockIdx.x * nlb + l;
+    line_ok = line < A.nlines;
+    base = line * n;
+  } else {
+    const long long lo = (long long)(blockIdx.x % A.nlo_blocks) * nlb + l;
+    const long long hi = blockIdx.x / A.nlo_blocks;
+    line_ok = lo < A.st;
+    base = lo + hi * A.st * n;
+  }
+  const long long st = CONTIG ? 1 : A.st;
+  const int i0 = j * L;
+  const int cnt = line_ok ? max(0, min(L, n - i0)) : 0;
+  const long long off0 = base + (long long)i0 * st;
+  const long long N = A.N;
+  const R k = (R)A.k;
+
+  R *sF = reinterpret_cast<R *>(smem);
+  R *sY = sF + (size_t)NQ * nlb * pitch;
+  double *sSig = reinterpret_cast<double *>(smem + ((2 * (size_t)NQ * nlb * pitch * sizeof(R) + 15) & ~(size_t)15));
+  double *red = sSig + (size_t)NQ * nlb;
+  const size_t myidx = (size_t)l * pitch + j;
+  auto put = [&](int q, R F, R Y) {
+    sF[(size_t)q * nlb * pitch + myidx] = F;
+    sY[(size_t)q * nlb * pitch + myidx] = Y;
+  };
+  auto carries = [&](int q, R &G, R &X, R &sg) {
+    G = sF[(size_t)q * nlb * pitch + myidx];
+    X = sY[(size_t)q * nlb * pitch + myidx];
+    sg = (R)sSig[(size_t)q * nlb + l];
+  };
+  auto qsrc = [&](int t) -> R {
+    return (A.phi[0] != nullptr && t < cnt) ? mms_q(A, off0 + (long long)t * st) : R(0);
+  };
+  R dD[S];
+  R pg[8];
+#pragma unroll
+  for (int s = 0; s < S; ++s) dD[s] = R(0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) pg[i] = R(0);
+  // -<lam, b - x>: contribution of one solve to D_s (times 1/D_s at the end)
+  auto dterm = [&](int s, const R (&lam)[L], const R (&b)[L], const R (&x)[L], R scale) {
+    R acc = R(0);
+#pragma unroll
+    for (int t = 0; t < L; ++t) acc = fma(lam[t], b[t] - x[t], acc);
+    dD[s] = fma(-scale, acc, dD[s]);
+  };
+
+  if constexpr (KIND == ADJ_LAST) {
+    // forward inputs of the last sweep: c_U, c_f, w (fin); adjoint input: Ubar_{n+1} (in[0])
+    // solves: phase A  q = 3s: P w ; 3s+1: T^T Ub ; 3s+2: S^T Ub
+    //         phase B  q = 3S+3s: T f1 ; +1: S f2 ; +2: P^T Ustar_bar
+    auto mat = [&](int q) -> const MatTab<R> & {
+      const int qq = q < 3 * S ? q : q - 3 * S;
+      const int s = qq / 3, r = qq - 3 * (qq / 3);
+      if (q < 3 * S) return r == 0 ? A.mat[s][0] : A.matT[s][r];
+      return r == 2 ? A.matT[s][0] : A.mat[s][r + 1];
+    };
+    R w[S][L], Us[S][L], a1[S][L], a2[S][L];
+    {
+      R ub[S][L];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        load_chunk<R, L, CONTIG>(w[s], A.fin[2] + s * N, off0, st, cnt);
+        load_chunk<R, L, CONTIG>(ub[s], A.in[0] + s * N, off0, st, cnt);
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        R F0, Y0, F1, Y1;
+        pass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
+        put(3 * s, F0, Y0);
+        pass1<R, L>(A.matT[s][1], m, j, ub[s], F1, Y1);
+        put(3 * s + 1, F1, Y1);
+        pass1<R, L>(A.matT[s][2], m, j, ub[s], F1, Y1);
+        put(3 * s + 2, F1, Y1);
+      }
+      __syncthreads();
+      scan_solves<R>(A, sF, sY, sSig, 0, 3 * S, mat);
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        R G, X, sg;
+        carries(3 * s, G, X, sg);
+        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, Us[s]);
+        carries(3 * s + 1, G, X, sg);
+        pass2<R, L>(A.matT[s][1], m, j, ub[s], G, X, sg, a1[s]);
+        carries(3 * s + 2, G, X, sg);
+        pass2<R, L>(A.matT[s][2], m, j, ub[s], G, X, sg, a2[s]);
+#pragma unroll
+        for (int t = 0; t < L; ++t) a2[s][t] = -a2[s][t];  // f2bar = S^T (-Ubar)
+      }
+    }
+    // pointwise: fstar_bar = k f1bar + k/2 f2bar, Ustar_bar = J^T fstar_bar,
+    // c_U_bar = 9 f1bar + 8 f2bar, c_f_bar = 2k f1bar + 3k/2 f2bar, f1, f2 for the D-gradient
+    R f1[S][L], f2[S][L], usb[S][L];
+    {
+      R cu[S][L], cf[S][L];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        load_chunk<R, L, CONTIG>(cu[s], A.fin[0] + s * N, off0, st, cnt);
+        load_chunk<R, L, CONTIG>(cf[s], A.fin[1] + s * N, off0, st, cnt);
+      }
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        R u[S], f[S], yb[S], ob[S];
+        const R q = qsrc(t);
+        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q)) : R(0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          u[s] = Us[s][t];
+          yb[s] = (t < cnt) ? fma(k, a1[s][t], R(0.5) * k * a2[s][t]) : R(0);
+        }
+        reaction_point<R, S>(A, u, f, src);
+        reaction_vjp<R, S>(A, u, yb, ob, pg, q);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          usb[s][t] = (t < cnt) ? ob[s] : R(0);
+          const R fs = (t < cnt) ? f[s] : R(0);
+          f1[s][t] = fma(R(9), cu[s][t], fma(R(2) * k, cf[s][t], k * fs));
+          f2[s][t] = fma(R(8), cu[s][t], fma(R(1.5) * k, cf[s][t], R(0.5) * k * fs));
+          cu[s][t] = fma(R(9), a1[s][t], R(8) * a2[s][t]);
+          cf[s][t] = fma(R(2) * k, a1[s][t], R(1.5) * k * a2[s][t]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        store_chunk<R, L, CONTIG>(cu[s], A.out[0] + s * N, off0, st, cnt);
+        store_chunk<R, L, CONTIG>(cf[s], A.out[1] + s * N, off0, st, cnt);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R F0, Y0;
+      pass1<R, L>(A.mat[s][1], m, j, f1[s], F0, Y0);
+      put(3 * S + 3 * s, F0, Y0);
+      pass1<R, L>(A.mat[s][2], m, j, f2[s], F0, Y0);
+      put(3 * S + 3 * s + 1, F0, Y0);
+      pass1<R, L>(A.matT[s][0], m, j, usb[s], F0, Y0);
+      put(3 * S + 3 * s + 2, F0, Y0);
+    }
+    __syncthreads();
+    scan_solves<R>(A, sF, sY, sSig, 3 * S, 3 * S, mat);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R x[L], G, X, sg;
+      carries(3 * S + 3 * s, G, X, sg);
+      pass2<R, L>(A.mat[s][1], m, j, f1[s], G, X, sg, x);
+      dterm(s, a1[s], f1[s], x, R(1));
+      carries(3 * S + 3 * s + 1, G, X, sg);
+      pass2<R, L>(A.mat[s][2], m, j, f2[s], G, X, sg, x);
+      dterm(s, a2[s], f2[s], x, R(1));
+      carries(3 * S + 3 * s + 2, G, X, sg);
+      pass2<R, L>(A.matT[s][0], m, j, usb[s], G, X, sg, x);  // wbar
+      dterm(s, x, w[s], Us[s], R(1));
+      store_chunk<R, L, CONTIG>(x, A.out[2] + s * N, off0, st, cnt);
+    }
+  } else {
+    // FIRST / MIDDLE: adjoint inputs cbar_U, cbar_f, wbar (in); forward inputs
+    // (fin): MIDDLE c_U, c_f, w of the previous axis; FIRST U_n (F(U_n) and
+    // w* = U_n + k F(U_n) recomputed here)
+    // solves q = 10s + {0: T^T cUb, 1: S^T cUb, 2: T^T cfb, 3: S^T cfb, 4: P^T wb,
+    //                   5: T xu, 6: S xu, 7: T xf, 8: S xf, 9: P xw}
+    auto mat = [&](int q) -> const MatTab<R> & {
+      const int s = q / 10, r = q - 10 * (q / 10);
+      if (r == 4) return A.matT[s][0];          // P^T
+      if (r == 9) return A.mat[s][0];           // P
+      if (r < 4) return A.matT[s][1 + (r & 1)];  // 0, 2: T^T ; 1, 3: S^T
+      return A.mat[s][1 + ((r - 5) & 1)];       // 5, 7: T ; 6, 8: S
+    };
+    R cb[S][L], fb[S][L], wb[S][L], xu[S][L], xf[S][L];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      load_chunk<R, L, CONTIG>(cb[s], A.in[0] + s * N, off0, st, cnt);
+      load_chunk<R, L, CONTIG>(fb[s], A.in[1] + s * N, off0, st, cnt);
+      load_chunk<R, L, CONTIG>(wb[s], A.in[2] + s * N, off0, st, cnt);
+      load_chunk<R, L, CONTIG>(xu[s], A.fin[0] + s * N, off0, st, cnt);
+    }
+    if constexpr (KIND == ADJ_MIDDLE) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) load_chunk<R, L, CONTIG>(xf[s], A.fin[1] + s * N, off0, st, cnt);
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {  // F(U_n, t_n)
+        R u[S], f[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u[s] = xu[s][t];
+        const R q = qsrc(t);
+        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q)) : R(0);
+        reaction_point<R, S>(A, u, f, src);
+#pragma unroll
+        for (int s = 0; s < S; ++s) xf[s][t] = (t < cnt) ? f[s] : R(0);
+      }
+    }
+    auto xw_at = [&](int s, R (&xw)[L]) {
+      if constexpr (KIND == ADJ_MIDDLE) {
+        load_chunk<R, L, CONTIG>(xw, A.fin[2] + s * N, off0, st, cnt);
+      } else {
+#pragma unroll
+        for (int t = 0; t < L; ++t) xw[t] = fma(k, xf[s][t], xu[s][t]);
+      }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R F0, Y0, F1, Y1, xw[L];
+      pass1x2<R, L>(A.matT[s][1], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
+      put(10 * s + 0, F0, Y0);
+      put(10 * s + 2, F1, Y1);
+      pass1x2<R, L>(A.matT[s][2], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
+      put(10 * s + 1, F0, Y0);
+      put(10 * s + 3, F1, Y1);
+      pass1<R, L>(A.matT[s][0], m, j, wb[s], F0, Y0);
+      put(10 * s + 4, F0, Y0);
+      pass1x2<R, L>(A.mat[s][1], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
+      put(10 * s + 5, F0, Y0);
+      put(10 * s + 7, F1, Y1);
+      pass1x2<R, L>(A.mat[s][2], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
+      put(10 * s + 6, F0, Y0);
+      put(10 * s + 8, F1, Y1);
+      xw_at(s, xw);
+      pass1<R, L>(A.mat[s][0], m, j, xw, F0, Y0);
+      put(10 * s + 9, F0, Y0);
+    }
+    __syncthreads();
+    scan_solves<R>(A, sF, sY, sSig, 0, NQ, mat);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R aT[L], aS[L], x[L], G, X, sg;
+      // cbar_U: lambda_T = 9 T^T cb, lambda_S = -8 S^T cb
+      carries(10 * s + 0, G, X, sg);
+      pass2<R, L>(A.matT[s][1], m, j, cb[s], G, X, sg, aT);
+      carries(10 * s + 5, G, X, sg);
+      pass2<R, L>(A.mat[s][1], m, j, xu[s], G, X, sg, x);
+      dterm(s, aT, xu[s], x, R(9));
+      carries(10 * s + 1, G, X, sg);
+      pass2<R, L>(A.matT[s][2], m, j, cb[s], G, X, sg, aS);
+      carries(10 * s + 6, G, X, sg);
+      pass2<R, L>(A.mat[s][2], m, j, xu[s], G, X, sg, x);
+      dterm(s, aS, xu[s], x, R(-8));
+#pragma unroll
+      for (int t = 0; t < L; ++t) cb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
+      // cbar_f
+      carries(10 * s + 2, G, X, sg);
+      pass2<R, L>(A.matT[s][1], m, j, fb[s], G, X, sg, aT);
+      carries(10 * s + 7, G, X, sg);
+      pass2<R, L>(A.mat[s][1], m, j, xf[s], G, X, sg, x);
+      dterm(s, aT, xf[s], x, R(9));
+      carries(10 * s + 3, G, X, sg);
+      pass2<R, L>(A.matT[s][2], m, j, fb[s], G, X, sg, aS);
+      carries(10 * s + 8, G, X, sg);
+      pass2<R, L>(A.mat[s][2], m, j, xf[s], G, X, sg, x);
+      dterm(s, aS, xf[s], x, R(-8));
+#pragma unroll
+      for (int t = 0; t < L; ++t) fb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
+      // wbar
+      R xw[L];
+      xw_at(s, xw);
+      carries(10 * s + 4, G, X, sg);
+      pass2<R, L>(A.matT[s][0], m, j, wb[s], G, X, sg, aT);
+      carries(10 * s + 9, G, X, sg);
+      pass2<R, L>(A.mat[s][0], m, j, xw, G, X, sg, x);
+      dterm(s, aT, xw, x, R(1));
+#pragma unroll
+      for (int t = 0; t < L; ++t) wb[s][t] = aT[t];
+    }
+    if constexpr (KIND == ADJ_MIDDLE) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        store_chunk<R, L, CONTIG>(cb[s], A.out[0] + s * N, off0, st, cnt);
+        store_chunk<R, L, CONTIG>(fb[s], A.out[1] + s * N, off0, st, cnt);
+        store_chunk<R, L, CONTIG>(wb[s], A.out[2] + s * N, off0, st, cnt);
+      }
+    } else {
+      // c_U = U_n, c_f = F(U_n), w* = U_n + k F(U_n):
+      // f0bar = cbar_f + k wbar*, Ubar_n = cbar_U + wbar* + J_F(U_n)^T f0bar
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        R u[S], yb[S], ob[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          u[s] = xu[s][t];
+          yb[s] = (t < cnt) ? fma(k, wb[s][t], fb[s][t]) : R(0);
+        }
+        reaction_vjp<R, S>(A, u, yb, ob, pg, qsrc(t));
+#pragma unroll
+        for (int s = 0; s < S; ++s) cb[s][t] = cb[s][t] + wb[s][t] + ob[s];
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s) store_chunk<R, L, CONTIG>(cb[s], A.out[0] + s * N, off0, st, cnt);
+    }
+  }
+  // accumulate dL/dD and dL/dparams
+  double v[MAX_SPECIES + 8];
+#pragma unroll
+  for (int s = 0; s < MAX_SPECIES; ++s) v[s] = (s < S && line_ok) ? (double)dD[s] * A.invD[s] : 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[MAX_SPECIES + i] = line_ok ? (double)pg[i] : 0.0;
+  block_accumulate<MAX_SPECIES + 8>(v, A.acc, red);
+}
+
+// L = 1/2 sum (U - target)^2, Ubar = U - target
+template <typename R>
+__global__ void __launch_bounds__(256) misfit_kernel(const R *__restrict__ U, const R *__restrict__ T,
+                                                      R *__restrict__ Ub, long long n, double *loss) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const R r = U[i] - T[i];
+    Ub[i] = r;
+    acc += 0.5 * (double)r * (double)r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    atomicAdd(loss, s);
+  }
+}
+
+}  // namespace etd

@@ -1,0 +1,17 @@
+// etd_adjoint_f32.cu -- adjoint sweep kernels and launchers for float.
+#include "etd_adjoint_launch.cuh"
+
+namespace etd {
+
+cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                           cudaStream_t s) {
+#define CALL(S_, L_, K_) launch_adj_one<float, S_, L_, K_>(a, nthreads, smem, s)
+  ETD_ADJ_DISPATCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, cudaStream_t s) {
+  return launch_misfit<float>(U, target, Ubar, n, loss, s);
+}
+
+}  // namespace etd

@@ -1,0 +1,17 @@
+// etd_adjoint_f64.cu -- adjoint sweep kernels and launchers for double.
+#include "etd_adjoint_launch.cuh"
+
+namespace etd {
+
+cudaError_t launch_adjoint(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                           cudaStream_t s) {
+#define CALL(S_, L_, K_) launch_adj_one<double, S_, L_, K_>(a, nthreads, smem, s)
+  ETD_ADJ_DISPATCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_loss(const double *U, const double *target, double *Ubar, long long n, double *loss, cudaStream_t s) {
+  return launch_misfit<double>(U, target, Ubar, n, loss, s);
+}
+
+}  // namespace etd

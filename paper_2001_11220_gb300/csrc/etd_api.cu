@@ -540,6 +540,12 @@ void etd_destroy(etd_ctx *ctx) {
     I.arena.release();
   }
   if (ctx->host_state) cudaFree(ctx->host_state);
+  if (ctx->adj_ws) cudaFree(ctx->adj_ws);
+  for (void *p : ctx->adj_ubar)
+    if (p) cudaFree(p);
+  if (ctx->adj_acc) cudaFree(ctx->adj_acc);
+  if (ctx->ckpt) cudaFree(ctx->ckpt);
+  if (ctx->seg) cudaFree(ctx->seg);
   for (auto &rec : ctx->prof_events) {
     cudaEventDestroy(rec.second.first);
     cudaEventDestroy(rec.second.second);

@@ -70,6 +70,11 @@ struct Instance {
   MatTab<float> tab32[2][3][MAX_SPECIES][3];
   MatTab<double> tab64[2][3][MAX_SPECIES][3];
   void *scratch[3] = {nullptr, nullptr, nullptr};  // c_U, c_f, w
+  // adjoint: launch plans and line tables at the adjoint chunk length
+  bool adj_ready = false;
+  AxisPlan aplan[3];
+  MatTab<float> atab32[2][3][MAX_SPECIES][3];
+  MatTab<double> atab64[2][3][MAX_SPECIES][3];
   DeviceArena arena;
   std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
 };
@@ -107,8 +112,13 @@ struct etd_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
   std::vector<cudaEvent_t> prof_pool;
   // adjoint / gradient workspace (allocated on first use)
-  void *adj_ws = nullptr;
-  size_t adj_ws_bytes = 0;
+  void *adj_ws = nullptr;         // 9 carried fields: forward axis-0 outputs, axis-1 outputs, adjoint fields
+  void *adj_ubar[2] = {nullptr, nullptr};
+  double *adj_acc = nullptr;      // dL/dD[2], dL/dparams[8], loss
+  void *ckpt = nullptr;           // checkpoint states
+  size_t ckpt_states = 0;
+  void *seg = nullptr;            // states of one recomputed segment
+  size_t seg_states = 0;
 };
 
 namespace etd {

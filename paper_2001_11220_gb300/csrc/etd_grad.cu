@@ -1,0 +1,346 @@
+// etd_grad.cu -- reverse mode: one adjoint step (etd_step_adjoint) and the
+// checkpointed gradient of a final-state misfit (etd_grad).
+//
+// Adjoint of one step n: recompute the forward sweeps' intermediates of step
+// n from U_n (axis-0 outputs; in 3D also the axis-1 outputs, kept out of
+// place), then run the adjoint sweeps in reverse axis order (last, middle,
+// first).  etd_grad stores U every ckpt steps on the forward pass; in the
+// reverse pass each segment is recomputed from its checkpoint and walked
+// backwards.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/etdrdpif.h"
+#include "etd_context.h"
+#include "etd_internal.h"
+#include "etd_tables.h"
+
+namespace etd {
+bool plan_axis(Instance &I, int a, int L, int max_threads);
+}
+
+using namespace etd;
+
+namespace {
+
+int pow2_floor_i(long long v) {
+  int p = 1;
+  while ((long long)p * 2 <= v) p *= 2;
+  return p;
+}
+
+bool plan_adjoint_axis(Instance &I, int a, int L) {
+  AxisPlan &P = I.aplan[a];
+  const long long n = I.n[a];
+  P.L = L;
+  P.m = (int)((n + L - 1) / L);
+  if (P.m > ETD_MAX_BLOCK_THREADS) return false;
+  P.kind = (a == 0) ? ADJ_FIRST : (a == I.dim - 1 ? ADJ_LAST : ADJ_MIDDLE);
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  P.st = st;
+  P.nlines = I.N / n;
+  P.pitch = (P.m % 2 == 0) ? P.m + 1 : P.m;
+  const long long avail = (a == 0) ? P.nlines : st;
+  int nlb = pow2_floor_i(std::min<long long>(32, ETD_MAX_BLOCK_THREADS / P.m));
+  while (nlb > 1 && nlb / 2 >= avail) nlb /= 2;
+  while (nlb > 1 && adjoint_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes) > 200 * 1024) nlb /= 2;
+  P.nlb = nlb;
+  P.nthreads = nlb * P.m;
+  P.smem = adjoint_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes);
+  if (a == 0) {
+    P.nlo_blocks = 1;
+    P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
+  } else {
+    P.nlo_blocks = (int)((st + nlb - 1) / nlb);
+    P.nblocks = (int)(P.nlo_blocks * (I.N / (st * n)));
+  }
+  P.sp = StagePlan{};
+  return P.smem <= 200 * 1024;
+}
+
+template <typename R>
+void upload(DeviceArena &arena, const HostTab &T, MatTab<R> &M, cudaError_t &err) {
+  std::vector<R> pos(T.pos.begin(), T.pos.end()), sum(T.sum.begin(), T.sum.end()), ch(T.chunk.begin(), T.chunk.end());
+  M.pos = (const typename V4T<R>::T *)arena.put(pos.data(), pos.size() * sizeof(R), err);
+  M.sum = (const typename V2T<R>::T *)arena.put(sum.data(), sum.size() * sizeof(R), err);
+  M.chunk = (const typename V4T<R>::T *)arena.put(ch.data(), ch.size() * sizeof(R), err);
+  M.sm_c = T.sm_c;
+  M.sm_inv = T.sm_inv;
+}
+
+etd_status prepare_adjoint(etd_ctx *ctx, Instance &I) {
+  if (!I.adj_ready) {
+    static const double gammas[3] = {1.0, 3.0, 4.0};
+    for (int a = 0; a < I.dim; ++a) {
+      int L = (I.real_bytes == 4 && I.S == 1) ? 8 : 4;
+      while (!plan_adjoint_axis(I, a, L) && L < 8) L *= 2;
+      if (!plan_adjoint_axis(I, a, L))
+        return fail(ctx, ETD_ERR_UNSUPPORTED, "adjoint: axis %d with n = %lld does not fit one block", a,
+                    (long long)I.n[a]);
+      const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+      cudaError_t err = cudaSuccess;
+      for (int s = 0; s < I.S; ++s)
+        for (int g = 0; g < 3; ++g)
+          for (int tr = 0; tr < 2; ++tr) {
+            HostTab T;
+            build_tab((int)I.n[a], I.bc[a], (I.k / gammas[g]) * I.D[s] / (h * h), tr != 0, L, T);
+            if (I.real_bytes == 8) upload<double>(I.arena, T, I.atab64[tr][a][s][g], err);
+            else upload<float>(I.arena, T, I.atab32[tr][a][s][g], err);
+            if (err != cudaSuccess) return cuda_fail(ctx, err, "adjoint tables");
+          }
+    }
+    I.adj_ready = true;
+  }
+  const size_t field = (size_t)I.S * I.N * I.real_bytes;
+  if (!ctx->adj_ws) {
+    if (cudaMalloc(&ctx->adj_ws, 9 * field) != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "adjoint workspace");
+    if (cudaMalloc(&ctx->adj_ubar[0], field) != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "adjoint workspace");
+    if (cudaMalloc(&ctx->adj_ubar[1], field) != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "adjoint workspace");
+    if (cudaMalloc((void **)&ctx->adj_acc, 16 * sizeof(double)) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "adjoint accumulators");
+  }
+  return ETD_OK;
+}
+
+template <typename R>
+void geometry(const AxisPlan &P, const Instance &I, int a, SweepArgs<R> &A) {
+  memset(&A, 0, sizeof(A));
+  A.N = I.N;
+  A.st = P.st;
+  A.nlines = P.nlines;
+  A.n = (int)I.n[a];
+  A.nlo_blocks = P.nlo_blocks;
+  A.m = P.m;
+  A.nlb = P.nlb;
+  A.pitch = P.pitch;
+  A.nblocks = P.nblocks;
+  A.k = I.k;
+  A.rkind = I.rkind;
+  for (int j = 0; j < 8; ++j) A.rp[j] = I.rp[j];
+  for (int b = 0; b < 3; ++b) A.phi[b] = (const R *)I.phi[b];
+  A.nx = (int)I.n[0];
+  A.ny = (int)I.n[1];
+  A.src_lf = I.src_lf;
+  A.axis = a;
+}
+
+// forward sweeps of step n up to (not including) the last axis: axis-0
+// outputs to fa, axis-1 outputs (3D) to fb
+template <typename R>
+cudaError_t forward_intermediates(const Instance &I, const R *Un, double t, R *fa, R *fb, cudaStream_t s) {
+  const size_t F = (size_t)I.S * I.N;
+  for (int a = 0; a < I.dim - 1; ++a) {
+    SweepArgs<R> A;
+    fill_args<R>(I, a, 0, A);
+    if (a == 0) {
+      A.in[0] = Un;
+    } else {
+      A.in[0] = fa;
+      A.in[1] = fa + F;
+      A.in[2] = fa + 2 * F;
+    }
+    R *o = (a == 0) ? fa : fb;
+    A.out[0] = o;
+    A.out[1] = o + F;
+    A.out[2] = o + 2 * F;
+    A.t_eval = t;
+    A.exp_mt = std::exp(-t);
+    const AxisPlan &P = I.plan[a];
+    cudaError_t e = launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double t, const R *ubar_next, R *ubar_out) {
+  cudaStream_t s = ctx->stream;
+  const size_t F = (size_t)I.S * I.N;
+  R *ws = (R *)ctx->adj_ws;
+  R *fa = ws, *fb = ws + 3 * F, *cb = ws + 6 * F;
+  cudaError_t e = forward_intermediates<R>(I, Un, t, fa, fb, s);
+  if (e != cudaSuccess) return e;
+  const R *z = (I.dim == 3) ? fb : fa;  // inputs of the last forward sweep
+  for (int a = I.dim - 1; a >= 0; --a) {
+    const AxisPlan &P = I.aplan[a];
+    SweepArgs<R> A;
+    geometry<R>(P, I, a, A);
+    for (int sp = 0; sp < I.S; ++sp) {
+      for (int g = 0; g < 3; ++g) {
+        if constexpr (sizeof(R) == 8) {
+          A.mat[sp][g] = I.atab64[0][a][sp][g];
+          A.matT[sp][g] = I.atab64[1][a][sp][g];
+        } else {
+          A.mat[sp][g] = I.atab32[0][a][sp][g];
+          A.matT[sp][g] = I.atab32[1][a][sp][g];
+        }
+      }
+      A.invD[sp] = 1.0 / I.D[sp];
+    }
+    A.acc = ctx->adj_acc;
+    if (P.kind == ADJ_LAST) {
+      A.in[0] = ubar_next;
+      A.fin[0] = z;
+      A.fin[1] = z + F;
+      A.fin[2] = z + 2 * F;
+      A.t_eval = t + I.k;
+    } else {
+      A.in[0] = cb;
+      A.in[1] = cb + F;
+      A.in[2] = cb + 2 * F;
+      A.t_eval = t;
+      if (P.kind == ADJ_MIDDLE) {
+        A.fin[0] = fa;
+        A.fin[1] = fa + F;
+        A.fin[2] = fa + 2 * F;
+      } else {
+        A.fin[0] = Un;
+      }
+    }
+    if (P.kind == ADJ_FIRST) {
+      A.out[0] = ubar_out;
+    } else {
+      A.out[0] = cb;
+      A.out[1] = cb + F;
+      A.out[2] = cb + 2 * F;
+    }
+    A.exp_mt = std::exp(-A.t_eval);
+    e = launch_adjoint(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t adjoint_step(etd_ctx *ctx, const Instance &I, const void *Un, double t, const void *ub_next, void *ub_out) {
+  if (I.real_bytes == 8)
+    return adjoint_step_t<double>(ctx, I, (const double *)Un, t, (const double *)ub_next, (double *)ub_out);
+  return adjoint_step_t<float>(ctx, I, (const float *)Un, t, (const float *)ub_next, (float *)ub_out);
+}
+
+etd_status check_grad_ctx(etd_ctx *ctx) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "gradients of batched contexts are not supported");
+  const Instance &I = ctx->inst[0];
+  for (int s = 0; s < I.S; ++s)
+    if (!(I.D[s] > 0))
+      return fail(ctx, ETD_ERR_UNSUPPORTED, "the adjoint needs D_s > 0 (D[%d] = %g): dL/dD is formed as "
+                                            "<lambda, b - x> / D_s", s, I.D[s]);
+  return ETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+etd_status etd_step_adjoint(etd_ctx *ctx, const void *Un, double t_n, const void *Ubar_next, void *Ubar_n,
+                            double *dD, double *dparams) {
+  etd_status st = check_grad_ctx(ctx);
+  if (st != ETD_OK) return st;
+  if (!Un || !Ubar_next || !Ubar_n) return fail(ctx, ETD_ERR_INVALID_ARG, "null state pointer");
+  if (!std::isfinite(t_n)) return fail(ctx, ETD_ERR_INVALID_ARG, "t_n not finite");
+  Instance &I = ctx->inst[0];
+  st = prepare_adjoint(ctx, I);
+  if (st != ETD_OK) return st;
+  cudaError_t e = cudaMemsetAsync(ctx->adj_acc, 0, 16 * sizeof(double), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "accumulator reset");
+  e = adjoint_step(ctx, I, Un, t_n, Ubar_next, Ubar_n);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint step launch");
+  double acc[16];
+  e = cudaMemcpyAsync(acc, ctx->adj_acc, sizeof(acc), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint accumulators");
+  if (dD)
+    for (int s = 0; s < I.S; ++s) dD[s] += acc[s];
+  if (dparams)
+    for (int j = 0; j < 8; ++j) dparams[j] += acc[MAX_SPECIES + j];
+  return ETD_OK;
+}
+
+etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target, int64_t nsteps, int64_t ckpt_every,
+                    double *loss, void *dU0, double *dD, double *dparams) {
+  etd_status st = check_grad_ctx(ctx);
+  if (st != ETD_OK) return st;
+  if (!U0 || !target || !dU0 || !loss) return fail(ctx, ETD_ERR_INVALID_ARG, "null argument");
+  if (nsteps < 0 || ckpt_every < 1) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0 or ckpt_every < 1");
+  if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
+  Instance &I = ctx->inst[0];
+  st = prepare_adjoint(ctx, I);
+  if (st != ETD_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const size_t bytes = (size_t)I.S * I.N * I.real_bytes;
+  const int64_t nseg = nsteps == 0 ? 1 : (nsteps + ckpt_every - 1) / ckpt_every;
+  const int64_t seglen = std::min<int64_t>(ckpt_every, std::max<int64_t>(nsteps, 1));
+  if (ctx->ckpt_states < (size_t)nseg) {
+    if (ctx->ckpt) cudaFree(ctx->ckpt);
+    ctx->ckpt = nullptr;
+    ctx->ckpt_states = 0;
+    if (cudaMalloc(&ctx->ckpt, bytes * nseg) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "checkpoint storage (%lld states)", (long long)nseg);
+    ctx->ckpt_states = nseg;
+  }
+  if (ctx->seg_states < (size_t)(seglen + 1)) {
+    if (ctx->seg) cudaFree(ctx->seg);
+    ctx->seg = nullptr;
+    ctx->seg_states = 0;
+    if (cudaMalloc(&ctx->seg, bytes * (seglen + 1)) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "segment storage (%lld states)", (long long)seglen + 1);
+    ctx->seg_states = seglen + 1;
+  }
+  unsigned char *ck = (unsigned char *)ctx->ckpt, *sg = (unsigned char *)ctx->seg;
+  unsigned char *run = sg + bytes * seglen;  // running state of the forward pass
+  cudaError_t e = cudaMemsetAsync(ctx->adj_acc, 0, 16 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(run, U0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "grad setup");
+  // forward pass with checkpoints
+  for (int64_t g = 0; g < nseg; ++g) {
+    e = cudaMemcpyAsync(ck + bytes * g, run, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "checkpoint copy");
+    const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
+    for (int64_t i = 0; i < len; ++i) {
+      e = forward_step(I, run, t0 + (double)(s0 + i) * I.k, s, nullptr);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "forward step");
+    }
+  }
+  // misfit and its gradient
+  void *ub = ctx->adj_ubar[0], *ub2 = ctx->adj_ubar[1];
+  if (I.real_bytes == 8)
+    e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
+                    ctx->adj_acc + 10, s);
+  else
+    e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N, ctx->adj_acc + 10,
+                    s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "misfit");
+  // reverse pass, segment by segment
+  for (int64_t g = nseg - 1; g >= 0 && nsteps > 0; --g) {
+    const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
+    e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
+    for (int64_t i = 1; i < len && e == cudaSuccess; ++i) {
+      e = cudaMemcpyAsync(sg + bytes * i, sg + bytes * (i - 1), bytes, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = forward_step(I, sg + bytes * i, t0 + (double)(s0 + i - 1) * I.k, s, nullptr);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "segment recompute");
+    for (int64_t i = len - 1; i >= 0; --i) {
+      e = adjoint_step(ctx, I, sg + bytes * i, t0 + (double)(s0 + i) * I.k, ub, ub2);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint step");
+      std::swap(ub, ub2);
+    }
+  }
+  e = cudaMemcpyAsync(dU0, ub, bytes, cudaMemcpyDeviceToDevice, s);
+  double acc[16];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, ctx->adj_acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient read-back");
+  *loss = acc[10];
+  if (dD)
+    for (int sp = 0; sp < I.S; ++sp) dD[sp] = acc[sp];
+  if (dparams)
+    for (int j = 0; j < 8; ++j) dparams[j] = acc[MAX_SPECIES + j];
+  return ETD_OK;
+}
+
+}  // extern "C"

@@ -85,7 +85,14 @@ template <typename R> struct SweepArgs {
   double src_lf;   // Sum_a (pi / L_a)^2
   int axis;        // swept axis
   StagePlan sp;    // staged-kernel plan
+  // adjoint sweeps only
+  MatTab<R> matT[MAX_SPECIES][3];  // tables of the transposed line matrices
+  const R *fin[3];                 // forward quantities recomputed for this sweep
+  double *acc;                     // device accumulators: dL/dD[MAX_SPECIES], dL/dparams[8]
+  double invD[MAX_SPECIES];        // 1 / D_s
 };
+
+enum AdjKind { ADJ_FIRST = 0, ADJ_MIDDLE = 1, ADJ_LAST = 2 };
 
 // host-side launchers (one translation unit per element type)
 cudaError_t launch_sweep(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads,
@@ -99,6 +106,22 @@ cudaError_t launch_sweep_batched(const SweepArgs<float> *args_dev, const int *bl
 cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *block_start_dev, int ninst,
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
                                  size_t smem, cudaStream_t s);
+
+cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_adjoint(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, cudaStream_t s);
+cudaError_t launch_loss(const double *U, const double *target, double *Ubar, long long n, double *loss,
+                        cudaStream_t s);
+
+// shared-memory bytes of one adjoint sweep block
+inline size_t adjoint_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes) {
+  int nq = (kind == ADJ_LAST) ? 6 * nspecies : 10 * nspecies;
+  size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes;
+  sums = (sums + 15) & ~(size_t)15;
+  return sums + (size_t)nq * nlb * sizeof(double) + 16 * sizeof(double) * 32;
+}
 
 // shared-memory bytes of one sweep block
 inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes) {

@@ -7,14 +7,6 @@ using namespace etd;
 
 extern "C" {
 
-etd_status etd_step_adjoint(etd_ctx *ctx, const void *, double, const void *, void *, double *, double *) {
-  return fail(ctx, ETD_ERR_UNSUPPORTED, "etd_step_adjoint not implemented");
-}
-
-etd_status etd_grad(etd_ctx *ctx, const void *, double, const void *, int64_t, int64_t, double *, void *, double *,
-                    double *) {
-  return fail(ctx, ETD_ERR_UNSUPPORTED, "etd_grad not implemented");
-}
 
 etd_status etd_batch_create(int32_t, const etd_grid *, const double *, const etd_reaction *, double, int32_t, void *,
                             etd_ctx **out) {
