@@ -147,6 +147,14 @@ etd_status etd_step_adjoint(etd_ctx *ctx, const void *Un, double t_n, const void
 etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target, int64_t nsteps,
                     int64_t ckpt_every, double *loss, void *dU0, double *dD, double *dparams);
 
+/* Vector-Jacobian product of a run: given U0 (device) at t0 and a cotangent
+ * Ubar_N = dL/dU_N (device) of the state after nsteps steps, writes
+ * dU0 = dL/dU0 (device) and dD[nspecies], dparams[8] (host) for any
+ * differentiable L of U_N (the reverse pass of etd_grad with the misfit
+ * replaced by the caller's cotangent; same checkpointing).  Synchronises. */
+etd_status etd_run_vjp(etd_ctx *ctx, const void *U0, double t0, int64_t nsteps, int64_t ckpt_every,
+                       const void *Ubar_N, void *dU0, double *dD, double *dparams);
+
 /* Batched ensemble: ninst independent problems (grids[i], D[i*nspecies ..],
  * reactions[i]; all instances share nspecies, dim and precision; k is
  * common) advanced together, one launch per sweep kind covering every

@@ -114,6 +114,18 @@ class EtdRdpIf:
                                   ctypes.byref(loss), ctypes.c_void_p(dU0.data_ptr()), dD, dp), self.ctx)
         return loss.value, dU0, np.array(dD[:]), np.array(dp[:])
 
+    def run_vjp(self, U0: torch.Tensor, t0: float, nsteps: int, Ubar_N: torch.Tensor, ckpt_every: int = 20):
+        """(dU0, dD, dparams) for the cotangent Ubar_N of the state after nsteps steps."""
+        self._check_state(U0)
+        self._check_state(Ubar_N)
+        dU0 = torch.empty_like(U0)
+        dD = (ctypes.c_double * len(self.D))()
+        dp = (ctypes.c_double * 8)()
+        B.check(self.lib.etd_run_vjp(self.ctx, ctypes.c_void_p(U0.data_ptr()), float(t0), int(nsteps),
+                                     int(ckpt_every), ctypes.c_void_p(Ubar_N.data_ptr()),
+                                     ctypes.c_void_p(dU0.data_ptr()), dD, dp), self.ctx)
+        return dU0, np.array(dD[:]), np.array(dp[:])
+
     def autotune(self, U_work: torch.Tensor):
         self._check_state(U_work)
         B.check(self.lib.etd_autotune(self.ctx, ctypes.c_void_p(U_work.data_ptr())), self.ctx)
@@ -127,6 +139,61 @@ class EtdRdpIf:
         ln = (ctypes.c_int64 * 3)()
         B.check(self.lib.etd_profile_read(self.ctx, ms, ln), self.ctx)
         return list(ms), list(ln)
+
+    def info(self) -> dict:
+        inf = B.etd_info()
+        B.check(self.lib.etd_get_info(self.ctx, ctypes.byref(inf)), self.ctx)
+        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block", "staged") else getattr(inf, f))
+                for f, _ in inf._fields_}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.etd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class EtdEnsemble:
+    """Many independent problems (same dimension, species count, precision and
+    time step; any grid size, boundaries, coefficients and reaction parameters)
+    advanced together: one kernel launch per sweep kind covers every instance."""
+
+    def __init__(self, workloads, precision="fp32", stream=None):
+        self.lib = B.load()
+        ws = list(workloads)
+        if not ws:
+            raise ValueError("empty ensemble")
+        self.k = float(ws[0].k)
+        if any(abs(w.k - self.k) > 0 for w in ws):
+            raise ValueError("every instance needs the same time step k")
+        self.S = ws[0].nspecies
+        self.precision = B.ETD_FP64 if precision in ("fp64", B.ETD_FP64) else B.ETD_FP32
+        self.dtype = torch.float64 if self.precision == B.ETD_FP64 else torch.float32
+        self.shapes = [w.shape for w in ws]
+        n = len(ws)
+        grids = (B.etd_grid * n)(*[make_grid(w.n, w.bc, w.length) for w in ws])
+        rx = (B.etd_reaction * n)(*[make_reaction(w.reaction, w.nspecies, w.params) for w in ws])
+        D = (ctypes.c_double * (n * self.S))(*[d for w in ws for d in w.D])
+        ctx = ctypes.c_void_p()
+        B.check(self.lib.etd_batch_create(n, grids, D, rx, self.k, self.precision, _stream_handle(stream),
+                                          ctypes.byref(ctx)), None)
+        self.ctx = ctx
+        self.n = n
+
+    def run(self, states, t0: float, nsteps: int):
+        if len(states) != self.n:
+            raise ValueError(f"expected {self.n} states")
+        for U, shp in zip(states, self.shapes):
+            if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous() and tuple(U.shape) == shp):
+                raise ValueError("every state must be a contiguous CUDA tensor of its instance's shape and dtype")
+        ptrs = (ctypes.c_void_p * self.n)(*[U.data_ptr() for U in states])
+        B.check(self.lib.etd_batch_run(self.ctx, ptrs, float(t0), int(nsteps)), self.ctx)
+        return states
 
     def info(self) -> dict:
         inf = B.etd_info()

@@ -172,8 +172,8 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
     }
   }
   if (a == 0) {
-    int nlb = std::max(1, 256 / P.m);
-    nlb = (int)std::min<long long>(nlb, P.nlines);
+    int nlb = pow2_floor(std::min(32, std::max(1, max_threads / P.m)));
+    while (nlb > 1 && nlb / 2 >= P.nlines) nlb /= 2;
     P.nlb = nlb;
     P.nlo_blocks = 1;
     P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
@@ -540,6 +540,11 @@ void etd_destroy(etd_ctx *ctx) {
     I.arena.release();
   }
   if (ctx->host_state) cudaFree(ctx->host_state);
+  if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
+  for (int a = 0; a < 3; ++a) {
+    if (ctx->batch_args[a]) cudaFree(ctx->batch_args[a]);
+    if (ctx->batch_block_start[a]) cudaFree(ctx->batch_block_start[a]);
+  }
   if (ctx->adj_ws) cudaFree(ctx->adj_ws);
   for (void *p : ctx->adj_ubar)
     if (p) cudaFree(p);

@@ -1,0 +1,188 @@
+// etd_batch.cu -- batched ensemble: many independent problems of uneven size
+// advanced together, one kernel launch per sweep kind covering every
+// instance (blocks find their instance by a prefix sum over block counts);
+// multi-step runs are captured into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/etdrdpif.h"
+#include "etd_context.h"
+#include "etd_internal.h"
+
+namespace etd {
+etd_status validate_problem(const etd_grid *grid, const double *D, const etd_reaction *rx, double k,
+                            int32_t precision);
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force);
+etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
+etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const double *D, const etd_reaction *rx,
+                         double k, int32_t precision, bool with_scratch);
+}  // namespace etd
+
+using namespace etd;
+
+namespace {
+
+template <typename R>
+etd_status upload_batch_args(etd_ctx *ctx, void *const *U) {
+  const int ninst = (int)ctx->inst.size();
+  const int dim = ctx->inst[0].dim;
+  std::vector<SweepArgs<R>> args(ninst);
+  for (int a = 0; a < dim; ++a) {
+    for (int i = 0; i < ninst; ++i) {
+      const Instance &I = ctx->inst[i];
+      SweepArgs<R> &A = args[i];
+      fill_args<R>(I, a, 0, A);
+      R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
+      const int kind = I.plan[a].kind;
+      if (kind == SWEEP_FIRST) {
+        A.in[0] = (const R *)U[i];
+        A.out[0] = cu; A.out[1] = cf; A.out[2] = w;
+      } else if (kind == SWEEP_MIDDLE) {
+        A.in[0] = cu; A.in[1] = cf; A.in[2] = w;
+        A.out[0] = cu; A.out[1] = cf; A.out[2] = w;
+      } else {
+        A.in[0] = cu; A.in[1] = cf; A.in[2] = w;
+        A.out[0] = (R *)U[i];
+      }
+    }
+    // ordered on the context's stream: launches still in flight keep reading the old arguments
+    cudaError_t e = cudaMemcpyAsync(ctx->batch_args[a], args.data(), sizeof(SweepArgs<R>) * ninst,
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // host buffer must outlive the copy
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch argument upload");
+  }
+  return ETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *D, const etd_reaction *reactions,
+                            double k, int32_t precision, void *stream, etd_ctx **out) {
+  if (!out) return fail(nullptr, ETD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ninst < 1 || !grids || !D || !reactions) return fail(nullptr, ETD_ERR_INVALID_ARG, "empty or null ensemble");
+  const int S = reactions[0].nspecies;
+  for (int i = 0; i < ninst; ++i) {
+    etd_status st = validate_problem(&grids[i], D + (size_t)i * S, &reactions[i], k, precision);
+    if (st != ETD_OK) return st;
+    if (grids[i].dim != grids[0].dim || reactions[i].nspecies != S)
+      return fail(nullptr, ETD_ERR_INVALID_ARG, "instance %d: every instance needs the same dim and nspecies", i);
+  }
+  etd_ctx *ctx = new (std::nothrow) etd_ctx();
+  if (!ctx) return fail(nullptr, ETD_ERR_OOM, "host allocation failed");
+  ctx->stream = (cudaStream_t)stream;
+  ctx->precision = precision;
+  ctx->batched = true;
+  ctx->inst.resize(ninst);
+  const int dim = grids[0].dim;
+  const int rb = precision == ETD_FP64 ? 8 : 4;
+  auto abort_create = [&](etd_status st) {
+    std::string msg = ctx->err;
+    etd_destroy(ctx);
+    return fail(nullptr, st, "%s", msg.c_str());
+  };
+  // common chunk length per axis (kernel template parameter), per-instance tiles
+  int Lax[3];
+  for (int a = 0; a < dim; ++a) Lax[a] = (rb == 4) ? (a == 0 ? 8 : 16) : (a == 0 ? 4 : 8);
+  size_t scratch_elems = 0;
+  for (int i = 0; i < ninst; ++i) {
+    Instance &I = ctx->inst[i];
+    etd_status st = init_instance(ctx, I, &grids[i], D + (size_t)i * S, &reactions[i], k, precision, false);
+    if (st != ETD_OK) return abort_create(st);
+    for (int a = 0; a < dim; ++a) {
+      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true)) {
+        fail(ctx, ETD_ERR_UNSUPPORTED, "instance %d axis %d does not fit one block", i, a);
+        return abort_create(ETD_ERR_UNSUPPORTED);
+      }
+      st = build_axis_tables(ctx, I, a);
+      if (st != ETD_OK) return abort_create(st);
+    }
+    scratch_elems += (size_t)3 * I.S * I.N;
+  }
+  if (cudaMalloc(&ctx->batch_scratch, scratch_elems * rb) != cudaSuccess) {
+    fail(ctx, ETD_ERR_OOM, "ensemble scratch of %zu bytes", scratch_elems * rb);
+    return abort_create(ETD_ERR_OOM);
+  }
+  size_t off = 0;
+  for (Instance &I : ctx->inst) {
+    const size_t F = (size_t)I.S * I.N;
+    for (int f = 0; f < 3; ++f) I.scratch[f] = (unsigned char *)ctx->batch_scratch + (off + f * F) * rb;
+    off += 3 * F;
+  }
+  for (int a = 0; a < dim; ++a) {
+    std::vector<int> bs(ninst + 1, 0);
+    int thr = 0;
+    size_t smem = 0;
+    for (int i = 0; i < ninst; ++i) {
+      const AxisPlan &P = ctx->inst[i].plan[a];
+      bs[i + 1] = bs[i] + P.nblocks;
+      thr = std::max(thr, P.nthreads);
+      smem = std::max(smem, P.smem);
+    }
+    ctx->batch_total_blocks[a] = bs[ninst];
+    ctx->batch_threads[a] = thr;
+    ctx->batch_smem[a] = smem;
+    ctx->batch_L[a] = Lax[a];
+    const size_t argb = (rb == 8 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>)) * ninst;
+    if (cudaMalloc(&ctx->batch_args[a], argb) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->batch_block_start[a], sizeof(int) * (ninst + 1)) != cudaSuccess) {
+      fail(ctx, ETD_ERR_OOM, "ensemble launch tables");
+      return abort_create(ETD_ERR_OOM);
+    }
+    if (cudaMemcpy(ctx->batch_block_start[a], bs.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      fail(ctx, ETD_ERR_CUDA, "ensemble launch tables upload");
+      return abort_create(ETD_ERR_CUDA);
+    }
+  }
+  *out = ctx;
+  return ETD_OK;
+}
+
+etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_batch_run on a single-problem context");
+  if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
+  if (nsteps < 0 || !std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "bad nsteps or t0");
+  const int ninst = (int)ctx->inst.size();
+  for (int i = 0; i < ninst; ++i)
+    if (!U[i]) return fail(ctx, ETD_ERR_INVALID_ARG, "U[%d] is NULL", i);
+  std::vector<void *> now(U, U + ninst);
+  if (now != ctx->batch_states) {
+    // the device arguments hold the state pointers: rebuild them, drop graphs built on the old ones
+    etd_status st = ctx->precision == ETD_FP64 ? upload_batch_args<double>(ctx, U) : upload_batch_args<float>(ctx, U);
+    if (st != ETD_OK) return st;
+    ctx->batch_states = now;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+  }
+  const Instance &I0 = ctx->inst[0];
+  const double k = I0.k;
+  auto enqueue = [&](cudaStream_t s, int64_t n) -> cudaError_t {
+    const double t = t0 + (double)n * k;
+    for (int a = 0; a < I0.dim; ++a) {
+      const int kind = I0.plan[a].kind;
+      const double te = kind == SWEEP_LAST ? t + k : t;
+      cudaError_t e;
+      if (ctx->precision == ETD_FP64)
+        e = launch_sweep_batched((const SweepArgs<double> *)ctx->batch_args[a], ctx->batch_block_start[a], ninst,
+                                 ctx->batch_total_blocks[a], I0.S, ctx->batch_L[a], kind, ctx->batch_threads[a],
+                                 ctx->batch_smem[a], s, te);
+      else
+        e = launch_sweep_batched((const SweepArgs<float> *)ctx->batch_args[a], ctx->batch_block_start[a], ninst,
+                                 ctx->batch_total_blocks[a], I0.S, ctx->batch_L[a], kind, ctx->batch_threads[a],
+                                 ctx->batch_smem[a], s, te);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  return run_steps(ctx, enqueue, GraphKey{ctx->batch_states.data(), nullptr, t0, nsteps}, nsteps);
+}
+
+}  // extern "C"

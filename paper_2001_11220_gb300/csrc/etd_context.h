@@ -17,21 +17,32 @@
 
 namespace etd {
 
-// device allocations of one instance's tables (one cudaMalloc each)
+// device memory of an instance's tables: 256-byte aligned pieces carved
+// from blocks of at least 1 MiB
 struct DeviceArena {
   std::vector<void *> blocks;
+  size_t used = 0, cap = 0;
   void *put(const void *host, size_t bytes, cudaError_t &err) {
     if (err != cudaSuccess) return nullptr;
-    void *d = nullptr;
-    err = cudaMalloc(&d, bytes < 16 ? 16 : bytes);
-    if (err != cudaSuccess) return nullptr;
-    blocks.push_back(d);
-    err = cudaMemcpy(d, host, bytes, cudaMemcpyHostToDevice);
-    return d;
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    if (blocks.empty() || used + need > cap) {
+      void *d = nullptr;
+      const size_t sz = need > ((size_t)1 << 20) ? need : ((size_t)1 << 20);
+      err = cudaMalloc(&d, sz);
+      if (err != cudaSuccess) return nullptr;
+      blocks.push_back(d);
+      used = 0;
+      cap = sz;
+    }
+    void *p = (unsigned char *)blocks.back() + used;
+    used += need;
+    err = cudaMemcpy(p, host, bytes, cudaMemcpyHostToDevice);
+    return p;
   }
   void release() {
     for (void *p : blocks) cudaFree(p);
     blocks.clear();
+    used = cap = 0;
   }
 };
 
@@ -100,13 +111,15 @@ struct etd_ctx {
   void *host_state = nullptr;           // device copy used by etd_run_host
   std::vector<void *> owned;            // context-level device buffers
   std::list<std::pair<etd::GraphKey, cudaGraphExec_t>> graphs;  // captured multi-step runs
-  // batched launch data (device)
-  void *batch_args[3] = {nullptr, nullptr, nullptr};  // SweepArgs<R>[ninst] per axis
+  // batched launch data: per axis, SweepArgs<R>[ninst] and block prefix sums on the device
+  void *batch_args[3] = {nullptr, nullptr, nullptr};
   int *batch_block_start[3] = {nullptr, nullptr, nullptr};
   int batch_total_blocks[3] = {0, 0, 0};
   int batch_threads[3] = {0, 0, 0};
   size_t batch_smem[3] = {0, 0, 0};
   int batch_L[3] = {0, 0, 0};
+  std::vector<void *> batch_states;  // state pointers the device args were built for
+  void *batch_scratch = nullptr;     // scratch of every instance, one allocation
   // per-sweep profiling (etd_profile)
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;

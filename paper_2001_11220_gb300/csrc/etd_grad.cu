@@ -261,11 +261,18 @@ etd_status etd_step_adjoint(etd_ctx *ctx, const void *Un, double t_n, const void
   return ETD_OK;
 }
 
-etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target, int64_t nsteps, int64_t ckpt_every,
-                    double *loss, void *dU0, double *dD, double *dparams) {
+}  // extern "C"
+
+namespace {
+
+// forward pass with checkpoints, then either the misfit (target != NULL) or a
+// given cotangent ubarN of U_N, then the reverse pass
+etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target, const void *ubarN, int64_t nsteps,
+                     int64_t ckpt_every, double *loss, void *dU0, double *dD, double *dparams) {
   etd_status st = check_grad_ctx(ctx);
   if (st != ETD_OK) return st;
-  if (!U0 || !target || !dU0 || !loss) return fail(ctx, ETD_ERR_INVALID_ARG, "null argument");
+  if (!U0 || !dU0 || (!target && !ubarN)) return fail(ctx, ETD_ERR_INVALID_ARG, "null argument");
+  if (target && !loss) return fail(ctx, ETD_ERR_INVALID_ARG, "loss is NULL");
   if (nsteps < 0 || ckpt_every < 1) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0 or ckpt_every < 1");
   if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
   Instance &I = ctx->inst[0];
@@ -296,7 +303,7 @@ etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target,
   cudaError_t e = cudaMemsetAsync(ctx->adj_acc, 0, 16 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(run, U0, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "grad setup");
-  // forward pass with checkpoints
+  // forward pass with checkpoints (U_{g ckpt} for every segment g)
   for (int64_t g = 0; g < nseg; ++g) {
     e = cudaMemcpyAsync(ck + bytes * g, run, bytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "checkpoint copy");
@@ -306,16 +313,21 @@ etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target,
       if (e != cudaSuccess) return cuda_fail(ctx, e, "forward step");
     }
   }
-  // misfit and its gradient
+  // cotangent of U_N: misfit gradient U_N - target, or the caller's
   void *ub = ctx->adj_ubar[0], *ub2 = ctx->adj_ubar[1];
-  if (I.real_bytes == 8)
-    e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
-                    ctx->adj_acc + 10, s);
-  else
-    e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N, ctx->adj_acc + 10,
-                    s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "misfit");
-  // reverse pass, segment by segment
+  if (target) {
+    if (I.real_bytes == 8)
+      e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
+                      ctx->adj_acc + 10, s);
+    else
+      e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N,
+                      ctx->adj_acc + 10, s);
+  } else {
+    e = cudaMemcpyAsync(ub, ubarN, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "final cotangent");
+  // reverse pass, segment by segment: recompute the segment's states from its
+  // checkpoint, then walk its steps backwards
   for (int64_t g = nseg - 1; g >= 0 && nsteps > 0; --g) {
     const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
     e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
@@ -335,12 +347,28 @@ etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target,
   if (e == cudaSuccess) e = cudaMemcpyAsync(acc, ctx->adj_acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient read-back");
-  *loss = acc[10];
+  if (loss) *loss = target ? acc[10] : 0.0;
   if (dD)
     for (int sp = 0; sp < I.S; ++sp) dD[sp] = acc[sp];
   if (dparams)
     for (int j = 0; j < 8; ++j) dparams[j] = acc[MAX_SPECIES + j];
   return ETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+etd_status etd_grad(etd_ctx *ctx, const void *U0, double t0, const void *target, int64_t nsteps, int64_t ckpt_every,
+                    double *loss, void *dU0, double *dD, double *dparams) {
+  if (!target) return fail(ctx, ETD_ERR_INVALID_ARG, "target is NULL");
+  return grad_core(ctx, U0, t0, target, nullptr, nsteps, ckpt_every, loss, dU0, dD, dparams);
+}
+
+etd_status etd_run_vjp(etd_ctx *ctx, const void *U0, double t0, int64_t nsteps, int64_t ckpt_every,
+                       const void *Ubar_N, void *dU0, double *dD, double *dparams) {
+  if (!Ubar_N) return fail(ctx, ETD_ERR_INVALID_ARG, "Ubar_N is NULL");
+  return grad_core(ctx, U0, t0, nullptr, Ubar_N, nsteps, ckpt_every, nullptr, dU0, dD, dparams);
 }
 
 }  // extern "C"

@@ -102,10 +102,10 @@ cudaError_t launch_sweep(const SweepArgs<double> &a, int nspecies, int L, int ki
 // batched: args[] in device memory, block_start[i] = first block of instance i (prefix, ninst+1)
 cudaError_t launch_sweep_batched(const SweepArgs<float> *args_dev, const int *block_start_dev, int ninst,
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
-                                 size_t smem, cudaStream_t s);
+                                 size_t smem, cudaStream_t s, double t_eval);
 cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *block_start_dev, int ninst,
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
-                                 size_t smem, cudaStream_t s);
+                                 size_t smem, cudaStream_t s, double t_eval);
 
 cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);

@@ -83,12 +83,12 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
 
 // manufactured source p0 ((p1 lf - 1) q + q/(1+q)), q = e^{-t} prod sin(pi x_a/L_a)
 template <typename R>
-__device__ __forceinline__ R mms_source(const SweepArgs<R> &A, long long pidx) {
+__device__ __forceinline__ R mms_source(const SweepArgs<R> &A, long long pidx, double exp_mt) {
   const long long x = pidx % A.nx;
   const long long r = pidx / A.nx;
   const long long y = r % A.ny;
   const long long z = r / A.ny;
-  R q = (R)A.exp_mt * A.phi[0][x] * A.phi[1][y];
+  R q = (R)exp_mt * A.phi[0][x] * A.phi[1][y];
   if (A.phi[2]) q *= A.phi[2][z];
   return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q));
 }
@@ -249,21 +249,16 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, 
 // -------------------------------------------------------------- the sweep
 
 template <typename R, int S, int L, bool CONTIG, int KIND>
-__device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem) {
+__device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
+                                            double exp_mt) {
   constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   const int tid = threadIdx.x;
   // threads past nlb*m (batched launches size blocks for the largest
   // instance) own no chunk but still take part in every barrier and scan
   const bool thr_ok = tid < nlb * m;
-  int l, j;
-  if constexpr (CONTIG) {
-    j = tid % m;
-    l = tid / m;
-  } else {
-    l = tid % nlb;
-    j = tid / nlb;
-  }
+  // lanes walk neighbouring lines on every axis: table reads are warp broadcasts
+  int l = tid % nlb, j = tid / nlb;
   if (!thr_ok) { l = 0; j = 0; }
   long long base;
   bool line_ok;
@@ -313,7 +308,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = cu[s][t];
         R src = R(0);
-        if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st);
+        if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st, exp_mt);
         reaction_point<R, S>(A, u, f, src);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -401,7 +396,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
 #pragma unroll
       for (int s = 0; s < S; ++s) u[s] = w[s][t];
       R src = R(0);
-      if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st);
+      if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st, exp_mt);
       reaction_point<R, S>(A, u, f, src);
 #pragma unroll
       for (int s = 0; s < S; ++s) {
@@ -439,14 +434,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
 template <typename R, int S, int L, bool CONTIG, int KIND>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel(const __grid_constant__ SweepArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  sweep_block<R, S, L, CONTIG, KIND>(A, blockIdx.x, smem);
+  sweep_block<R, S, L, CONTIG, KIND>(A, blockIdx.x, smem, A.t_eval, A.exp_mt);
 }
 
 // Batched ensemble: one launch covers every instance; block b belongs to the
 // instance i with block_start[i] <= b < block_start[i+1].
 template <typename R, int S, int L, bool CONTIG, int KIND>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel_batched(const SweepArgs<R> *__restrict__ args,
-                                                              const int *__restrict__ block_start, int ninst) {
+                                                              const int *__restrict__ block_start, int ninst,
+                                                              double t_eval, double exp_mt) {
   extern __shared__ __align__(16) unsigned char smem[];
   int lo = 0, hi = ninst - 1;
   const int b = blockIdx.x;
@@ -454,7 +450,7 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel_batched(const Sw
     const int mid = (lo + hi + 1) >> 1;
     if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
   }
-  sweep_block<R, S, L, CONTIG, KIND>(args[lo], b - block_start[lo], smem);
+  sweep_block<R, S, L, CONTIG, KIND>(args[lo], b - block_start[lo], smem, t_eval, exp_mt);
 }
 
 }  // namespace etd

@@ -11,8 +11,8 @@ cudaError_t launch_sweep(const SweepArgs<double> &a, int nspecies, int L, int ki
 }
 
 cudaError_t launch_sweep_batched(const SweepArgs<double> *args, const int *bs, int ninst, int total, int nspecies,
-                                 int L, int kind, int nthreads, size_t smem, cudaStream_t s) {
-#define CALL(S_, L_, K_) launch_one_batched<double, S_, L_, K_>(args, bs, ninst, total, nthreads, smem, s)
+                                 int L, int kind, int nthreads, size_t smem, cudaStream_t s, double t_eval) {
+#define CALL(S_, L_, K_) launch_one_batched<double, S_, L_, K_>(args, bs, ninst, total, nthreads, smem, s, t_eval)
   ETD_DISPATCH(CALL)
 #undef CALL
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -78,12 +79,12 @@ cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStr
 
 template <typename R, int S, int L, int KIND>
 cudaError_t launch_one_batched(const SweepArgs<R> *args, const int *bs, int ninst, int total, int nthreads,
-                               size_t smem, cudaStream_t s) {
+                               size_t smem, cudaStream_t s, double t_eval) {
   constexpr bool CONTIG = (KIND == SWEEP_FIRST);
   auto fn = sweep_kernel_batched<R, S, L, CONTIG, KIND>;
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
-  fn<<<total, nthreads, smem, s>>>(args, bs, ninst);
+  fn<<<total, nthreads, smem, s>>>(args, bs, ninst, t_eval, std::exp(-t_eval));
   return cudaGetLastError();
 }
 

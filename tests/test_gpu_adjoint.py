@@ -161,3 +161,35 @@ def test_adjoint_rejects_zero_diffusion():
     with pytest.raises(EtdError):
         ctx.step_adjoint(U, 0.0, U.clone())
     ctx.close()
+
+
+def test_autograd_simulate_matches_oracle_adjoint():
+    """torch.autograd through simulate() for a loss that is not the built-in misfit
+    (sum of w * U_N^2): compared with the oracle's step adjoints chained by hand."""
+    from paper_2001_11220_gb300.autograd import simulate
+    w = case("bru2d_ag", (18, 14), W.NEUMANN, (0.02, 0.03), "brusselator", (1.0, 3.4), 0.05, ((1.0, 3.4), 0.1))
+    nsteps = 6
+    U0 = W.initial_state(w)
+    rng = np.random.default_rng(11)
+    wt = rng.random(U0.shape)
+    U0t = torch.tensor(U0, device="cuda", requires_grad=True)
+    Dt = torch.tensor(w.D, dtype=torch.float64, requires_grad=True)
+    pt = torch.tensor(w.params, dtype=torch.float64, requires_grad=True)
+    UN = simulate(U0t, Dt, pt, n=w.n, bc=w.bc, reaction=w.reaction, k=w.k, nsteps=nsteps, ckpt_every=4)
+    loss = (torch.tensor(wt, device="cuda") * UN * UN).sum()
+    loss.backward()
+    # oracle: forward states, then chained step adjoints with cotangent 2 w U_N
+    P = oracle_problem(w)
+    states = [U0]
+    for i in range(nsteps):
+        states.append(oracle.step(P, states[-1], i * w.k))
+    ub = 2 * wt * states[-1]
+    dD = np.zeros(2)
+    dp = np.zeros(8)
+    for i in reversed(range(nsteps)):
+        ub, d1, p1 = oracle.step_adjoint(P, states[i], i * w.k, ub)
+        dD += d1
+        dp += p1
+    assert rel(U0t.grad.cpu().numpy(), ub) <= 1e-10
+    assert rel(Dt.grad.numpy(), dD) <= 1e-9
+    assert rel(pt.grad.numpy(), dp[:2]) <= 1e-9
