@@ -152,6 +152,85 @@ def workload_desc(w, precision):
             "l2": "inputs larger than L2: each sweep streams 4-6 fields of %d MB" % (w.npoints * (4 if precision == "fp32" else 8) // 2**20)}
 
 
+def _timed(fn, stream, reps=1):
+    """device time of fn() on stream (CUDA events), ms per call"""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
+    """Throughput of the other benchmark problems (cell-species-steps/s):
+    forward + adjoint (checkpointed gradient) on the main workload and on the
+    256^3 periodic Gray-Scott problem, the 4096^2 periodic Schnakenberg step,
+    and the 512-instance Brusselator ensemble."""
+    import torch
+    from paper_2001_11220_gb300.api import EtdEnsemble
+    out = {}
+
+    def mk(w, prec):
+        with torch.cuda.stream(stream):
+            c = EtdRdpIf.from_workload(w, prec, stream=stream)
+            U = torch.tensor(W.initial_state(w), device="cuda", dtype=c.dtype)
+        return c, U
+
+    # forward + adjoint: etd_grad over 20 steps, checkpoint every 10 (main workload)
+    w = W.mms_3d(P_BENCH)
+    c, U = mk(w, "fp32")
+    T = U.clone()
+    nst = 20
+    ms = _timed(lambda: c.grad(U, 0.0, T, nst, 10), stream)
+    out["mms3d_256_fp32_fwd_adjoint"] = {"value": w.npoints * w.nspecies * nst / (ms / 1e3), "unit": UNIT,
+                                         "ms_per_step": ms / nst, "steps": nst, "ckpt_every": 10}
+    c.close()
+    del U, T
+    # 3D Gray-Scott periodic 256^3, 2 species, k = 1: forward and checkpointed gradient (ckpt 20)
+    w = W.gray_scott_3d(256, steps=20)
+    c, U = mk(w, "fp32")
+    tg = torch.tensor(W.initial_state(w, seed=2002), device="cuda", dtype=torch.float32)
+    V = U.clone()
+    msf = _timed(lambda: c.run(V, 0.0, 20), stream)
+    msg = _timed(lambda: c.grad(U, 0.0, tg, 20, 20), stream)
+    units = w.npoints * w.nspecies * 20
+    out["grayscott3d_256_fp32"] = {"fwd": units / (msf / 1e3), "fwd_adjoint": units / (msg / 1e3), "unit": UNIT,
+                                   "fwd_ms_per_step": msf / 20, "fwd_adjoint_ms_per_step": msg / 20}
+    c.close()
+    del U, V, tg
+    # 2D Schnakenberg periodic 4096^2 (cyclic lines, FP64 Sherman-Morrison scalar), FP32 state
+    w = W.schnakenberg_2d(4096, steps=20)
+    c, U = mk(w, "fp32")
+    ms = _timed(lambda: c.run(U, 0.0, 20), stream)
+    out["schnakenberg2d_4096_fp32"] = {"value": w.npoints * w.nspecies * 20 / (ms / 1e3), "unit": UNIT,
+                                       "ms_per_step": ms / 20, "chunk": c.info()["chunk"][:2],
+                                       "staged": c.info()["staged"][:2]}
+    c.close()
+    del U
+    # batched ensemble: 512 Brusselator instances 64^2 .. 512^2, FP32, one launch per sweep
+    from paper_2001_11220_gb300.parallel import aggregate, shard
+    ws_all = W.ensemble(512, steps=20)
+    ws = [ws_all[i] for i in shard(len(ws_all), world, rank)]   # instances are independent: shard by rank
+    with torch.cuda.stream(stream):
+        ens = EtdEnsemble(ws, "fp32", stream=stream)
+        states = [torch.tensor(W.initial_state(x), device="cuda", dtype=torch.float32) for x in ws]
+    barrier()
+    ms = _timed(lambda: ens.run(states, 0.0, 20), stream)
+    units = sum(x.npoints * x.nspecies for x in ws) * 20
+    ms_max, units_all, thr = aggregate(ms, units)
+    out["ensemble512_brusselator_fp32"] = {"value": thr, "unit": UNIT, "ms_per_step": ms_max / 20,
+                                           "instances": len(ws_all), "cell_species": int(units_all) // 20,
+                                           "scaling": "strong (instances sharded across ranks)"}
+    ens.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, timed on the host cores on a bounded
     sample of the same workload (each 'step' = one oracle step of 256^3)."""
@@ -188,6 +267,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -261,11 +341,8 @@ def main():
     with ClockSampler(local) as clk:
         ms, per = timed(ctx, U, K, profile=True)
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * units_per_step * K / (ms_max / 1e3)
+    from paper_2001_11220_gb300.parallel import aggregate, shard
+    ms_max, _, value = aggregate(ms, units_per_step * K)   # max time over ranks, summed work
 
     # per-sweep roofline: dominant kernel = largest total device time
     kinds = ["sweep_first_x", "sweep_middle_y", "sweep_last_z"]
@@ -325,6 +402,9 @@ def main():
     e2e_v = world * units_per_step * args.e2e_steps / float(e2e_t.item())
     state_bytes = info["state_bytes"]
 
+    # ---- further workloads on this GPU (each a few device-timed steps)
+    others = {} if args.no_extra else extra_workloads(EtdRdpIf, W, stream, world, rank, barrier)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = oracle_baseline(w, 1)
@@ -343,6 +423,7 @@ def main():
                         "d2h_bytes_per_step": state_bytes},
                 "gpu_launches": launches, "clocks": clocks}
         line.update(extra)
+        line["workloads"] = others
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
