@@ -73,10 +73,10 @@ __device__ __forceinline__ void reaction_vjp(const SweepArgs<R> &A, const R (&u)
       return;
     case 5: {  // enzyme kinetics + manufactured source
       const R d = R(1) + u[0];
-      out[0] = -yb[0] / (d * d);
+      out[0] = -rdiv(yb[0], d * d);
       if (q != R(0)) {
         const R lf = (R)A.src_lf;
-        pg[0] += (((R)A.rp[1] * lf - R(1)) * q + q / (R(1) + q)) * yb[0];
+        pg[0] += (((R)A.rp[1] * lf - R(1)) * q + rdiv(q, R(1) + q)) * yb[0];
         pg[1] += (R)A.rp[0] * lf * q * yb[0];
       }
       return;
@@ -110,12 +110,14 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
     R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R G = R(0);
+#pragma unroll 8
     for (int j = 0; j < m; ++j) {
       const R f = F[j];
       F[j] = G;
       G = fma(M.chunk[j].x, G, f);
     }
     R X = R(0);
+#pragma unroll 8
     for (int j = m - 1; j >= 0; --j) {
       const typename V4T<R>::T c = M.chunk[j];
       const R y = fma(c.y, F[j], Y[j]);
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       for (int t = 0; t < L; ++t) {
         R u[S], f[S], yb[S], ob[S];
         const R q = qsrc(t);
-        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q)) : R(0);
+        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q)) : R(0);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           u[s] = Us[s][t];
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = xu[s][t];
         const R q = qsrc(t);
-        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q)) : R(0);
+        const R src = (q != R(0)) ? (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q)) : R(0);
         reaction_point<R, S>(A, u, f, src);
 #pragma unroll
         for (int s = 0; s < S; ++s) xf[s][t] = (t < cnt) ? f[s] : R(0);

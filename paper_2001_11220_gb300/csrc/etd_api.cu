@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -111,10 +112,9 @@ static StagePlan stage_plan(const Instance &I, const AxisPlan &P, int nlb, int n
   sp.vec = (!contig && P.st % VW == 0 && nlb % VW == 0) ? 1 : 0;
   sp.off_buf = 0;
   size_t off = align16((size_t)nbuf * nin * te * rb);
-  sp.off_f0 = (unsigned)off;
-  if (P.kind == SWEEP_FIRST) off = align16(off + (size_t)S * te * rb);
+  sp.off_f0 = (unsigned)off;  // unused: F(U_n) stays in registers
   sp.off_out = (unsigned)off;
-  if (contig) off = align16(off + (size_t)3 * S * te * rb);
+  if (contig) off = align16(off + (size_t)(P.kind == SWEEP_LAST ? 1 : 3) * S * te * rb);
   sp.off_sum = (unsigned)off;
   off = align16(off + (size_t)2 * nq * nlb * pitch * rb);
   sp.off_sig = (unsigned)off;
@@ -153,7 +153,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
     if (top < avail && top * 2 <= std::min(cap, max_threads / P.m)) top *= 2;
     // prefer two resident blocks per SM (their exchange phases overlap), then one
     int chosen = 0;
-    if (nlb_force > 0) {
+    if (nlb_force > 0 && !reg_force) {
       if (nlb_force * P.m > max_threads || stage_plan(I, P, nlb_force, 2).bytes > kStageSmemCap) return false;
       chosen = nlb_force;
     }
@@ -173,6 +173,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   }
   if (a == 0) {
     int nlb = pow2_floor(std::min(32, std::max(1, max_threads / P.m)));
+    if (reg_force && nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
     while (nlb > 1 && nlb / 2 >= P.nlines) nlb /= 2;
     P.nlb = nlb;
     P.nlo_blocks = 1;
@@ -182,6 +183,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
     if (nlb >= 32) nlb = (nlb / 32) * 32;
     nlb = (int)std::min<long long>(nlb, ((st + 31) / 32) * 32);
     nlb = std::max(1, nlb);
+    if (reg_force && nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
     P.nlb = nlb;
     P.nlo_blocks = (int)((st + nlb - 1) / nlb);
     const long long nhi = I.N / (st * n);
@@ -212,6 +214,13 @@ static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::
   M.pos = (const typename V4T<R>::T *)arena.put(pos.data(), pos.size() * sizeof(R), err);
   M.sum = (const typename V2T<R>::T *)arena.put(sum.data(), sum.size() * sizeof(R), err);
   M.chunk = (const typename V4T<R>::T *)arena.put(chunk.data(), chunk.size() * sizeof(R), err);
+  std::vector<R> e1(T.e1.begin(), T.e1.end()), v1(T.v1.begin(), T.v1.end()), w1(T.w1.begin(), T.w1.end()),
+      z1(T.z1.begin(), T.z1.end());
+  M.e1 = (const R *)arena.put(e1.data(), e1.size() * sizeof(R), err);
+  M.v1 = (const R *)arena.put(v1.data(), v1.size() * sizeof(R), err);
+  M.w1 = (const R *)arena.put(w1.data(), w1.size() * sizeof(R), err);
+  M.z1 = (const R *)arena.put(z1.data(), z1.size() * sizeof(R), err);
+  M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
   (void)owned;
@@ -382,8 +391,22 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   I.rkind = rx->kind;
   for (int j = 0; j < 8; ++j) I.rp[j] = rx->params[j];
   I.real_bytes = precision == ETD_FP64 ? 8 : 4;
+  // ETD_TILES="L:nlb:staged,..." (one entry per axis) forces tile shapes, e.g.
+  // to reproduce an autotuned configuration in a profiler run
+  const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
     int L = default_chunk(I, a);
+    int fl = 0, fn = 0, fs = 0;
+    if (forced) {
+      const char *p = forced;
+      for (int b = 0; b < a && p; ++b) {
+        p = strchr(p, ',');
+        if (p) ++p;
+      }
+      if (p && sscanf(p, "%d:%d:%d", &fl, &fn, &fs) == 3 && (fl == 4 || fl == 8 || fl == 16) &&
+          plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fs ? fn : 0, !fs))
+        continue;
+    }
     while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
     if (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
       return fail(ctx, ETD_ERR_UNSUPPORTED, "axis %d with n = %lld does not fit one block", a, (long long)I.n[a]);

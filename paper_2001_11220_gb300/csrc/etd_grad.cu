@@ -69,6 +69,13 @@ void upload(DeviceArena &arena, const HostTab &T, MatTab<R> &M, cudaError_t &err
   M.pos = (const typename V4T<R>::T *)arena.put(pos.data(), pos.size() * sizeof(R), err);
   M.sum = (const typename V2T<R>::T *)arena.put(sum.data(), sum.size() * sizeof(R), err);
   M.chunk = (const typename V4T<R>::T *)arena.put(ch.data(), ch.size() * sizeof(R), err);
+  std::vector<R> e1(T.e1.begin(), T.e1.end()), v1(T.v1.begin(), T.v1.end()), w1(T.w1.begin(), T.w1.end()),
+      z1(T.z1.begin(), T.z1.end());
+  M.e1 = (const R *)arena.put(e1.data(), e1.size() * sizeof(R), err);
+  M.v1 = (const R *)arena.put(v1.data(), v1.size() * sizeof(R), err);
+  M.w1 = (const R *)arena.put(w1.data(), w1.size() * sizeof(R), err);
+  M.z1 = (const R *)arena.put(z1.data(), z1.size() * sizeof(R), err);
+  M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
 }

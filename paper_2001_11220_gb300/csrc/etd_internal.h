@@ -41,10 +41,15 @@ template <> struct V2T<double> { using T = double2; };
 //   chunk[j]     = (Aend, kappa, Bst, 0): with a_i = -l_i e_i,
 //                  G_in[j+1] = Aend G_in[j] + F_j;
 //                  X[j] = Y_j + kappa G_in[j] + Bst X[j+1]
+//   e1, v1, w1, z1 [j*L+t]: the same e, v, w, z as separate arrays, read four
+//                  positions at a time in interior chunks (0 < j < m-1), where
+//                  every row has l = u = -r: nl = r, alpha = -r e
 template <typename R> struct MatTab {
   const typename V4T<R>::T *pos;
   const typename V2T<R>::T *sum;
   const typename V4T<R>::T *chunk;
+  const R *e1, *v1, *w1, *z1;
+  double r;       // interior off-diagonal magnitude
   double sm_c;    // v_{p-1} of the Sherman-Morrison rank-one term (periodic)
   double sm_inv;  // 1 / (1 + v.z)                                  (periodic)
 };

@@ -78,6 +78,15 @@ void stage_tab(const HostTab &T, MatTab<R> &M, Carve &cv, std::vector<std::pair<
   M.sum = (const typename V2T<R>::T *)up.back().first;
   up.push_back({cv.take(T.chunk.size() * sizeof(R)), std::vector<R>(T.chunk.begin(), T.chunk.end())});
   M.chunk = (const typename V4T<R>::T *)up.back().first;
+  up.push_back({cv.take(T.e1.size() * sizeof(R)), std::vector<R>(T.e1.begin(), T.e1.end())});
+  M.e1 = (const R *)up.back().first;
+  up.push_back({cv.take(T.v1.size() * sizeof(R)), std::vector<R>(T.v1.begin(), T.v1.end())});
+  M.v1 = (const R *)up.back().first;
+  up.push_back({cv.take(T.w1.size() * sizeof(R)), std::vector<R>(T.w1.begin(), T.w1.end())});
+  M.w1 = (const R *)up.back().first;
+  up.push_back({cv.take(T.z1.size() * sizeof(R)), std::vector<R>(T.z1.begin(), T.z1.end())});
+  M.z1 = (const R *)up.back().first;
+  M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
 }

@@ -33,6 +33,11 @@ namespace etd {
 template <typename R>
 __device__ __forceinline__ R ld_nc(const R *p) { return __ldg(p); }
 
+// a / b in the reactions: IEEE division in FP64; the hardware fast divide
+// (a few ulp) in FP32, whose arithmetic error budget is far larger
+__device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+
 // ---------------------------------------------------------------- reaction
 
 template <typename R, int S>
@@ -70,7 +75,7 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
       }
       break;
     case 5:  // enzyme kinetics (Section 8.1) plus the manufactured source
-      f[0] = -u[0] / (R(1) + u[0]) + src;
+      f[0] = -rdiv(u[0], R(1) + u[0]) + src;
 #pragma unroll
       for (int s = 1; s < S; ++s) f[s] = R(0);
       return;
@@ -90,7 +95,26 @@ __device__ __forceinline__ R mms_source(const SweepArgs<R> &A, long long pidx, d
   const long long z = r / A.ny;
   R q = (R)exp_mt * A.phi[0][x] * A.phi[1][y];
   if (A.phi[2]) q *= A.phi[2][z];
-  return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + q / (R(1) + q));
+  return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q));
+}
+
+// e^{-t} prod_{b != axis} sin(pi x_b / L_b) for one line: x axis line index
+// (y + z ny), strided axes (lo, hi) line coordinates; 0 without a source
+template <typename R>
+__device__ __forceinline__ R line_source_base(const SweepArgs<R> &A, bool contig, long long line, long long lo,
+                                              long long hi, double exp_mt) {
+  if (A.phi[0] == nullptr) return R(0);
+  R q = (R)exp_mt;
+  if (contig) {
+    q *= A.phi[1][line % A.ny];
+    if (A.phi[2]) q *= A.phi[2][line / A.ny];
+  } else if (A.axis == 1) {  // lo = x, hi = z
+    q *= A.phi[0][lo];
+    if (A.phi[2]) q *= A.phi[2][hi];
+  } else {  // axis 2: lo = x + y nx
+    q *= A.phi[0][lo % A.nx] * A.phi[1][lo / A.nx];
+  }
+  return q;
 }
 
 // ------------------------------------------------------------ chunk loads
@@ -146,12 +170,51 @@ __device__ __forceinline__ void store_chunk(const R (&v)[L], R *__restrict__ p, 
     if (t < cnt) p[off + (long long)t * st] = v[t];
 }
 
+
+// ------------------------------------------- interior chunks, FP32 fast path
+// In chunks 0 < j < m-1 every row has l = u = -r, so the forward multiplier
+// is the constant r and alpha = -r e: only e (and v, w, z) vary per position,
+// read four positions per load.  Edge chunks (Neumann rows, padding) and FP64
+// use the exact per-position tables.
+template <typename R>
+__device__ __forceinline__ bool interior_chunk(const MatTab<R> &M, int j, int m) {
+  if constexpr (sizeof(R) == 4) return j > 0 && j < m - 1 && M.e1 != nullptr;
+  else return false;
+}
+
+template <int L>
+__device__ __forceinline__ void load_row4(const float *__restrict__ p, float (&a)[L]) {
+#pragma unroll
+  for (int t = 0; t < L; t += 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p + t));
+    a[t] = v.x;
+    a[t + 1] = v.y;
+    a[t + 2] = v.z;
+    a[t + 3] = v.w;
+  }
+}
+
 // ------------------------------------------------------ pass 1 / pass 2
 
 // chunk summaries of one RHS against one matrix
 template <typename R, int L>
 __device__ __forceinline__ void pass1(const MatTab<R> &M, int m, int j, const R (&b)[L], R &F, R &Y) {
   R f = R(0), y = R(0);
+  if constexpr (sizeof(R) == 4 && L % 4 == 0) {
+    if (interior_chunk(M, j, m)) {
+      float v[L], w[L];
+      load_row4<L>(M.v1 + j * L, v);
+      load_row4<L>(M.w1 + j * L, w);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        f = fmaf(v[t], b[t], f);
+        y = fmaf(w[t], b[t], y);
+      }
+      F = f;
+      Y = y;
+      return;
+    }
+  }
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const typename V2T<R>::T vw = M.sum[j * L + t];
@@ -167,6 +230,22 @@ template <typename R, int L>
 __device__ __forceinline__ void pass1x2(const MatTab<R> &M, int m, int j, const R (&b0)[L], const R (&b1)[L],
                                         R &F0, R &Y0, R &F1, R &Y1) {
   R f0 = R(0), y0 = R(0), f1 = R(0), y1 = R(0);
+  if constexpr (sizeof(R) == 4 && L % 4 == 0) {
+    if (interior_chunk(M, j, m)) {
+      float v[L], w[L];
+      load_row4<L>(M.v1 + j * L, v);
+      load_row4<L>(M.w1 + j * L, w);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        f0 = fmaf(v[t], b0[t], f0);
+        y0 = fmaf(w[t], b0[t], y0);
+        f1 = fmaf(v[t], b1[t], f1);
+        y1 = fmaf(w[t], b1[t], y1);
+      }
+      F0 = f0; Y0 = y0; F1 = f1; Y1 = y1;
+      return;
+    }
+  }
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const typename V2T<R>::T vw = M.sum[j * L + t];
@@ -184,6 +263,36 @@ __device__ __forceinline__ void pass1x2(const MatTab<R> &M, int m, int j, const 
 template <typename R, int L>
 __device__ __forceinline__ void pass2(const MatTab<R> &M, int m, int j, const R (&b)[L], R Gin, R Xr, R sig,
                                       R (&x)[L]) {
+  if constexpr (sizeof(R) == 4 && L % 4 == 0) {
+    if (interior_chunk(M, j, m)) {
+      float e[L];
+      load_row4<L>(M.e1 + j * L, e);
+      const float r = (float)M.r;
+      float g = Gin;
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        g = fmaf(r, g, b[t]) * e[t];
+        x[t] = g;
+      }
+      float xn = Xr;
+      if (sig != 0.f) {
+        float z[L];
+        load_row4<L>(M.z1 + j * L, z);
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+          xn = fmaf(r * e[t], xn, x[t]);
+          x[t] = fmaf(-sig, z[t], xn);
+        }
+      } else {
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+          xn = fmaf(r * e[t], xn, x[t]);
+          x[t] = xn;
+        }
+      }
+      return;
+    }
+  }
   R g = Gin;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
@@ -229,12 +338,14 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, 
     R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R G = R(0);
+#pragma unroll 8
     for (int j = 0; j < m; ++j) {
       const R f = F[j];
       F[j] = G;
       G = fma(M.chunk[j].x, G, f);
     }
     R X = R(0);
+#pragma unroll 8
     for (int j = m - 1; j >= 0; --j) {
       const typename V4T<R>::T c = M.chunk[j];
       const R y = fma(c.y, F[j], Y[j]);
@@ -248,40 +359,38 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, 
 
 // -------------------------------------------------------------- the sweep
 
-template <typename R, int S, int L, bool CONTIG, int KIND>
-__device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
-                                            double exp_mt) {
+// What one thread knows about its chunk of one line.
+template <typename R>
+struct ChunkPos {
+  int l, j;      // line within the block/tile, chunk index
+  int i0, cnt;   // first position of the chunk, positions inside the line
+  bool thr_ok;   // the thread owns a chunk (false for padding threads)
+  R qbase;       // manufactured-source factor of the line (0: none)
+};
+
+// One fused sweep of one block on register-resident chunks.  load(f, s, v)
+// fills v with input field f (FIRST: 0 = U_n; MIDDLE/LAST: 0 = c_U, 1 = c_f,
+// 2 = w) of species s, zero past the end of the line; store(f, s, v) writes
+// output field f (FIRST/MIDDLE: c_U, c_f, w; LAST: 0 = U_{n+1}).  exch is the
+// block's exchange space (chunk summaries, carries, Sherman-Morrison scalars).
+template <typename R, int S, int L, int KIND, typename LoadF, typename StoreF>
+__device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPos<R> &c, unsigned char *exch,
+                                            LoadF load, StoreF store) {
   constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
-  const int tid = threadIdx.x;
-  // threads past nlb*m (batched launches size blocks for the largest
-  // instance) own no chunk but still take part in every barrier and scan
-  const bool thr_ok = tid < nlb * m;
-  // lanes walk neighbouring lines on every axis: table reads are warp broadcasts
-  int l = tid % nlb, j = tid / nlb;
-  if (!thr_ok) { l = 0; j = 0; }
-  long long base;
-  bool line_ok;
-  if constexpr (CONTIG) {
-    const long long line = (long long)bid * nlb + l;
-    line_ok = thr_ok && line < A.nlines;
-    base = line * A.n;
-  } else {
-    const long long lo = (long long)(bid % A.nlo_blocks) * nlb + l;
-    const long long hi = bid / A.nlo_blocks;
-    line_ok = thr_ok && lo < A.st;
-    base = lo + hi * A.st * A.n;
-  }
-  const long long st = CONTIG ? 1 : A.st;
-  const int i0 = j * L;
-  const int cnt = line_ok ? max(0, min(L, A.n - i0)) : 0;
-  const long long off0 = base + (long long)i0 * st;
-  const long long N = A.N;
+  const int l = c.l, j = c.j, cnt = c.cnt, i0 = c.i0;
+  const bool thr_ok = c.thr_ok;
   const bool periodic = A.mat[0][0].sm_inv != 0.0;
-
-  R *sF = reinterpret_cast<R *>(smem);
+  const R qbase = c.qbase;
+  const R *phia = A.phi[A.axis];
+  auto src_at = [&](int t) -> R {  // manufactured source at position t of the chunk
+    if (qbase == R(0) || t >= cnt) return R(0);
+    const R q = qbase * phia[i0 + t];
+    return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q));
+  };
+  R *sF = reinterpret_cast<R *>(exch);
   R *sY = sF + (size_t)NQ * nlb * pitch;
-  double *sSig = reinterpret_cast<double *>(smem + ((2 * (size_t)NQ * nlb * pitch * sizeof(R) + 15) & ~(size_t)15));
+  double *sSig = reinterpret_cast<double *>(exch + ((2 * (size_t)NQ * nlb * pitch * sizeof(R) + 15) & ~(size_t)15));
   const size_t myidx = (size_t)l * pitch + j;
   auto put = [&](int q, R F, R Y) {
     if (thr_ok) {
@@ -299,17 +408,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
   if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
     R cu[S][L], cf[S][L], w[S][L];
     if constexpr (KIND == SWEEP_FIRST) {
-      // U_n, F(U_n, t_n); w* = U_n + k F(U_n) is formed on the fly
+      // U_n, F(U_n, t_n), w* = U_n + k F(U_n)
 #pragma unroll
-      for (int s = 0; s < S; ++s) load_chunk<R, L, CONTIG>(cu[s], A.in[0] + s * N, off0, st, cnt);
+      for (int s = 0; s < S; ++s) load(0, s, cu[s]);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         R u[S], f[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = cu[s][t];
-        R src = R(0);
-        if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st, exp_mt);
-        reaction_point<R, S>(A, u, f, src);
+        reaction_point<R, S>(A, u, f, src_at(t));
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           cf[s][t] = (t < cnt) ? f[s] : R(0);
@@ -319,9 +426,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     } else {
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        load_chunk<R, L, CONTIG>(cu[s], A.in[0] + s * N, off0, st, cnt);
-        load_chunk<R, L, CONTIG>(cf[s], A.in[1] + s * N, off0, st, cnt);
-        load_chunk<R, L, CONTIG>(w[s], A.in[2] + s * N, off0, st, cnt);
+        load(0, s, cu[s]);
+        load(1, s, cf[s]);
+        load(2, s, w[s]);
       }
     }
     // pass 1: five solves per species share one exchange
@@ -350,26 +457,26 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
       pass2<R, L>(A.mat[s][2], m, j, cu[s], G, X, sg, xb);
 #pragma unroll
       for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
-      store_chunk<R, L, CONTIG>(xa, A.out[0] + s * N, off0, st, cnt);
+      store(0, s, xa);
       carries(5 * s + 2, G, X, sg);
       pass2<R, L>(A.mat[s][1], m, j, cf[s], G, X, sg, xa);
       carries(5 * s + 3, G, X, sg);
       pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
 #pragma unroll
       for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
-      store_chunk<R, L, CONTIG>(xa, A.out[1] + s * N, off0, st, cnt);
+      store(1, s, xa);
       carries(5 * s + 4, G, X, sg);
       pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, xa);
-      store_chunk<R, L, CONTIG>(xa, A.out[2] + s * N, off0, st, cnt);
+      store(2, s, xa);
     }
   } else {
     // LAST: phase A  U* = P_d w ; phase B  U_{n+1} = T_d f1 - S_d f2
     R cu[S][L], cf[S][L], w[S][L];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      load_chunk<R, L, CONTIG>(cu[s], A.in[0] + s * N, off0, st, cnt);
-      load_chunk<R, L, CONTIG>(cf[s], A.in[1] + s * N, off0, st, cnt);
-      load_chunk<R, L, CONTIG>(w[s], A.in[2] + s * N, off0, st, cnt);
+      load(0, s, cu[s]);
+      load(1, s, cf[s]);
+      load(2, s, w[s]);
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -395,9 +502,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
       R u[S], f[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) u[s] = w[s][t];
-      R src = R(0);
-      if (A.phi[0] != nullptr && t < cnt) src = mms_source(A, off0 + (long long)t * st, exp_mt);
-      reaction_point<R, S>(A, u, f, src);
+      reaction_point<R, S>(A, u, f, src_at(t));
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const R fs = (t < cnt) ? f[s] : R(0);
@@ -426,9 +531,52 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
       pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
 #pragma unroll
       for (int t = 0; t < L; ++t) xa[t] -= xb[t];
-      store_chunk<R, L, CONTIG>(xa, A.out[0] + s * N, off0, st, cnt);
+      store(0, s, xa);
     }
   }
+}
+
+// Register kernel: one block per group of nlb lines, inputs loaded straight
+// from global memory (vector loads on x, coalesced row segments on strided axes).
+template <typename R, int S, int L, bool CONTIG, int KIND>
+__device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
+                                            double exp_mt) {
+  (void)t_eval;
+  const int m = A.m, nlb = A.nlb;
+  const int tid = threadIdx.x;
+  // threads past nlb*m (batched launches size blocks for the largest
+  // instance) own no chunk but still take part in every barrier and scan
+  const bool thr_ok = tid < nlb * m;
+  // lanes walk neighbouring lines on every axis: table reads are warp broadcasts
+  int l = tid % nlb, j = tid / nlb;
+  if (!thr_ok) { l = 0; j = 0; }
+  long long base;
+  bool line_ok;
+  ChunkPos<R> c;
+  if constexpr (CONTIG) {
+    const long long line = (long long)bid * nlb + l;
+    line_ok = thr_ok && line < A.nlines;
+    base = line * A.n;
+    c.qbase = line_ok ? line_source_base(A, true, line, 0, 0, exp_mt) : R(0);
+  } else {
+    const long long lo = (long long)(bid % A.nlo_blocks) * nlb + l;
+    const long long hi = bid / A.nlo_blocks;
+    line_ok = thr_ok && lo < A.st;
+    base = lo + hi * A.st * A.n;
+    c.qbase = line_ok ? line_source_base(A, false, 0, lo, hi, exp_mt) : R(0);
+  }
+  const long long st = CONTIG ? 1 : A.st;
+  c.l = l;
+  c.j = j;
+  c.i0 = j * L;
+  c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
+  c.thr_ok = thr_ok;
+  const long long off0 = base + (long long)c.i0 * st;
+  const long long N = A.N;
+  const int cnt = c.cnt;
+  auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG>(v, A.in[f] + s * N, off0, st, cnt); };
+  auto store = [&](int f, int s, const R (&v)[L]) { store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt); };
+  chunk_sweep<R, S, L, KIND>(A, c, smem, load, store);
 }
 
 template <typename R, int S, int L, bool CONTIG, int KIND>

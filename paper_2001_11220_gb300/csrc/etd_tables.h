@@ -16,6 +16,10 @@ enum { BC_DIRICHLET = 0, BC_NEUMANN = 1, BC_PERIODIC = 2 };
 struct HostTab {
   int p = 0, L = 0, m = 0;
   std::vector<double> pos, sum, chunk;
+  // interior-chunk arrays (chunk-major, one value per position): pivot
+  // reciprocal e, summary weights v and w, Sherman-Morrison vector z
+  std::vector<double> e1, v1, w1, z1;
+  double r = 0.0;  // interior off-diagonal magnitude: l_i = u_i = -r
   double sm_c = 0.0, sm_inv = 0.0;
 };
 
@@ -90,6 +94,11 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
   T.pos.assign((size_t)4 * L * m, 0.0);
   T.sum.assign((size_t)2 * L * m, 0.0);
   T.chunk.assign((size_t)4 * m, 0.0);
+  T.e1.assign((size_t)L * m, 1.0);
+  T.v1.assign((size_t)L * m, 0.0);
+  T.w1.assign((size_t)L * m, 0.0);
+  T.z1.assign((size_t)L * m, 0.0);
+  T.r = r;
   std::vector<double> ca(L), ce(L), cal(L), cnl(L), A(L), V(L), Wt(L), Sx(L);
   for (int j = 0; j < m; ++j) {
     const int tl = std::min(L, p - j * L) - 1;  // last real position of the chunk
@@ -105,6 +114,8 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
       T.pos[4 * q + 1] = ce[t];
       T.pos[4 * q + 2] = cal[t];
       T.pos[4 * q + 3] = real ? z[i] : 0.0;
+      T.e1[q] = ce[t];
+      T.z1[q] = real ? z[i] : 0.0;
     }
     // A_t = prod_{r<=t} a_r ; W_t = prod_{r<t} (-alpha_r)
     double acc = 1.0;
@@ -126,6 +137,8 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
       const size_t q = (size_t)j * L + t;
       T.sum[2 * q + 0] = ce[t] * V[t];
       T.sum[2 * q + 1] = ce[t] * Sx[t];
+      T.v1[q] = ce[t] * V[t];
+      T.w1[q] = ce[t] * Sx[t];
     }
     T.chunk[4 * j + 0] = A[tl];
     T.chunk[4 * j + 1] = kap;

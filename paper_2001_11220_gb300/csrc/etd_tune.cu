@@ -69,12 +69,13 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       const int L = I.real_bytes == 4 ? Ls32[li] : Ls64[li];
       for (int nlb : nlbs) cands.push_back({L, nlb, false});
       cands.push_back({L, 0, true});
+      for (int nlb : {8, 16}) cands.push_back({L, nlb, true});
     }
     const AxisPlan keep = I.plan[a];
     double best = 1e30;
     Cand pick{keep.L, keep.sp.staged ? keep.nlb : 0, !keep.sp.staged};
     for (const Cand &c : cands) {
-      if (!plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.reg ? 0 : c.nlb, c.reg)) continue;
+      if (!plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg)) continue;
       if (c.reg && I.plan[a].sp.staged) continue;
       etd_status st = build_axis_tables(ctx, I, a);
       if (st != ETD_OK) return st;
@@ -89,7 +90,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
         pick = c;
       }
     }
-    if (!plan_axis_ex(I, a, pick.L, ETD_MAX_BLOCK_THREADS, pick.reg ? 0 : pick.nlb, pick.reg))
+    if (!plan_axis_ex(I, a, pick.L, ETD_MAX_BLOCK_THREADS, pick.nlb, pick.reg))
       return fail(ctx, ETD_ERR_CUDA, "autotune: best candidate of axis %d no longer plans", a);
     etd_status st = build_axis_tables(ctx, I, a);
     if (st != ETD_OK) return st;
