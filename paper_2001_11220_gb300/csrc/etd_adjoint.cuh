@@ -103,6 +103,10 @@ template <typename R, typename GetMat>
 __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
                                             GetMat mat) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  if (m > 32) {
+    scan_lines_warp<R>(A, sF, sY, sSig, q0, nq, mat);
+    return;
+  }
   for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
     const int l = u % nlb;
     const int q = q0 + u / nlb;

@@ -325,10 +325,93 @@ __device__ __forceinline__ void solve_matrix(int q, int &s, int &g) {
   }
 }
 
+
+// Long lines (m > 32 chunks): one warp per (line, solve).  Each lane composes
+// the affine chunk maps of a contiguous block of chunks, a shuffle scan over
+// the lanes gives every block its carries, and the lane re-walks its block to
+// emit G_in[j] and X[j+1] (forward map G -> Aend G + F, backward map
+// X -> Bst X + Y + kappa G_in).
+template <typename R, typename GetMat>
+__device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
+                                                GetMat mat) {
+  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  // full warps only: a trailing partial warp (blockDim not a multiple of 32) stays out of the shuffles
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp >= nw) return;
+  const int per = (m + 31) >> 5;
+  const int j0 = min(lane * per, m), j1 = min(j0 + per, m);
+  for (int u = warp; u < nlb * nq; u += nw) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    const MatTab<R> &M = mat(q);
+    R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    // forward: block map G_out = a G_in + b
+    R a = R(1), b = R(0);
+    for (int jj = j0; jj < j1; ++jj) {
+      const R Aj = M.chunk[jj].x;
+      b = fma(Aj, b, F[jj]);
+      a *= Aj;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R ap = __shfl_up_sync(0xffffffffu, a, off), bp = __shfl_up_sync(0xffffffffu, b, off);
+      if (lane >= off) {
+        b = fma(a, bp, b);
+        a *= ap;
+      }
+    }
+    R G = __shfl_up_sync(0xffffffffu, b, 1);
+    if (lane == 0) G = R(0);
+    const R Gtot = __shfl_sync(0xffffffffu, b, 31);  // forward value at the last position
+    for (int jj = j0; jj < j1; ++jj) {
+      const typename V4T<R>::T c = M.chunk[jj];
+      const R f = F[jj];
+      F[jj] = G;
+      Y[jj] = fma(c.y, G, Y[jj]);
+      G = fma(c.x, G, f);
+    }
+    // backward: block map X_out = a X_in + b, composed from the right
+    a = R(1);
+    b = R(0);
+    for (int jj = j1 - 1; jj >= j0; --jj) {
+      const R Bj = M.chunk[jj].z;
+      b = fma(Bj, b, Y[jj]);
+      a *= Bj;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R an = __shfl_down_sync(0xffffffffu, a, off), bn = __shfl_down_sync(0xffffffffu, b, off);
+      if (lane + off < 32) {
+        b = fma(a, bn, b);
+        a *= an;
+      }
+    }
+    R X = __shfl_down_sync(0xffffffffu, b, 1);
+    if (lane == 31) X = R(0);
+    for (int jj = j1 - 1; jj >= j0; --jj) {
+      const R yv = Y[jj];
+      Y[jj] = X;
+      X = fma(M.chunk[jj].z, X, yv);
+    }
+    const R X0 = __shfl_sync(0xffffffffu, X, 0);  // first position of the line
+    if (lane == 0)
+      sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X0 + M.sm_c * (double)Gtot) * M.sm_inv : 0.0;
+  }
+}
+
 template <typename R, int S, int KIND>
 __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
                                            bool periodic) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  if (m > 32) {
+    scan_lines_warp<R>(A, sF, sY, sSig, q0, nq, [&](int q) -> const MatTab<R> & {
+      int ms, mg;
+      solve_matrix<R, S, KIND>(q, ms, mg);
+      return A.mat[ms][mg];
+    });
+    return;
+  }
   for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
     const int l = u % nlb;
     const int q = q0 + u / nlb;
