@@ -49,20 +49,25 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# sources that compile into the forward sweep kernels (their DRAM traffic
+# depends on nothing else but the tile shapes, recorded beside each entry)
+SWEEP_SOURCES = ("etd_internal.h", "etd_tables.h", "etd_sweep.cuh", "etd_sweep_smem.cuh", "etd_sweep_launch.cuh",
+                 "etd_sweep_f32.cu", "etd_sweep_f64.cu")
+
+
 def _csrc_hash() -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2001_11220_gb300", "csrc")
-    for fn in sorted(os.listdir(cs)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(cs, fn), "rb") as f:
-                h.update(fn.encode())
-                h.update(f.read())
+    for fn in SWEEP_SOURCES:
+        with open(os.path.join(cs, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, workload: str):
+def _traffic(kernel: str, workload: str, tiles: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel sources changed since it was captured."""
+    kernel sources or the tile shapes changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -70,7 +75,7 @@ def _traffic(kernel: str, workload: str):
     except Exception:
         return None
     ent = tab.get(workload, {}).get(kernel)
-    if not ent or ent.get("csrc_hash") != _csrc_hash():
+    if not ent or ent.get("csrc_hash") != _csrc_hash() or ent.get("tiles") != tiles:
         return None
     return float(ent["dram_bytes_per_launch"])
 
@@ -338,6 +343,9 @@ def main():
         ctx.autotune(Wk)                      # tile shapes timed per axis on a scratch state
         del Wk
     info = ctx.info()
+    # tile shapes per axis in the ETD_TILES format (L:lines:staged:pack), to reproduce in a profiler run
+    tiles = ",".join(f"{info['chunk'][a]}:{info['lines_per_block'][a]}:{info['staged'][a]}:{info['pack'][a]}"
+                     for a in range(w.dim))
     with ClockSampler(local) as clk:
         ms, per = timed(ctx, U, K, profile=True)
     clocks = clk.summary()
@@ -355,7 +363,7 @@ def main():
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_src = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(kinds[dom], f"mms3d_{P_BENCH}_{args.precision}"),
+            "traffic": _traffic(kinds[dom], f"mms3d_{P_BENCH}_{args.precision}", tiles),
             "kernel": kinds[dom], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": alg_bytes,
             "per_sweep_ms": {kinds[i]: sweep_ms[i] / max(1, sweep_launches[i]) for i in range(3)},
@@ -417,7 +425,7 @@ def main():
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": dict(workload_desc(w, args.precision), parallelism="replicas" if world > 1 else "single",
                                chunk=info["chunk"][:3], lines_per_block=info["lines_per_block"][:3],
-                               staged=info["staged"][:3], autotuned=not args.no_autotune),
+                               staged=info["staged"][:3], tiles=tiles, autotuned=not args.no_autotune),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes},

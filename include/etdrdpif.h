@@ -105,7 +105,10 @@ typedef struct {
   int32_t launches_per_step;     /* kernels one etd_step enqueues */
   int32_t chunk[3];              /* chunk length per axis (elements per thread) */
   int32_t lines_per_block[3];    /* lines per tile / block per axis */
-  int32_t staged[3];             /* 1: persistent shared-memory-staged kernel, 0: register kernel */
+  int32_t staged[3];             /* 0: register kernel, 1: persistent shared-memory-staged kernel,
+                                    2: FP32 tile kernel (lines_per_block then counts line units) */
+  int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
+                                    (lines_per_block then counts pairs), 1: one line per thread */
 } etd_info;
 
 /* Create a context for one problem.  Validates every argument
@@ -123,6 +126,10 @@ etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction 
 /* One ETD-RDP-IF step in place: U (device, layout above) holds U_n at time
  * t_n on entry and U_{n+1} on return (stream-ordered). */
 etd_status etd_step(etd_ctx *ctx, void *U, double t_n);
+/* State pointers (U, U0, targets) must be 16-byte aligned when an axis runs
+ * an FP32 tile kernel (etd_info.staged == 2; only after etd_autotune or an
+ * ETD_TILES override): ETD_ERR_INVALID_ARG otherwise.  cudaMalloc and torch
+ * allocations are. */
 
 /* nsteps steps from time t0, in place on device U. */
 etd_status etd_run(etd_ctx *ctx, void *U, double t0, int64_t nsteps);

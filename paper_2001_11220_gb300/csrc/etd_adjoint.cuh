@@ -104,7 +104,7 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
                                             GetMat mat) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   if (m > 32) {
-    scan_lines_warp<R>(A, sF, sY, sSig, q0, nq, mat);
+    scan_lines_warp<R, R, 1, double>(A, sF, sY, sSig, q0, nq, mat);
     return;
   }
   for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
@@ -113,21 +113,8 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
     const MatTab<R> &M = mat(q);
     R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    R G = R(0);
-#pragma unroll 8
-    for (int j = 0; j < m; ++j) {
-      const R f = F[j];
-      F[j] = G;
-      G = fma(M.chunk[j].x, G, f);
-    }
-    R X = R(0);
-#pragma unroll 8
-    for (int j = m - 1; j >= 0; --j) {
-      const typename V4T<R>::T c = M.chunk[j];
-      const R y = fma(c.y, F[j], Y[j]);
-      Y[j] = X;
-      X = fma(c.z, X, y);
-    }
+    R G, X;
+    chain_line<R, R>(M, F, Y, m, G, X);
     sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X + M.sm_c * (double)G) * M.sm_inv : 0.0;
   }
 }

@@ -132,7 +132,7 @@ static const size_t kStageSmemHalf = 110 * 1024;     // two blocks per SM
 // short enough to stage go to the persistent double-buffered kernel; longer
 // ones to the register kernel.  nlb_force > 0 asks for the staged kernel with
 // that many lines per tile, reg_force for the register kernel (autotuning).
-bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force) {
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force, int pack) {
   AxisPlan &P = I.plan[a];
   const long long n = I.n[a];
   P.L = L;
@@ -144,6 +144,25 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   P.st = st;
   P.nlines = I.N / n;
   P.pitch = pick_pitch(P.m);
+  P.pk = 1;
+  if (pack == 2) {
+    // register kernel on line pairs (lo, lo + 1) of a strided FP32 axis with an even stride
+    if (I.real_bytes != 4 || a == 0 || st % 2 != 0 || L != 8) return false;
+    const long long npairs = st / 2;
+    int nlb = std::max(1, max_threads / P.m);
+    if (nlb >= 32) nlb = (nlb / 32) * 32;
+    nlb = (int)std::min<long long>(nlb, ((npairs + 31) / 32) * 32);
+    nlb = std::max(1, nlb);
+    if (nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
+    P.pk = 2;
+    P.sp = StagePlan{};
+    P.nlb = nlb;
+    P.nlo_blocks = (int)((npairs + nlb - 1) / nlb);
+    P.nblocks = (int)(P.nlo_blocks * (I.N / (st * n)));
+    P.nthreads = nlb * P.m;
+    P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 2);
+    return P.smem <= 200 * 1024;
+  }
   // staged plan: largest power-of-two lines per tile that fits with double buffering
   P.sp = StagePlan{};
   {
@@ -194,7 +213,75 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   return P.smem <= 200 * 1024;
 }
 
-bool plan_axis(Instance &I, int a, int L, int max_threads) { return plan_axis_ex(I, a, L, max_threads, 0, false); }
+bool plan_axis(Instance &I, int a, int L, int max_threads) { return plan_axis_ex(I, a, L, max_threads, 0, false, 1); }
+
+// FP32 tile kernel: NLB lines per block (NLB / pk line units of L-position
+// chunks), every input field of the block's lines staged in shared memory
+// with 16-byte copies (strided axes: stride a multiple of 4 elements; x axis:
+// line length a multiple of 4)
+bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
+  AxisPlan &P = I.plan[a];
+  const long long n = I.n[a];
+  if (I.real_bytes != 4 || (L != 8 && L != 16) || (NLB != 16 && NLB != 32) || (pk != 1 && pk != 2)) return false;
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  const bool contig = (a == 0);
+  if (contig ? (n % 4 != 0 || pk != 1) : (st % 4 != 0)) return false;
+  const int m = (int)((n + L - 1) / L);
+  const int W = NLB / pk;
+  if ((long long)W * m > 512) return false;
+  P.L = L;
+  P.m = m;
+  P.kind = contig ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
+  P.st = st;
+  P.nlines = I.N / n;
+  P.pitch = pick_pitch(m);
+  P.pk = pk;
+  const int S = I.S, nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
+  StagePlan sp{};
+  sp.staged = 2;
+  const long long mL = (long long)m * L;
+  long long ft;
+  if (contig) {
+    sp.tile_pitch = (int)(((mL + 31) / 32) * 32 + 4);  // 4 (mod 32): conflict-free 16-byte reads
+    ft = (long long)NLB * sp.tile_pitch;
+  } else {
+    const int padj = (W < 32) ? NLB : 0;
+    ft = (long long)m * (L * NLB + padj);
+  }
+  ft = (ft + 3) & ~3LL;
+  sp.tile_elems = (int)ft;
+  sp.nin = contig ? S : 3 * S;
+  sp.nbuf = 1;
+  sp.vec = 1;
+  size_t off = align16((size_t)3 * S * ft * 4);
+  sp.off_sum = (unsigned)off;
+  off = align16(off + (size_t)2 * nq * W * P.pitch * 4 * pk);
+  sp.off_sig = (unsigned)off;
+  off += (size_t)nq * W * pk * sizeof(double);
+  sp.bytes = (unsigned)off;
+  if (sp.bytes > 227 * 1024) return false;
+  P.nlb = W;
+  P.nthreads = W * m;
+  P.smem = sp.bytes;
+  if (contig) {
+    P.nlo_blocks = 1;
+    P.nblocks = (int)((P.nlines + NLB - 1) / NLB);
+  } else {
+    P.nlo_blocks = (int)((st + NLB - 1) / NLB);
+    P.nblocks = (int)(P.nlo_blocks * (I.N / (st * n)));
+  }
+  sp.ntiles = P.nblocks;
+  P.sp = sp;
+  return true;
+}
+
+// tile kernels move U with 16-byte copies
+bool needs_aligned_state(const Instance &I) {
+  for (int a = 0; a < I.dim; ++a)
+    if (I.plan[a].sp.staged == 2) return true;
+  return false;
+}
 
 int default_chunk(const Instance &I, int a) {
   // staged kernels: 16 positions per thread (FP32) keeps the per-line chain of
@@ -220,6 +307,16 @@ static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::
   M.v1 = (const R *)arena.put(v1.data(), v1.size() * sizeof(R), err);
   M.w1 = (const R *)arena.put(w1.data(), w1.size() * sizeof(R), err);
   M.z1 = (const R *)arena.put(z1.data(), z1.size() * sizeof(R), err);
+  M.rows1 = nullptr;
+  M.rows2 = nullptr;
+  if constexpr (sizeof(R) == 4) {
+    // FP32 coefficient rows, and the same rows with each value in both lanes for line pairs
+    const std::vector<float> r1 = fp32_rows(T);
+    std::vector<float> r2(2 * r1.size());
+    for (size_t q = 0; q < r1.size(); ++q) r2[2 * q] = r2[2 * q + 1] = r1[q];
+    M.rows1 = (const float *)arena.put(r1.data(), r1.size() * sizeof(float), err);
+    M.rows2 = (const float2 *)arena.put(r2.data(), r2.size() * sizeof(float), err);
+  }
   M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
@@ -301,13 +398,19 @@ void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
       else A.mat[s][g] = I.tab32[transpose][a][s][g];
     }
   A.k = I.k;
+  A.kR = (R)I.k;
   A.rkind = I.rkind;
-  for (int j = 0; j < 8; ++j) A.rp[j] = I.rp[j];
+  for (int j = 0; j < 8; ++j) {
+    A.rp[j] = I.rp[j];
+    A.rpR[j] = (R)I.rp[j];
+  }
   for (int b = 0; b < 3; ++b) A.phi[b] = (const R *)I.phi[b];
   A.nx = (int)I.n[0];
   A.ny = (int)I.n[1];
   A.src_lf = I.src_lf;
+  A.src_lfR = (R)I.src_lf;
   A.axis = a;
+  A.pk = P.pk;
   A.sp = P.sp;
 }
 template void fill_args<float>(const Instance &, int, int, SweepArgs<float> &);
@@ -338,6 +441,7 @@ cudaError_t prof_end(etd_ctx *ctx, cudaStream_t s, int kind, cudaEvent_t ev0) {
 
 template <typename R>
 static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t s, etd_ctx *prof) {
+  if (needs_aligned_state(I) && (reinterpret_cast<uintptr_t>(U) & 15)) return cudaErrorMisalignedAddress;
   R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
   for (int a = 0; a < I.dim; ++a) {
     const AxisPlan &P = I.plan[a];
@@ -357,6 +461,7 @@ static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t
       A.t_eval = t + I.k;
     }
     A.exp_mt = std::exp(-A.t_eval);
+    A.exp_mtR = (R)A.exp_mt;
     cudaEvent_t ev0;
     cudaError_t e = prof_begin(prof, s, ev0);
     if (e != cudaSuccess) return e;
@@ -391,21 +496,24 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   I.rkind = rx->kind;
   for (int j = 0; j < 8; ++j) I.rp[j] = rx->params[j];
   I.real_bytes = precision == ETD_FP64 ? 8 : 4;
-  // ETD_TILES="L:nlb:staged,..." (one entry per axis) forces tile shapes, e.g.
-  // to reproduce an autotuned configuration in a profiler run
+  // ETD_TILES="L:nlb:kernel[:pack],..." (one entry per axis; kernel 0
+  // register, 1 staged, 2 tile with nlb lines per block) forces tile shapes,
+  // e.g. to reproduce an autotuned configuration in a profiler run
   const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
     int L = default_chunk(I, a);
-    int fl = 0, fn = 0, fs = 0;
+    int fl = 0, fn = 0, fs = 0, fp = 1;
     if (forced) {
       const char *p = forced;
       for (int b = 0; b < a && p; ++b) {
         p = strchr(p, ',');
         if (p) ++p;
       }
-      if (p && sscanf(p, "%d:%d:%d", &fl, &fn, &fs) == 3 && (fl == 4 || fl == 8 || fl == 16) &&
-          plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fs ? fn : 0, !fs))
-        continue;
+      if (p && sscanf(p, "%d:%d:%d:%d", &fl, &fn, &fs, &fp) >= 3 && (fl == 4 || fl == 8 || fl == 16)) {
+        if (fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)
+                    : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1))
+          continue;
+      }
     }
     while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
     if (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
@@ -463,6 +571,8 @@ etd_status etd_step(etd_ctx *ctx, void *U, double t_n) {
   if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_step on a batched context");
   if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
+  if (needs_aligned_state(ctx->inst[0]) && (reinterpret_cast<uintptr_t>(U) & 15))
+    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be 16-byte aligned (FP32 tile kernels copy 16 bytes at a time)");
   if (!std::isfinite(t_n)) return fail(ctx, ETD_ERR_INVALID_ARG, "t_n not finite");
   cudaError_t e = forward_step(ctx->inst[0], U, t_n, ctx->stream, ctx);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etd_step launch");
@@ -475,6 +585,8 @@ etd_status etd_run(etd_ctx *ctx, void *U, double t0, int64_t nsteps) {
   if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
   if (nsteps < 0) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0");
   if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
+  if (needs_aligned_state(ctx->inst[0]) && (reinterpret_cast<uintptr_t>(U) & 15))
+    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be 16-byte aligned (FP32 tile kernels copy 16 bytes at a time)");
   const Instance &I = ctx->inst[0];
   return run_steps(ctx, [&](cudaStream_t s, int64_t n) -> cudaError_t {
     return forward_step(I, U, t0 + (double)n * I.k, s, ctx);
@@ -549,6 +661,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     info->chunk[a] = I.plan[a].L;
     info->lines_per_block[a] = I.plan[a].nlb;
     info->staged[a] = I.plan[a].sp.staged;
+    info->pack[a] = I.plan[a].pk;
   }
   return ETD_OK;
 }

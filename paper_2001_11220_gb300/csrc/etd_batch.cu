@@ -16,7 +16,7 @@
 namespace etd {
 etd_status validate_problem(const etd_grid *grid, const double *D, const etd_reaction *rx, double k,
                             int32_t precision);
-bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force);
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force, int pack);
 etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
 etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const double *D, const etd_reaction *rx,
                          double k, int32_t precision, bool with_scratch);
@@ -96,7 +96,7 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
     etd_status st = init_instance(ctx, I, &grids[i], D + (size_t)i * S, &reactions[i], k, precision, false);
     if (st != ETD_OK) return abort_create(st);
     for (int a = 0; a < dim; ++a) {
-      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true)) {
+      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true, 1)) {
         fail(ctx, ETD_ERR_UNSUPPORTED, "instance %d axis %d does not fit one block", i, a);
         return abort_create(ETD_ERR_UNSUPPORTED);
       }

@@ -59,6 +59,7 @@ struct AxisPlan {
   long long st = 1;    // element stride of the axis
   long long nlines = 1;
   size_t smem = 0;     // register kernel: shared memory bytes
+  int pk = 1;          // 2: register kernel on FP32 line pairs (nlb counts pairs)
   StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel
 };
 

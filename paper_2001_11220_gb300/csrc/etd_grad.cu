@@ -75,6 +75,8 @@ void upload(DeviceArena &arena, const HostTab &T, MatTab<R> &M, cudaError_t &err
   M.v1 = (const R *)arena.put(v1.data(), v1.size() * sizeof(R), err);
   M.w1 = (const R *)arena.put(w1.data(), w1.size() * sizeof(R), err);
   M.z1 = (const R *)arena.put(z1.data(), z1.size() * sizeof(R), err);
+  M.rows1 = nullptr;
+  M.rows2 = nullptr;  // adjoint sweeps run one line per thread
   M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
@@ -127,12 +129,17 @@ void geometry(const AxisPlan &P, const Instance &I, int a, SweepArgs<R> &A) {
   A.pitch = P.pitch;
   A.nblocks = P.nblocks;
   A.k = I.k;
+  A.kR = (R)I.k;
   A.rkind = I.rkind;
-  for (int j = 0; j < 8; ++j) A.rp[j] = I.rp[j];
+  for (int j = 0; j < 8; ++j) {
+    A.rp[j] = I.rp[j];
+    A.rpR[j] = (R)I.rp[j];
+  }
   for (int b = 0; b < 3; ++b) A.phi[b] = (const R *)I.phi[b];
   A.nx = (int)I.n[0];
   A.ny = (int)I.n[1];
   A.src_lf = I.src_lf;
+  A.src_lfR = (R)I.src_lf;
   A.axis = a;
 }
 
@@ -157,6 +164,7 @@ cudaError_t forward_intermediates(const Instance &I, const R *Un, double t, R *f
     A.out[2] = o + 2 * F;
     A.t_eval = t;
     A.exp_mt = std::exp(-t);
+    A.exp_mtR = (R)A.exp_mt;
     const AxisPlan &P = I.plan[a];
     cudaError_t e = launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
     if (e != cudaSuccess) return e;
@@ -217,6 +225,7 @@ cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double 
       A.out[2] = cb + 2 * F;
     }
     A.exp_mt = std::exp(-A.t_eval);
+    A.exp_mtR = (R)A.exp_mt;
     e = launch_adjoint(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
     if (e != cudaSuccess) return e;
   }

@@ -44,11 +44,17 @@ template <> struct V2T<double> { using T = double2; };
 //   e1, v1, w1, z1 [j*L+t]: the same e, v, w, z as separate arrays, read four
 //                  positions at a time in interior chunks (0 < j < m-1), where
 //                  every row has l = u = -r: nl = r, alpha = -r e
+//   rows1 (FP32 forward sweeps): six rows of m*L entries, row k at k*m*L:
+//                  ne = nl e, e, -alpha, z, v, w at every position (the forward
+//                  recurrence as g_i = ne_i g_{i-1} + e_i b_i)
+//   rows2 (FP32 line pairs): the same rows with each value in both lanes of a float2
 template <typename R> struct MatTab {
   const typename V4T<R>::T *pos;
   const typename V2T<R>::T *sum;
   const typename V4T<R>::T *chunk;
   const R *e1, *v1, *w1, *z1;
+  const R *rows1;
+  const typename V2T<R>::T *rows2;
   double r;       // interior off-diagonal magnitude
   double sm_c;    // v_{p-1} of the Sherman-Morrison rank-one term (periodic)
   double sm_inv;  // 1 / (1 + v.z)                                  (periodic)
@@ -57,8 +63,10 @@ template <typename R> struct MatTab {
 // Shared-memory staging plan of the persistent sweep kernels (byte offsets
 // into dynamic shared memory; every region 16-byte aligned).
 struct StagePlan {
-  int staged;       // 1: persistent shared-memory-staged kernel, 0: register kernel
+  int staged;       // 0: register kernel, 1: persistent shared-memory-staged kernel,
+                    // 2: FP32 tile kernel (one tile of whole lines per block, compile-time geometry)
   int tile_elems;   // elements of one staged field tile
+  int tile_pitch;   // tile kernel, x axis: row pitch (elements) of a field tile
   int nin;          // staged input fields per tile
   int nbuf;         // 1 or 2 tile buffers (2 = next tile prefetched during compute)
   int vec;          // strided tiles: 1 = 16-byte async copies per row segment
@@ -88,7 +96,12 @@ template <typename R> struct SweepArgs {
   const R *phi[3]; // sin(pi x_a / L_a) per axis (manufactured source), NULL otherwise
   int nx, ny;      // grid extents of axes 0 and 1 (point -> coordinates)
   double src_lf;   // Sum_a (pi / L_a)^2
+  // k, the reaction parameters, src_lf and e^{-t_eval} rounded to R once on
+  // the host (the kernels never convert FP64 parameters per thread)
+  R kR, src_lfR, exp_mtR;
+  R rpR[8];
   int axis;        // swept axis
+  int pk;          // 2: register kernel on line pairs (nlb counts pairs), else 1
   StagePlan sp;    // staged-kernel plan
   // adjoint sweeps only
   MatTab<R> matT[MAX_SPECIES][3];  // tables of the transposed line matrices
@@ -112,6 +125,16 @@ cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *b
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
                                  size_t smem, cudaStream_t s, double t_eval);
 
+// FP32 tile kernels: NLB lines per block, pk = 1 or 2 (line pairs, strided axes)
+cudaError_t launch_tile(const SweepArgs<float> &a, int nspecies, int L, int NLB, int kind, int pk, int nthreads,
+                        size_t smem, cudaStream_t s);
+cudaError_t launch_tile_first(const SweepArgs<float> &a, int nspecies, int L, int NLB, int nthreads, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_tile_middle(const SweepArgs<float> &a, int nspecies, int L, int NLB, int pk, int nthreads,
+                               size_t smem, cudaStream_t s);
+cudaError_t launch_tile_last(const SweepArgs<float> &a, int nspecies, int L, int NLB, int pk, int nthreads,
+                             size_t smem, cudaStream_t s);
+
 cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_adjoint(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
@@ -128,12 +151,13 @@ inline size_t adjoint_smem_bytes(int kind, int nspecies, int nlb, int pitch, siz
   return sums + (size_t)nq * nlb * sizeof(double) + 16 * sizeof(double) * 32;
 }
 
-// shared-memory bytes of one sweep block
-inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes) {
+// shared-memory bytes of one sweep block (pk = 2: nlb line pairs); the
+// Sherman-Morrison scalars take 8 bytes each (stored in the sweep's precision)
+inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes, int pk = 1) {
   int nq = (kind == SWEEP_LAST) ? 3 * nspecies : 5 * nspecies;
-  size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes;
+  size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes * pk;
   sums = (sums + 15) & ~(size_t)15;
-  return sums + (size_t)nq * nlb * sizeof(double);
+  return sums + (size_t)nq * nlb * pk * sizeof(double);
 }
 
 }  // namespace etd

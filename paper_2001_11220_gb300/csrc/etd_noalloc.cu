@@ -86,6 +86,13 @@ void stage_tab(const HostTab &T, MatTab<R> &M, Carve &cv, std::vector<std::pair<
   M.w1 = (const R *)up.back().first;
   up.push_back({cv.take(T.z1.size() * sizeof(R)), std::vector<R>(T.z1.begin(), T.z1.end())});
   M.z1 = (const R *)up.back().first;
+  M.rows1 = nullptr;
+  M.rows2 = nullptr;  // the no-allocation step plans one line per thread
+  if constexpr (sizeof(R) == 4) {
+    const std::vector<float> r1 = fp32_rows(T);
+    up.push_back({cv.take(r1.size() * sizeof(R)), std::vector<R>(r1.begin(), r1.end())});
+    M.rows1 = (const float *)up.back().first;
+  }
   M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;

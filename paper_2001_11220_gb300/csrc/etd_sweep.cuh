@@ -16,10 +16,12 @@
 // field once and writes each output field once (Figs. flow2d / flow3d fused
 // into FIRST / MIDDLE / LAST).
 //
-// Thread mapping: contiguous axis (x): lanes walk the chunks of a line
-// (j = tid % m) and load L consecutive elements with vector loads; strided
-// axes: lanes walk neighbouring lines (l = tid % nlb) so every load of
-// position i is one coalesced row segment across the warp.
+// Thread mapping: lanes walk neighbouring lines (l = tid % nlb), so table
+// reads are warp broadcasts and, on strided axes, every load of position i is
+// one coalesced row segment across the warp.  Pair mode (FP32, strided axes
+// with an even stride): each thread owns the same chunk of two neighbouring
+// lines as one float2 and runs every recurrence in the packed two-lane FP32
+// instructions, halving the instructions per point.
 #pragma once
 
 #include "etd_internal.h"
@@ -33,6 +35,72 @@ namespace etd {
 template <typename R>
 __device__ __forceinline__ R ld_nc(const R *p) { return __ldg(p); }
 
+// ------------------------------------------------------------ lane values
+// V = R (one line per thread) or float2 (a pair of neighbouring lines).  For
+// V = R the helpers are exactly the scalar operations (FP64 results do not
+// change); for float2 they are the packed two-lane instructions.
+template <typename R, int PK> struct LaneT { using T = R; };
+template <> struct LaneT<float, 2> { using T = float2; };
+
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+// a - b in one rounding: b * (-1) is exact
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ double vneg(double a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <typename V> struct Splat;
+template <> struct Splat<float> { __device__ static float of(float c) { return c; } };
+template <> struct Splat<double> { __device__ static double of(double c) { return c; } };
+template <> struct Splat<float2> { __device__ static float2 of(float c) { return make_float2(c, c); } };
+
+template <typename V> __device__ __forceinline__ bool v_nonzero(V a) { return a != V(0); }
+template <> __device__ __forceinline__ bool v_nonzero<float2>(float2 a) { return a.x != 0.f || a.y != 0.f; }
+
+__device__ __forceinline__ float v_shfl_up(float a, int off) { return __shfl_up_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ double v_shfl_up(double a, int off) { return __shfl_up_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ float2 v_shfl_up(float2 a, int off) {
+  return make_float2(__shfl_up_sync(0xffffffffu, a.x, off), __shfl_up_sync(0xffffffffu, a.y, off));
+}
+__device__ __forceinline__ float v_shfl_down(float a, int off) { return __shfl_down_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ double v_shfl_down(double a, int off) { return __shfl_down_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ float2 v_shfl_down(float2 a, int off) {
+  return make_float2(__shfl_down_sync(0xffffffffu, a.x, off), __shfl_down_sync(0xffffffffu, a.y, off));
+}
+__device__ __forceinline__ float v_shfl(float a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+__device__ __forceinline__ double v_shfl(double a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+__device__ __forceinline__ float2 v_shfl(float2 a, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
+
+// Sherman-Morrison scalar sigma = (v . y) / (1 + v . z) in FP64 from the
+// line's first (y_0) and last (y_{p-1}) values, one per lane of V, stored
+// in the precision the sweep uses it in (FP32 sweeps round it once here)
+template <typename T>
+__device__ __forceinline__ void put_sigma(T *dst, const MatTab<float> &M, float y0, float yl) {
+  if (M.sm_inv != 0.0) dst[0] = (T)(((double)y0 + M.sm_c * (double)yl) * M.sm_inv);
+  else dst[0] = T(0);
+}
+__device__ __forceinline__ void put_sigma(double *dst, const MatTab<double> &M, double y0, double yl) {
+  if (M.sm_inv != 0.0) dst[0] = (y0 + M.sm_c * yl) * M.sm_inv;
+  else dst[0] = 0.0;
+}
+__device__ __forceinline__ void put_sigma(float *dst, const MatTab<float> &M, float2 y0, float2 yl) {
+  put_sigma(dst, M, y0.x, yl.x);
+  put_sigma(dst + 1, M, y0.y, yl.y);
+}
+template <typename R>
+__device__ __forceinline__ R get_sigma(const R *src, R) { return src[0]; }
+__device__ __forceinline__ float2 get_sigma(const float *src, float2) { return make_float2(src[0], src[1]); }
+
 // a / b in the reactions: IEEE division in FP64; the hardware fast divide
 // (a few ulp) in FP32, whose arithmetic error budget is far larger
 __device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
@@ -45,11 +113,11 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
   switch (A.rkind) {
     case 1:
 #pragma unroll
-      for (int s = 0; s < S; ++s) f[s] = fma((R)A.rp[0], u[s], (R)A.rp[1]);
+      for (int s = 0; s < S; ++s) f[s] = fma(A.rpR[0], u[s], A.rpR[1]);
       return;
     case 2:
       if constexpr (S == 2) {  // Brusselator: a + u^2 v - (b+1) u ; b u - u^2 v
-        const R a = (R)A.rp[0], b = (R)A.rp[1];
+        const R a = A.rpR[0], b = A.rpR[1];
         const R uuv = u[0] * u[0] * u[1];
         f[0] = a + uuv - (b + R(1)) * u[0];
         f[1] = b * u[0] - uuv;
@@ -58,7 +126,7 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
       break;
     case 3:
       if constexpr (S == 2) {  // Schnakenberg: g (a - u + u^2 v) ; g (b - u^2 v)
-        const R a = (R)A.rp[0], b = (R)A.rp[1], g = (R)A.rp[2];
+        const R a = A.rpR[0], b = A.rpR[1], g = A.rpR[2];
         const R uuv = u[0] * u[0] * u[1];
         f[0] = g * (a - u[0] + uuv);
         f[1] = g * (b - uuv);
@@ -67,7 +135,7 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
       break;
     case 4:
       if constexpr (S == 2) {  // Gray-Scott: -u v^2 + F (1-u) ; u v^2 - (F+kappa) v
-        const R F = (R)A.rp[0], kap = (R)A.rp[1];
+        const R F = A.rpR[0], kap = A.rpR[1];
         const R uvv = u[0] * u[1] * u[1];
         f[0] = F * (R(1) - u[0]) - uvv;
         f[1] = uvv - (F + kap) * u[1];
@@ -86,25 +154,13 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
   for (int s = 0; s < S; ++s) f[s] = R(0);
 }
 
-// manufactured source p0 ((p1 lf - 1) q + q/(1+q)), q = e^{-t} prod sin(pi x_a/L_a)
-template <typename R>
-__device__ __forceinline__ R mms_source(const SweepArgs<R> &A, long long pidx, double exp_mt) {
-  const long long x = pidx % A.nx;
-  const long long r = pidx / A.nx;
-  const long long y = r % A.ny;
-  const long long z = r / A.ny;
-  R q = (R)exp_mt * A.phi[0][x] * A.phi[1][y];
-  if (A.phi[2]) q *= A.phi[2][z];
-  return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q));
-}
-
 // e^{-t} prod_{b != axis} sin(pi x_b / L_b) for one line: x axis line index
 // (y + z ny), strided axes (lo, hi) line coordinates; 0 without a source
 template <typename R>
 __device__ __forceinline__ R line_source_base(const SweepArgs<R> &A, bool contig, long long line, long long lo,
-                                              long long hi, double exp_mt) {
+                                              long long hi, R exp_mt) {
   if (A.phi[0] == nullptr) return R(0);
-  R q = (R)exp_mt;
+  R q = exp_mt;
   if (contig) {
     q *= A.phi[1][line % A.ny];
     if (A.phi[2]) q *= A.phi[2][line / A.ny];
@@ -309,11 +365,222 @@ __device__ __forceinline__ void pass2(const MatTab<R> &M, int m, int j, const R 
   }
 }
 
+// ------------------------------------------------- pass 1 / pass 2, FP32
+// FP32 sweeps read per-position coefficient rows (MatTab::rows1, and
+// MatTab::rows2 with each value in both lanes of a float2 for line pairs):
+// row k at k m L (k: 0 ne = nl e, 1 e, 2 -alpha, 3 z, 4 v, 5 w), entry (t, j)
+// at j L + t for every position (edge chunks and padding included), 16 bytes
+// per load.  The forward recurrence runs as g_i = ne_i g_{i-1} + e_i b_i: one
+// FMA on the dependency chain per position (e_i b_i is off the chain).  FP64
+// keeps the operation order of Section 7 (pass1 / pass2 above).
+__device__ __forceinline__ const float *rows_of(const MatTab<float> &M, float) { return M.rows1; }
+__device__ __forceinline__ const float2 *rows_of(const MatTab<float> &M, float2) { return M.rows2; }
+
+template <int L>
+__device__ __forceinline__ void load_rows(const float *__restrict__ p, float (&a)[L]) {
+  static_assert(L % 4 == 0, "FP32 rows are read four positions at a time");
+#pragma unroll
+  for (int t = 0; t < L; t += 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p + t));
+    a[t] = q.x;
+    a[t + 1] = q.y;
+    a[t + 2] = q.z;
+    a[t + 3] = q.w;
+  }
+}
+template <int L>
+__device__ __forceinline__ void load_rows(const float2 *__restrict__ p, float2 (&a)[L]) {
+#pragma unroll
+  for (int t = 0; t < L; t += 2) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p + t));
+    a[t] = make_float2(q.x, q.y);
+    a[t + 1] = make_float2(q.z, q.w);
+  }
+}
+
+// chunk summaries F = sum v b, Y = sum w b of one or two right-hand sides
+template <typename V, int L>
+__device__ __forceinline__ void pass1v(const MatTab<float> &M, int m, int j, const V (&b)[L], V &F, V &Y) {
+  const size_t ml = (size_t)m * L;
+  const V *row = rows_of(M, V()) + (size_t)j * L;
+  V v[L], w[L];
+  load_rows<L>(row + 4 * ml, v);
+  load_rows<L>(row + 5 * ml, w);
+  V f = Splat<V>::of(0.f), y = f;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    f = vfma(v[t], b[t], f);
+    y = vfma(w[t], b[t], y);
+  }
+  F = f;
+  Y = y;
+}
+
+template <typename V, int L>
+__device__ __forceinline__ void pass1x2v(const MatTab<float> &M, int m, int j, const V (&b0)[L], const V (&b1)[L],
+                                         V &F0, V &Y0, V &F1, V &Y1) {
+  const size_t ml = (size_t)m * L;
+  const V *row = rows_of(M, V()) + (size_t)j * L;
+  V v[L], w[L];
+  load_rows<L>(row + 4 * ml, v);
+  load_rows<L>(row + 5 * ml, w);
+  V f0 = Splat<V>::of(0.f), y0 = f0, f1 = f0, y1 = f0;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    f0 = vfma(v[t], b0[t], f0);
+    y0 = vfma(w[t], b0[t], y0);
+    f1 = vfma(v[t], b1[t], f1);
+    y1 = vfma(w[t], b1[t], y1);
+  }
+  F0 = f0; Y0 = y0; F1 = f1; Y1 = y1;
+}
+
+// Carries and Sherman-Morrison scalar of one solve: G (forward value before
+// the chunk), X (solution after the chunk), ns = -sigma (0 on open lines).
+template <typename V> struct Carry { V G, X, ns; };
+
+// Two independent solves (matrices M0, M1; SAME: one matrix, rows read once)
+// run interleaved: forward values into g0 / g1 (which may alias b0 / b1),
+// then the backward recurrence hands each solution value to epi(t, k, x),
+// k = 0, 1, from the last position down.
+template <typename V, int L, bool SAME, typename Epi>
+__device__ __forceinline__ void pass2x2v(const MatTab<float> &M0, const MatTab<float> &M1, int m, int j,
+                                         const V (&b0)[L], const V (&b1)[L], Carry<V> c0, Carry<V> c1, V (&g0)[L],
+                                         V (&g1)[L], Epi epi) {
+  const size_t ml = (size_t)m * L;
+  const V *r0 = rows_of(M0, V()) + (size_t)j * L;
+  const V *r1 = SAME ? r0 : rows_of(M1, V()) + (size_t)j * L;
+  {
+    V ne0[L], e0[L];
+    load_rows<L>(r0, ne0);
+    load_rows<L>(r0 + ml, e0);
+    if constexpr (SAME) {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        c0.G = vfma(ne0[t], c0.G, vmul(e0[t], b0[t]));
+        c1.G = vfma(ne0[t], c1.G, vmul(e0[t], b1[t]));
+        g0[t] = c0.G;
+        g1[t] = c1.G;
+      }
+    } else {
+      V ne1[L], e1[L];
+      load_rows<L>(r1, ne1);
+      load_rows<L>(r1 + ml, e1);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        c0.G = vfma(ne0[t], c0.G, vmul(e0[t], b0[t]));
+        c1.G = vfma(ne1[t], c1.G, vmul(e1[t], b1[t]));
+        g0[t] = c0.G;
+        g1[t] = c1.G;
+      }
+    }
+  }
+  V na0[L], na1[L];
+  load_rows<L>(r0 + 2 * ml, na0);
+  if constexpr (SAME) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) na1[t] = na0[t];
+  } else {
+    load_rows<L>(r1 + 2 * ml, na1);
+  }
+  if (v_nonzero(c0.ns) || v_nonzero(c1.ns)) {
+    V z0[L], z1[L];
+    load_rows<L>(r0 + 3 * ml, z0);
+    if constexpr (SAME) {
+#pragma unroll
+      for (int t = 0; t < L; ++t) z1[t] = z0[t];
+    } else {
+      load_rows<L>(r1 + 3 * ml, z1);
+    }
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      c0.X = vfma(na0[t], c0.X, g0[t]);
+      c1.X = vfma(na1[t], c1.X, g1[t]);
+      epi(t, 0, vfma(c0.ns, z0[t], c0.X));
+      epi(t, 1, vfma(c1.ns, z1[t], c1.X));
+    }
+  } else {
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      c0.X = vfma(na0[t], c0.X, g0[t]);
+      c1.X = vfma(na1[t], c1.X, g1[t]);
+      epi(t, 0, c0.X);
+      epi(t, 1, c1.X);
+    }
+  }
+}
+
+// one solve: forward values into g (may alias b), solutions to epi(t, x)
+template <typename V, int L, typename Epi>
+__device__ __forceinline__ void pass2v(const MatTab<float> &M, int m, int j, const V (&b)[L], Carry<V> c, V (&g)[L],
+                                       Epi epi) {
+  const size_t ml = (size_t)m * L;
+  const V *row = rows_of(M, V()) + (size_t)j * L;
+  {
+    V ne[L], e[L];
+    load_rows<L>(row, ne);
+    load_rows<L>(row + ml, e);
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      c.G = vfma(ne[t], c.G, vmul(e[t], b[t]));
+      g[t] = c.G;
+    }
+  }
+  V na[L];
+  load_rows<L>(row + 2 * ml, na);
+  if (v_nonzero(c.ns)) {
+    V z[L];
+    load_rows<L>(row + 3 * ml, z);
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      c.X = vfma(na[t], c.X, g[t]);
+      epi(t, vfma(c.ns, z[t], c.X));
+    }
+  } else {
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      c.X = vfma(na[t], c.X, g[t]);
+      epi(t, c.X);
+    }
+  }
+}
+
 // --------------------------------------------------------------- scan
 
-// Chain the chunk summaries of solves q0..q0+nq-1 for every line of the
-// block.  sF/sY hold F_j / Y_j on entry and the carries G_in[j] / X[j+1] on
-// return; sSig the FP64 Sherman-Morrison scalar per (solve, line).
+// chunk-table entry j through the read-only path: the compiler may then
+// hoist these loads past the scan's shared-memory stores
+__device__ __forceinline__ float4 ld_chunk(const MatTab<float> &M, int j) { return __ldg(M.chunk + j); }
+__device__ __forceinline__ double4 ld_chunk(const MatTab<double> &M, int j) {
+  const double2 *p = reinterpret_cast<const double2 *>(M.chunk + j);
+  const double2 a = __ldg(p), b = __ldg(p + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// Sequential carry chain of one (line, solve) over its m chunks: F[j] (chunk
+// summary) becomes the forward carry G_in[j], Y[j] the backward carry X[j+1];
+// G and X return the line's last forward value and first solution value.
+template <typename R, typename V>
+__device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m, V &Gout, V &Xout) {
+  V G = Splat<V>::of(R(0));
+#pragma unroll 8
+  for (int j = 0; j < m; ++j) {
+    const V f = F[j];
+    F[j] = G;
+    G = vfma(Splat<V>::of(ld_chunk(M, j).x), G, f);
+  }
+  V X = Splat<V>::of(R(0));
+#pragma unroll 8
+  for (int j = m - 1; j >= 0; --j) {
+    const typename V4T<R>::T c = ld_chunk(M, j);
+    const V y = vfma(Splat<V>::of(c.y), F[j], Y[j]);
+    Y[j] = X;
+    X = vfma(Splat<V>::of(c.z), X, y);
+  }
+  Gout = G;
+  Xout = X;
+}
+
+// solve q of a sweep -> (species, matrix index)
 template <typename R, int S, int KIND>
 __device__ __forceinline__ void solve_matrix(int q, int &s, int &g) {
   if constexpr (KIND == SWEEP_LAST) {
@@ -330,9 +597,10 @@ __device__ __forceinline__ void solve_matrix(int q, int &s, int &g) {
 // the affine chunk maps of a contiguous block of chunks, a shuffle scan over
 // the lanes gives every block its carries, and the lane re-walks its block to
 // emit G_in[j] and X[j+1] (forward map G -> Aend G + F, backward map
-// X -> Bst X + Y + kappa G_in).
-template <typename R, typename GetMat>
-__device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
+// X -> Bst X + Y + kappa G_in).  V is the lane value (one line or a pair);
+// sSig holds PK Sherman-Morrison scalars per (solve, line unit).
+template <typename R, typename V, int PK, typename SigT, typename GetMat>
+__device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, V *sF, V *sY, SigT *sSig, int q0, int nq,
                                                 GetMat mat) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   // full warps only: a trailing partial warp (blockDim not a multiple of 32) stays out of the shuffles
@@ -340,72 +608,74 @@ __device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, R *sF, R 
   if (warp >= nw) return;
   const int per = (m + 31) >> 5;
   const int j0 = min(lane * per, m), j1 = min(j0 + per, m);
+  const V one = Splat<V>::of(R(1)), zero = Splat<V>::of(R(0));
   for (int u = warp; u < nlb * nq; u += nw) {
     const int l = u % nlb;
     const int q = q0 + u / nlb;
     const MatTab<R> &M = mat(q);
-    R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
     // forward: block map G_out = a G_in + b
-    R a = R(1), b = R(0);
+    V a = one, b = zero;
     for (int jj = j0; jj < j1; ++jj) {
-      const R Aj = M.chunk[jj].x;
-      b = fma(Aj, b, F[jj]);
-      a *= Aj;
+      const V Aj = Splat<V>::of(ld_chunk(M, jj).x);
+      b = vfma(Aj, b, F[jj]);
+      a = vmul(a, Aj);
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const R ap = __shfl_up_sync(0xffffffffu, a, off), bp = __shfl_up_sync(0xffffffffu, b, off);
+      const V ap = v_shfl_up(a, off), bp = v_shfl_up(b, off);
       if (lane >= off) {
-        b = fma(a, bp, b);
-        a *= ap;
+        b = vfma(a, bp, b);
+        a = vmul(a, ap);
       }
     }
-    R G = __shfl_up_sync(0xffffffffu, b, 1);
-    if (lane == 0) G = R(0);
-    const R Gtot = __shfl_sync(0xffffffffu, b, 31);  // forward value at the last position
+    V G = v_shfl_up(b, 1);
+    if (lane == 0) G = zero;
+    const V Gtot = v_shfl(b, 31);  // forward value at the last position
     for (int jj = j0; jj < j1; ++jj) {
-      const typename V4T<R>::T c = M.chunk[jj];
-      const R f = F[jj];
+      const typename V4T<R>::T c = ld_chunk(M, jj);
+      const V f = F[jj];
       F[jj] = G;
-      Y[jj] = fma(c.y, G, Y[jj]);
-      G = fma(c.x, G, f);
+      Y[jj] = vfma(Splat<V>::of(c.y), G, Y[jj]);
+      G = vfma(Splat<V>::of(c.x), G, f);
     }
     // backward: block map X_out = a X_in + b, composed from the right
-    a = R(1);
-    b = R(0);
+    a = one;
+    b = zero;
     for (int jj = j1 - 1; jj >= j0; --jj) {
-      const R Bj = M.chunk[jj].z;
-      b = fma(Bj, b, Y[jj]);
-      a *= Bj;
+      const V Bj = Splat<V>::of(ld_chunk(M, jj).z);
+      b = vfma(Bj, b, Y[jj]);
+      a = vmul(a, Bj);
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const R an = __shfl_down_sync(0xffffffffu, a, off), bn = __shfl_down_sync(0xffffffffu, b, off);
+      const V an = v_shfl_down(a, off), bn = v_shfl_down(b, off);
       if (lane + off < 32) {
-        b = fma(a, bn, b);
-        a *= an;
+        b = vfma(a, bn, b);
+        a = vmul(a, an);
       }
     }
-    R X = __shfl_down_sync(0xffffffffu, b, 1);
-    if (lane == 31) X = R(0);
+    V X = v_shfl_down(b, 1);
+    if (lane == 31) X = zero;
     for (int jj = j1 - 1; jj >= j0; --jj) {
-      const R yv = Y[jj];
+      const V yv = Y[jj];
       Y[jj] = X;
-      X = fma(M.chunk[jj].z, X, yv);
+      X = vfma(Splat<V>::of(ld_chunk(M, jj).z), X, yv);
     }
-    const R X0 = __shfl_sync(0xffffffffu, X, 0);  // first position of the line
-    if (lane == 0)
-      sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X0 + M.sm_c * (double)Gtot) * M.sm_inv : 0.0;
+    const V X0 = v_shfl(X, 0);  // first position of the line
+    if (lane == 0) put_sigma(sSig + ((size_t)q * nlb + l) * PK, M, X0, Gtot);
   }
 }
 
-template <typename R, int S, int KIND>
-__device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
-                                           bool periodic) {
+// Chain the chunk summaries of solves q0..q0+nq-1 for every line (or line
+// pair) of the block.  sF/sY hold F_j / Y_j on entry and the carries G_in[j]
+// / X[j+1] on return; sSig the FP64 Sherman-Morrison scalars.
+template <typename R, typename V, int PK, int S, int KIND>
+__device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   if (m > 32) {
-    scan_lines_warp<R>(A, sF, sY, sSig, q0, nq, [&](int q) -> const MatTab<R> & {
+    scan_lines_warp<R, V, PK>(A, sF, sY, sSig, q0, nq, [&](int q) -> const MatTab<R> & {
       int ms, mg;
       solve_matrix<R, S, KIND>(q, ms, mg);
       return A.mat[ms][mg];
@@ -418,92 +688,124 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, R *sF, R *sY, 
     int ms, mg;
     solve_matrix<R, S, KIND>(q, ms, mg);
     const MatTab<R> &M = A.mat[ms][mg];
-    R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    R G = R(0);
-#pragma unroll 8
-    for (int j = 0; j < m; ++j) {
-      const R f = F[j];
-      F[j] = G;
-      G = fma(M.chunk[j].x, G, f);
-    }
-    R X = R(0);
-#pragma unroll 8
-    for (int j = m - 1; j >= 0; --j) {
-      const typename V4T<R>::T c = M.chunk[j];
-      const R y = fma(c.y, F[j], Y[j]);
-      Y[j] = X;
-      X = fma(c.z, X, y);
-    }
-    // cyclic line: y_0 = X, y_{p-1} = G; sigma = (v . y) / (1 + v . z) in FP64
-    sSig[(size_t)q * nlb + l] = periodic ? ((double)X + M.sm_c * (double)G) * M.sm_inv : 0.0;
+    V *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V G, X;
+    chain_line<R, V>(M, F, Y, m, G, X);
+    // cyclic line: y_0 = X, y_{p-1} = G
+    put_sigma(sSig + ((size_t)q * nlb + l) * PK, M, X, G);
   }
 }
 
 // -------------------------------------------------------------- the sweep
 
-// What one thread knows about its chunk of one line.
-template <typename R>
+// What one thread knows about its chunk of one line (or line pair).
+template <typename R, int PK = 1>
 struct ChunkPos {
-  int l, j;      // line within the block/tile, chunk index
+  using V = typename LaneT<R, PK>::T;
+  int l, j;      // line (pair) within the block/tile, chunk index
   int i0, cnt;   // first position of the chunk, positions inside the line
   bool thr_ok;   // the thread owns a chunk (false for padding threads)
-  R qbase;       // manufactured-source factor of the line (0: none)
+  V qbase;       // manufactured-source factor of the line(s) (0: none)
 };
+
+// per-lane manufactured source p0 ((p1 lf - 1) q + q/(1+q)) at q = qbase phi_axis[i]
+template <typename R>
+__device__ __forceinline__ R source_of(const SweepArgs<R> &A, R q) {
+  return A.rpR[0] * ((A.rpR[1] * A.src_lfR - R(1)) * q + rdiv(q, R(1) + q));
+}
 
 // One fused sweep of one block on register-resident chunks.  load(f, s, v)
 // fills v with input field f (FIRST: 0 = U_n; MIDDLE/LAST: 0 = c_U, 1 = c_f,
 // 2 = w) of species s, zero past the end of the line; store(f, s, v) writes
 // output field f (FIRST/MIDDLE: c_U, c_f, w; LAST: 0 = U_{n+1}).  exch is the
 // block's exchange space (chunk summaries, carries, Sherman-Morrison scalars).
-template <typename R, int S, int L, int KIND, typename LoadF, typename StoreF>
-__device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPos<R> &c, unsigned char *exch,
+// PK = 2: every value is a float2 holding a pair of neighbouring lines.
+template <typename R, int S, int L, int KIND, int PK, typename LoadF, typename StoreF>
+__device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPos<R, PK> &c, unsigned char *exch,
                                             LoadF load, StoreF store) {
+  using V = typename LaneT<R, PK>::T;
   constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   const int l = c.l, j = c.j, cnt = c.cnt, i0 = c.i0;
   const bool thr_ok = c.thr_ok;
-  const bool periodic = A.mat[0][0].sm_inv != 0.0;
-  const R qbase = c.qbase;
+  const V zero = Splat<V>::of(R(0));
   const R *phia = A.phi[A.axis];
-  auto src_at = [&](int t) -> R {  // manufactured source at position t of the chunk
-    if (qbase == R(0) || t >= cnt) return R(0);
-    const R q = qbase * phia[i0 + t];
-    return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q));
+  auto src_at = [&](int t) -> V {  // manufactured source at position t of the chunk
+    if (!v_nonzero(c.qbase) || t >= cnt) return zero;
+    const R ph = __ldg(phia + i0 + t);
+    if constexpr (PK == 1) {
+      return source_of(A, c.qbase * ph);
+    } else {
+      return make_float2(source_of(A, c.qbase.x * ph), source_of(A, c.qbase.y * ph));
+    }
   };
-  R *sF = reinterpret_cast<R *>(exch);
-  R *sY = sF + (size_t)NQ * nlb * pitch;
-  double *sSig = reinterpret_cast<double *>(exch + ((2 * (size_t)NQ * nlb * pitch * sizeof(R) + 15) & ~(size_t)15));
+  auto react = [&](const V (&u)[S], V (&f)[S], V src) {
+    if constexpr (PK == 1) {
+      reaction_point<R, S>(A, u, f, src);
+    } else {
+      R ux[S], uy[S], fx[S], fy[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        ux[s] = u[s].x;
+        uy[s] = u[s].y;
+      }
+      reaction_point<R, S>(A, ux, fx, src.x);
+      reaction_point<R, S>(A, uy, fy, src.y);
+#pragma unroll
+      for (int s = 0; s < S; ++s) f[s] = make_float2(fx[s], fy[s]);
+    }
+  };
+  auto p1 = [&](const MatTab<R> &M, const V (&b)[L], V &F, V &Y) {
+    if constexpr (sizeof(R) == 8) pass1<R, L>(M, m, j, b, F, Y);
+    else pass1v<V, L>(M, m, j, b, F, Y);
+  };
+  auto p1x2 = [&](const MatTab<R> &M, const V (&b0)[L], const V (&b1)[L], V &F0, V &Y0, V &F1, V &Y1) {
+    if constexpr (sizeof(R) == 8) pass1x2<R, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+    else pass1x2v<V, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+  };
+  V *sF = reinterpret_cast<V *>(exch);
+  V *sY = sF + (size_t)NQ * nlb * pitch;
+  R *sSig = reinterpret_cast<R *>(exch + ((2 * (size_t)NQ * nlb * pitch * sizeof(V) + 15) & ~(size_t)15));
   const size_t myidx = (size_t)l * pitch + j;
-  auto put = [&](int q, R F, R Y) {
+  auto put = [&](int q, V F, V Y) {
     if (thr_ok) {
       sF[(size_t)q * nlb * pitch + myidx] = F;
       sY[(size_t)q * nlb * pitch + myidx] = Y;
     }
   };
-  auto carries = [&](int q, R &Gin, R &Xr, R &sig) {
+  auto carries = [&](int q, V &Gin, V &Xr, V &sig) {
     Gin = sF[(size_t)q * nlb * pitch + myidx];
     Xr = sY[(size_t)q * nlb * pitch + myidx];
-    sig = (R)sSig[(size_t)q * nlb + l];
+    sig = get_sigma(sSig + ((size_t)q * nlb + l) * PK, zero);
   };
+  auto carry = [&](int q) {  // FP32 form: ns = -sigma
+    Carry<V> cq;
+    V sg;
+    carries(q, cq.G, cq.X, sg);
+    cq.ns = vneg(sg);
+    return cq;
+  };
+  const V k9 = Splat<V>::of(R(9)), km8 = Splat<V>::of(R(-8));
   // solve q -> (species, matrix): FIRST/MIDDLE: q = 5s + {0: T.cU, 1: S.cU, 2: T.cf, 3: S.cf, 4: P.w}
   //                               LAST: q = s (P.w), S + 2s (T.f1), S + 2s + 1 (S.f2)
   if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
-    R cu[S][L], cf[S][L], w[S][L];
+    V cu[S][L], cf[S][L], w[S][L];
     if constexpr (KIND == SWEEP_FIRST) {
       // U_n, F(U_n, t_n), w* = U_n + k F(U_n)
+      const V kk = Splat<V>::of(A.kR);
 #pragma unroll
       for (int s = 0; s < S; ++s) load(0, s, cu[s]);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
-        R u[S], f[S];
+        V u[S], f[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = cu[s][t];
-        reaction_point<R, S>(A, u, f, src_at(t));
+        react(u, f, src_at(t));
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          cf[s][t] = (t < cnt) ? f[s] : R(0);
-          w[s][t] = fma((R)A.k, cf[s][t], cu[s][t]);
+          cf[s][t] = (t < cnt) ? f[s] : zero;
+          w[s][t] = vfma(kk, cf[s][t], cu[s][t]);
         }
       }
     } else {
@@ -517,44 +819,63 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     // pass 1: five solves per species share one exchange
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R F0, Y0, F1, Y1;
-      pass1x2<R, L>(A.mat[s][1], m, j, cu[s], cf[s], F0, Y0, F1, Y1);
+      V F0, Y0, F1, Y1;
+      p1x2(A.mat[s][1], cu[s], cf[s], F0, Y0, F1, Y1);
       put(5 * s + 0, F0, Y0);
       put(5 * s + 2, F1, Y1);
-      pass1x2<R, L>(A.mat[s][2], m, j, cu[s], cf[s], F0, Y0, F1, Y1);
+      p1x2(A.mat[s][2], cu[s], cf[s], F0, Y0, F1, Y1);
       put(5 * s + 1, F0, Y0);
       put(5 * s + 3, F1, Y1);
-      pass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
+      p1(A.mat[s][0], w[s], F0, Y0);
       put(5 * s + 4, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, S, KIND>(A, sF, sY, sSig, 0, NQ, periodic);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ);
     __syncthreads();
     // pass 2: c_U <- 9 T c_U - 8 S c_U, c_f likewise, w <- P w
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R xa[L], xb[L], G, X, sg;
-      carries(5 * s + 0, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
-      carries(5 * s + 1, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, cu[s], G, X, sg, xb);
+      if constexpr (sizeof(R) == 4) {
+        // T on (c_U, c_f) into (xa, xc); S on (c_U, c_f) in place, folded into 9 T - 8 S
+        V xa[L], xc[L];
+        pass2x2v<V, L, true>(A.mat[s][1], A.mat[s][1], m, j, cu[s], cf[s], carry(5 * s + 0), carry(5 * s + 2), xa,
+                             xc, [&](int t, int k, V x) {
+                               if (k == 0) xa[t] = x;
+                               else xc[t] = x;
+                             });
+        pass2x2v<V, L, true>(A.mat[s][2], A.mat[s][2], m, j, cu[s], cf[s], carry(5 * s + 1), carry(5 * s + 3),
+                             cu[s], cf[s], [&](int t, int k, V x) {
+                               if (k == 0) xa[t] = vfma(k9, xa[t], vmul(km8, x));
+                               else xc[t] = vfma(k9, xc[t], vmul(km8, x));
+                             });
+        store(0, s, xa);
+        store(1, s, xc);
+        pass2v<V, L>(A.mat[s][0], m, j, w[s], carry(5 * s + 4), w[s], [&](int t, V x) { w[s][t] = x; });
+        store(2, s, w[s]);
+      } else {
+        V xa[L], xb[L], G, X, sg;
+        carries(5 * s + 0, G, X, sg);
+        pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
+        carries(5 * s + 1, G, X, sg);
+        pass2<R, L>(A.mat[s][2], m, j, cu[s], G, X, sg, xb);
 #pragma unroll
-      for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
-      store(0, s, xa);
-      carries(5 * s + 2, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, cf[s], G, X, sg, xa);
-      carries(5 * s + 3, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
+        for (int t = 0; t < L; ++t) xa[t] = vfma(k9, xa[t], vmul(km8, xb[t]));
+        store(0, s, xa);
+        carries(5 * s + 2, G, X, sg);
+        pass2<R, L>(A.mat[s][1], m, j, cf[s], G, X, sg, xa);
+        carries(5 * s + 3, G, X, sg);
+        pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
 #pragma unroll
-      for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
-      store(1, s, xa);
-      carries(5 * s + 4, G, X, sg);
-      pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, xa);
-      store(2, s, xa);
+        for (int t = 0; t < L; ++t) xa[t] = vfma(k9, xa[t], vmul(km8, xb[t]));
+        store(1, s, xa);
+        carries(5 * s + 4, G, X, sg);
+        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, xa);
+        store(2, s, xa);
+      }
     }
   } else {
     // LAST: phase A  U* = P_d w ; phase B  U_{n+1} = T_d f1 - S_d f2
-    R cu[S][L], cf[S][L], w[S][L];
+    V cu[S][L], cf[S][L], w[S][L];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       load(0, s, cu[s]);
@@ -563,109 +884,178 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R F0, Y0;
-      pass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
+      V F0, Y0;
+      p1(A.mat[s][0], w[s], F0, Y0);
       put(s, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, S, KIND>(A, sF, sY, sSig, 0, S, periodic);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, S);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R x[L], G, X, sg;
-      carries(s, G, X, sg);
-      pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, x);
+      if constexpr (sizeof(R) == 4) {
+        pass2v<V, L>(A.mat[s][0], m, j, w[s], carry(s), w[s], [&](int t, V x) { w[s][t] = x; });  // w <- U*
+      } else {
+        V x[L], G, X, sg;
+        carries(s, G, X, sg);
+        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, x);
 #pragma unroll
-      for (int t = 0; t < L; ++t) w[s][t] = x[t];  // w now holds U*
+        for (int t = 0; t < L; ++t) w[s][t] = x[t];  // w now holds U*
+      }
     }
     // F(U*, t_{n+1}); f1, f2 overwrite c_U, c_f
-    const R k = (R)A.k;
+    const R k = A.kR;
+    const V k2 = Splat<V>::of(R(2) * k), kk = Splat<V>::of(k), k15 = Splat<V>::of(R(1.5) * k),
+            k05 = Splat<V>::of(R(0.5) * k), k8 = Splat<V>::of(R(8));
 #pragma unroll
     for (int t = 0; t < L; ++t) {
-      R u[S], f[S];
+      V u[S], f[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) u[s] = w[s][t];
-      reaction_point<R, S>(A, u, f, src_at(t));
+      react(u, f, src_at(t));
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const R fs = (t < cnt) ? f[s] : R(0);
-        const R a = cu[s][t], b = cf[s][t];
-        cu[s][t] = fma(R(9), a, fma(R(2) * k, b, k * fs));
-        cf[s][t] = fma(R(8), a, fma(R(1.5) * k, b, R(0.5) * k * fs));
+        const V fs = (t < cnt) ? f[s] : zero;
+        const V a = cu[s][t], b = cf[s][t];
+        cu[s][t] = vfma(k9, a, vfma(k2, b, vmul(kk, fs)));
+        cf[s][t] = vfma(k8, a, vfma(k15, b, vmul(k05, fs)));
       }
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R F0, Y0, F1, Y1;
-      pass1<R, L>(A.mat[s][1], m, j, cu[s], F0, Y0);
-      pass1<R, L>(A.mat[s][2], m, j, cf[s], F1, Y1);
+      V F0, Y0, F1, Y1;
+      p1(A.mat[s][1], cu[s], F0, Y0);
+      p1(A.mat[s][2], cf[s], F1, Y1);
       put(S + 2 * s, F0, Y0);
       put(S + 2 * s + 1, F1, Y1);
     }
     __syncthreads();
-    scan_lines<R, S, KIND>(A, sF, sY, sSig, S, 2 * S, periodic);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R xa[L], xb[L], G, X, sg;
-      carries(S + 2 * s, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
-      carries(S + 2 * s + 1, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
+      if constexpr (sizeof(R) == 4) {
+        // T f1 and S f2 interleaved in place; c_U <- T f1 - S f2
+        pass2x2v<V, L, false>(A.mat[s][1], A.mat[s][2], m, j, cu[s], cf[s], carry(S + 2 * s), carry(S + 2 * s + 1),
+                              cu[s], cf[s], [&](int t, int k, V x) {
+                                if (k == 0) cu[s][t] = x;
+                                else cu[s][t] = vsub(cu[s][t], x);
+                              });
+        store(0, s, cu[s]);
+      } else {
+        V xa[L], xb[L], G, X, sg;
+        carries(S + 2 * s, G, X, sg);
+        pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
+        carries(S + 2 * s + 1, G, X, sg);
+        pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
 #pragma unroll
-      for (int t = 0; t < L; ++t) xa[t] -= xb[t];
-      store(0, s, xa);
+        for (int t = 0; t < L; ++t) xa[t] = vsub(xa[t], xb[t]);
+        store(0, s, xa);
+      }
     }
   }
 }
 
-// Register kernel: one block per group of nlb lines, inputs loaded straight
-// from global memory (vector loads on x, coalesced row segments on strided axes).
-template <typename R, int S, int L, bool CONTIG, int KIND>
+// line pairs: L positions of two neighbouring lines, 8-byte loads (st2 = stride in pairs)
+template <int L>
+__device__ __forceinline__ void load_pairs(float2 (&v)[L], const float2 *__restrict__ p, int st2, int cnt) {
+  if (cnt == L) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) v[t] = __ldg(p + t * st2);
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? __ldg(p + t * st2) : make_float2(0.f, 0.f);
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void store_pairs(const float2 (&v)[L], float2 *__restrict__ p, int st2, int cnt) {
+  if (cnt == L) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) p[t * st2] = v[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t)
+      if (t < cnt) p[t * st2] = v[t];
+  }
+}
+
+// Register kernel: one block per group of nlb lines (nlb line pairs for
+// PK = 2), inputs loaded straight from global memory (vector loads on x,
+// coalesced row segments on strided axes).
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1>
 __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
-                                            double exp_mt) {
+                                            R exp_mt) {
   (void)t_eval;
   const int m = A.m, nlb = A.nlb;
   const int tid = threadIdx.x;
   // threads past nlb*m (batched launches size blocks for the largest
   // instance) own no chunk but still take part in every barrier and scan
   const bool thr_ok = tid < nlb * m;
-  // lanes walk neighbouring lines on every axis: table reads are warp broadcasts
   int l = tid % nlb, j = tid / nlb;
   if (!thr_ok) { l = 0; j = 0; }
-  long long base;
-  bool line_ok;
-  ChunkPos<R> c;
-  if constexpr (CONTIG) {
-    const long long line = (long long)bid * nlb + l;
-    line_ok = thr_ok && line < A.nlines;
-    base = line * A.n;
-    c.qbase = line_ok ? line_source_base(A, true, line, 0, 0, exp_mt) : R(0);
-  } else {
-    const long long lo = (long long)(bid % A.nlo_blocks) * nlb + l;
-    const long long hi = bid / A.nlo_blocks;
-    line_ok = thr_ok && lo < A.st;
-    base = lo + hi * A.st * A.n;
-    c.qbase = line_ok ? line_source_base(A, false, 0, lo, hi, exp_mt) : R(0);
-  }
-  const long long st = CONTIG ? 1 : A.st;
-  c.l = l;
-  c.j = j;
-  c.i0 = j * L;
-  c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
-  c.thr_ok = thr_ok;
-  const long long off0 = base + (long long)c.i0 * st;
   const long long N = A.N;
-  const int cnt = c.cnt;
-  auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG>(v, A.in[f] + s * N, off0, st, cnt); };
-  auto store = [&](int f, int s, const R (&v)[L]) { store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt); };
-  chunk_sweep<R, S, L, KIND>(A, c, smem, load, store);
+  if constexpr (PK == 2) {
+    // strided axis, even stride: pair l covers lines lo, lo + 1 of one row
+    static_assert(!CONTIG && sizeof(R) == 4, "line pairs: FP32 strided sweeps");
+    const long long lo = (long long)(bid % A.nlo_blocks) * nlb * 2 + 2 * l;
+    const long long hi = bid / A.nlo_blocks;
+    const bool line_ok = thr_ok && lo < A.st;
+    ChunkPos<R, 2> c;
+    c.qbase = line_ok ? make_float2(line_source_base(A, false, 0, lo, hi, exp_mt),
+                                    line_source_base(A, false, 0, lo + 1, hi, exp_mt))
+                      : make_float2(0.f, 0.f);
+    c.l = l;
+    c.j = j;
+    c.i0 = j * L;
+    c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
+    c.thr_ok = thr_ok;
+    const long long off0 = (lo + hi * A.st * A.n + (long long)c.i0 * A.st) >> 1;  // in pairs
+    const int st2 = (int)(A.st >> 1);
+    const int cnt = c.cnt;
+    auto load = [&](int f, int s, float2 (&v)[L]) {
+      load_pairs<L>(v, reinterpret_cast<const float2 *>(A.in[f] + s * N) + off0, st2, cnt);
+    };
+    auto store = [&](int f, int s, const float2 (&v)[L]) {
+      store_pairs<L>(v, reinterpret_cast<float2 *>(A.out[f] + s * N) + off0, st2, cnt);
+    };
+    chunk_sweep<R, S, L, KIND, 2>(A, c, smem, load, store);
+  } else {
+    long long base;
+    bool line_ok;
+    ChunkPos<R> c;
+    if constexpr (CONTIG) {
+      const long long line = (long long)bid * nlb + l;
+      line_ok = thr_ok && line < A.nlines;
+      base = line * A.n;
+      c.qbase = line_ok ? line_source_base(A, true, line, 0, 0, exp_mt) : R(0);
+    } else {
+      const long long lo = (long long)(bid % A.nlo_blocks) * nlb + l;
+      const long long hi = bid / A.nlo_blocks;
+      line_ok = thr_ok && lo < A.st;
+      base = lo + hi * A.st * A.n;
+      c.qbase = line_ok ? line_source_base(A, false, 0, lo, hi, exp_mt) : R(0);
+    }
+    const long long st = CONTIG ? 1 : A.st;
+    c.l = l;
+    c.j = j;
+    c.i0 = j * L;
+    c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
+    c.thr_ok = thr_ok;
+    const long long off0 = base + (long long)c.i0 * st;
+    const int cnt = c.cnt;
+    auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG>(v, A.in[f] + s * N, off0, st, cnt); };
+    auto store = [&](int f, int s, const R (&v)[L]) {
+      store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt);
+    };
+    chunk_sweep<R, S, L, KIND, 1>(A, c, smem, load, store);
+  }
 }
 
-template <typename R, int S, int L, bool CONTIG, int KIND>
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel(const __grid_constant__ SweepArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  sweep_block<R, S, L, CONTIG, KIND>(A, blockIdx.x, smem, A.t_eval, A.exp_mt);
+  sweep_block<R, S, L, CONTIG, KIND, PK>(A, blockIdx.x, smem, A.t_eval, A.exp_mtR);
 }
 
 // Batched ensemble: one launch covers every instance; block b belongs to the
@@ -673,7 +1063,7 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel(const __grid_con
 template <typename R, int S, int L, bool CONTIG, int KIND>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel_batched(const SweepArgs<R> *__restrict__ args,
                                                               const int *__restrict__ block_start, int ninst,
-                                                              double t_eval, double exp_mt) {
+                                                              double t_eval, R exp_mt) {
   extern __shared__ __align__(16) unsigned char smem[];
   int lo = 0, hi = ninst - 1;
   const int b = blockIdx.x;

@@ -60,6 +60,7 @@ inline cudaError_t persistent_grid(const void *fn, int nthreads, size_t smem, in
 template <typename R, int S, int L, int KIND>
 cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStream_t s) {
   constexpr bool CONTIG = (KIND == SWEEP_FIRST);
+  if (a.sp.staged == 2) return cudaErrorInvalidValue;  // tile kernels: launch_tile
   if (a.sp.staged) {
     auto fn = sweep_staged_kernel<R, S, L, CONTIG, KIND>;
     cudaError_t e = ensure_smem((const void *)fn, a.sp.bytes);
@@ -70,6 +71,16 @@ cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStr
     fn<<<grid, nthreads, a.sp.bytes, s>>>(a);
     return cudaGetLastError();
   }
+  if constexpr (sizeof(R) == 4 && !CONTIG && L == 8) {
+    if (a.pk == 2) {
+      auto fp = sweep_kernel<R, S, L, false, KIND, 2>;
+      cudaError_t e = ensure_smem((const void *)fp, smem);
+      if (e != cudaSuccess) return e;
+      fp<<<a.nblocks, nthreads, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  if (a.pk != 1) return cudaErrorInvalidValue;
   auto fn = sweep_kernel<R, S, L, CONTIG, KIND>;
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
@@ -84,7 +95,7 @@ cudaError_t launch_one_batched(const SweepArgs<R> *args, const int *bs, int nins
   auto fn = sweep_kernel_batched<R, S, L, CONTIG, KIND>;
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
-  fn<<<total, nthreads, smem, s>>>(args, bs, ninst, t_eval, std::exp(-t_eval));
+  fn<<<total, nthreads, smem, s>>>(args, bs, ninst, t_eval, (R)std::exp(-t_eval));
   return cudaGetLastError();
 }
 

@@ -127,7 +127,7 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<R> &A, const TileCoor
 template <typename R, bool CONTIG>
 __device__ __forceinline__ R source_base(const SweepArgs<R> &A, const TileCoord &c, int l) {
   if (A.phi[0] == nullptr || l >= c.nvalid) return R(0);
-  R q = (R)A.exp_mt;
+  R q = A.exp_mtR;
   if constexpr (CONTIG) {  // line index = y + z ny
     const long long line = c.line0 + l;
     const long long y = line % A.ny, z = line / A.ny;
@@ -145,7 +145,7 @@ __device__ __forceinline__ R source_base(const SweepArgs<R> &A, const TileCoord 
 
 template <typename R>
 __device__ __forceinline__ R source_at(const SweepArgs<R> &A, R q) {
-  return (R)A.rp[0] * (((R)A.rp[1] * (R)A.src_lf - R(1)) * q + rdiv(q, R(1) + q));
+  return A.rpR[0] * ((A.rpR[1] * A.src_lfR - R(1)) * q + rdiv(q, R(1) + q));
 }
 
 // Tile layouts (positions past the end of a line are zero and stay zero):
@@ -193,7 +193,7 @@ __device__ __forceinline__ void compute_tile(const SweepArgs<R> &A, const TileCo
         if (t < cnt) po[(long long)t * A.st] = v[t];
     }
   };
-  chunk_sweep<R, S, L, KIND>(A, p, smem + A.sp.off_sum, load, store);
+  chunk_sweep<R, S, L, KIND, 1>(A, p, smem + A.sp.off_sum, load, store);
   if constexpr (CONTIG) {
     // coalesced write-back: thread (lp, cc) writes elements cc + k m of line lp
     constexpr int NOUT = (KIND == SWEEP_LAST) ? S : 3 * S;

@@ -147,6 +147,22 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
   }
 }
 
+// FP32 coefficient rows of the forward sweeps (MatTab::rows1): row k at k m L
+// holds ne = nl e, e, -alpha, z, v, w for every position, products in FP64
+inline std::vector<float> fp32_rows(const HostTab &T) {
+  const size_t ml = T.e1.size();
+  std::vector<float> r1(6 * ml);
+  for (size_t q = 0; q < ml; ++q) {
+    r1[q] = (float)(T.pos[4 * q] * T.pos[4 * q + 1]);
+    r1[ml + q] = (float)T.pos[4 * q + 1];
+    r1[2 * ml + q] = -(float)T.pos[4 * q + 2];
+    r1[3 * ml + q] = (float)T.pos[4 * q + 3];
+    r1[4 * ml + q] = (float)T.sum[2 * q];
+    r1[5 * ml + q] = (float)T.sum[2 * q + 1];
+  }
+  return r1;
+}
+
 inline double grid_h(int bc, long long p, double len) {
   if (bc == BC_DIRICHLET) return len / (double)(p + 1);
   if (bc == BC_NEUMANN) return len / (double)(p - 1);

@@ -1,6 +1,7 @@
 // etd_tune.cu -- tile-shape autotuner: for every axis, time each candidate
-// (chunk length L, lines per tile, staged or register kernel) on the
-// context's stream with CUDA events and keep the fastest.
+// (chunk length L, lines per tile, staged or register kernel, one line or a
+// line pair per thread) on the context's stream with CUDA events and keep
+// the fastest.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -11,7 +12,8 @@
 #include "etd_context.h"
 
 namespace etd {
-bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force);
+bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force, int pack);
+bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk);
 etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
 }  // namespace etd
 
@@ -22,7 +24,14 @@ namespace {
 struct Cand {
   int L, nlb;
   bool reg;
+  int pack;
+  bool tile = false;  // FP32 tile kernel with nlb lines per block
 };
+
+bool plan_cand(Instance &I, int a, const Cand &c) {
+  if (c.tile) return plan_axis_tile(I, a, c.L, c.nlb, c.pack);
+  return plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg, c.pack);
+}
 
 // device time of axis a's sweep, averaged over `reps` steps
 etd_status time_axis(etd_ctx *ctx, Instance &I, int a, void *U, int reps, double &ms) {
@@ -61,21 +70,29 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
   if (!U_work) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work is NULL");
   Instance &I = ctx->inst[0];
   ctx->graphs.clear();
-  const int Ls32[] = {8, 16}, Ls64[] = {4, 8};
+  const int Ls32[] = {4, 8, 16}, Ls64[] = {4, 8};
   const int nlbs[] = {4, 8, 16, 32, 64};
   for (int a = 0; a < I.dim; ++a) {
     std::vector<Cand> cands;
-    for (int li = 0; li < 2; ++li) {
+    const int nL = I.real_bytes == 4 ? 3 : 2;
+    for (int li = 0; li < nL; ++li) {
       const int L = I.real_bytes == 4 ? Ls32[li] : Ls64[li];
-      for (int nlb : nlbs) cands.push_back({L, nlb, false});
-      cands.push_back({L, 0, true});
-      for (int nlb : {8, 16}) cands.push_back({L, nlb, true});
+      for (int nlb : nlbs) cands.push_back({L, nlb, false, 1});
+      cands.push_back({L, 0, true, 1});
+      for (int nlb : {8, 16}) cands.push_back({L, nlb, true, 1});
+      if (L == 8)
+        for (int nlb : {0, 8, 16, 32}) cands.push_back({L, nlb, true, 2});  // line pairs (planner checks)
+      if (I.real_bytes == 4 && L >= 8)
+        for (int nlb : {16, 32})
+          for (int pk : {1, 2}) cands.push_back({L, nlb, false, pk, true});  // tile kernels
     }
     const AxisPlan keep = I.plan[a];
     double best = 1e30;
-    Cand pick{keep.L, keep.sp.staged ? keep.nlb : 0, !keep.sp.staged};
+    Cand pick{keep.L, keep.sp.staged || keep.pk == 2 ? keep.nlb : 0, !keep.sp.staged, keep.pk,
+              keep.sp.staged == 2};
+    if (pick.tile) pick.nlb = keep.nlb * keep.pk;
     for (const Cand &c : cands) {
-      if (!plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg)) continue;
+      if (!plan_cand(I, a, c)) continue;
       if (c.reg && I.plan[a].sp.staged) continue;
       etd_status st = build_axis_tables(ctx, I, a);
       if (st != ETD_OK) return st;
@@ -83,14 +100,15 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       st = time_axis(ctx, I, a, U_work, 5, ms);
       if (st != ETD_OK) return st;
       if (std::getenv("ETD_TUNE_VERBOSE"))
-        fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d %s -> %.4f ms\n", a, c.L, I.plan[a].nlb,
-                I.plan[a].sp.staged ? "staged" : "register", ms);
+        fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d %s%s -> %.4f ms\n", a, c.L, I.plan[a].nlb,
+                I.plan[a].sp.staged == 2 ? "tile" : (I.plan[a].sp.staged ? "staged" : "register"),
+                I.plan[a].pk == 2 ? " pairs" : "", ms);
       if (ms < best) {
         best = ms;
         pick = c;
       }
     }
-    if (!plan_axis_ex(I, a, pick.L, ETD_MAX_BLOCK_THREADS, pick.nlb, pick.reg))
+    if (!plan_cand(I, a, pick))
       return fail(ctx, ETD_ERR_CUDA, "autotune: best candidate of axis %d no longer plans", a);
     etd_status st = build_axis_tables(ctx, I, a);
     if (st != ETD_OK) return st;

@@ -242,3 +242,114 @@ def test_autotuned_tiles_keep_parity():
     err = rel_err(U.cpu().numpy(), oracle_run(w, U0, 1, t0=0.3))
     ctx.close()
     assert err <= FP64_TOL, err
+
+
+# Line-pair mode (FP32 strided sweeps, two neighbouring lines per thread in
+# packed two-lane arithmetic), forced through ETD_TILES on every strided axis
+PAIR_CASES = [
+    case("pair_bru2d_neu", (64, 64), W.NEUMANN, (2e-3, 2e-3), "brusselator", (1.0, 3.4), k=0.01),
+    case("pair_sch2d_per", (40, 29), W.PERIODIC, (0.01, 0.1), "schnakenberg", (0.1, 0.9, 10.0)),
+    case("pair_gs2d_ragged", (34, 47), (W.PERIODIC, W.NEUMANN), (0.02, 0.01), "gray_scott", (0.04, 0.06), k=0.5),
+    case("pair_gs3d", (20, 17, 23), (W.PERIODIC, W.NEUMANN, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+         (0.04, 0.06), k=0.5),
+    case("pair_mms3d", (16, 16, 16), W.DIRICHLET, (1.0,), "enzyme", (1.0, 1.0), k=1 / 17, ic="sine"),
+    case("pair_lin3d", (30, 22, 9), W.NEUMANN, (0.3,), "linear", (-0.7, 0.2), k=0.1),
+    case("pair_long_per", (6, 1100), (W.NEUMANN, W.PERIODIC), (0.5, 2.0), "schnakenberg", (0.1, 0.9, 10.0),
+         k=0.01, ic="uniform", ic_args=((1.0, 0.9), 1e-2)),
+]
+
+
+def pair_tiles(dim):
+    return ",".join(["8:0:0:1"] + ["8:0:0:2"] * (dim - 1))
+
+
+@pytest.mark.parametrize("w", PAIR_CASES, ids=lambda w: w.name)
+def test_line_pairs_fp32_vs_oracle(w, monkeypatch):
+    monkeypatch.setenv("ETD_TILES", pair_tiles(len(w.n)))
+    ctx = _api().from_workload(w, "fp32")
+    assert ctx.info()["pack"][1:len(w.n)] == [2] * (len(w.n) - 1)
+    U0 = W.initial_state(w)
+    U = torch.tensor(U0, device="cuda", dtype=torch.float32)
+    ctx.run(U, 0.3, 1)
+    torch.cuda.synchronize()
+    one = U.double().cpu().numpy()
+    ctx.run(U, 0.3 + w.k, 2)
+    torch.cuda.synchronize()
+    three = U.double().cpu().numpy()
+    ctx.close()
+    e1 = rel_err(one, oracle_run(w, U0, 1, t0=0.3))
+    e3 = rel_err(three, oracle_run(w, U0, 3, t0=0.3))
+    print(f"{w.name}: FP32 line pairs vs FP64 oracle: 1 step {e1:.3e}, 3 steps {e3:.3e}")
+    assert e1 <= FP32_STEP_TOL and e3 <= 3 * FP32_STEP_TOL, (e1, e3)
+
+
+def test_line_pairs_grad_matches_single_lines(monkeypatch):
+    """The gradient's forward recomputation runs the pair kernels when they are
+    planned: its FP32 result matches the one-line-per-thread gradient."""
+    w = W.gray_scott_3d(16, steps=4).with_(k=0.5, D=(0.01, 0.005))
+    U0 = torch.tensor(W.initial_state(w), device="cuda", dtype=torch.float32)
+    tg = torch.tensor(W.initial_state(w, seed=5), device="cuda", dtype=torch.float32)
+    out = []
+    for tiles in (None, pair_tiles(3)):
+        if tiles:
+            monkeypatch.setenv("ETD_TILES", tiles)
+        ctx = _api().from_workload(w, "fp32")
+        out.append(ctx.grad(U0, 0.0, tg, 4, 2))
+        ctx.close()
+    (l0, g0, d0, p0), (l1, g1, d1, p1) = out
+    assert abs(l1 - l0) <= 1e-5 * abs(l0)
+    assert float((g1 - g0).abs().max() / g0.abs().max()) <= 1e-4
+    assert np.max(np.abs(d1 - d0)) <= 1e-3 * np.max(np.abs(d0))
+
+
+# FP32 tile kernels (shared-memory tiles of whole lines, compile-time tile
+# geometry), forced through ETD_TILES: one line per thread on every axis, and
+# line pairs on the strided axes
+TILE_CASES = [
+    case("tile_bru2d_neu", (64, 64), W.NEUMANN, (2e-3, 2e-3), "brusselator", (1.0, 3.4), k=0.01),
+    case("tile_sch2d_per", (40, 28), W.PERIODIC, (0.01, 0.1), "schnakenberg", (0.1, 0.9, 10.0)),
+    case("tile_gs2d_ragged", (36, 47), (W.PERIODIC, W.NEUMANN), (0.02, 0.01), "gray_scott", (0.04, 0.06), k=0.5),
+    case("tile_gs3d", (20, 16, 23), (W.PERIODIC, W.NEUMANN, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+         (0.04, 0.06), k=0.5),
+    case("tile_mms3d", (16, 16, 16), W.DIRICHLET, (1.0,), "enzyme", (1.0, 1.0), k=1 / 17, ic="sine"),
+    case("tile_lin3d", (28, 20, 37), W.NEUMANN, (0.3,), "linear", (-0.7, 0.2), k=0.1),
+]
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["lines", "pairs"])
+@pytest.mark.parametrize("w", TILE_CASES, ids=lambda w: w.name)
+def test_tile_kernels_fp32_vs_oracle(w, pairs, monkeypatch):
+    d = len(w.n)
+    monkeypatch.setenv("ETD_TILES", ",".join(["8:16:2:1"] + ["8:16:2:%d" % (2 if pairs else 1)] * (d - 1)))
+    ctx = _api().from_workload(w, "fp32")
+    inf = ctx.info()
+    assert inf["staged"][:d] == [2] * d, inf
+    U0 = W.initial_state(w)
+    U = torch.tensor(U0, device="cuda", dtype=torch.float32)
+    ctx.run(U, 0.3, 1)
+    torch.cuda.synchronize()
+    one = U.double().cpu().numpy()
+    ctx.run(U, 0.3 + w.k, 2)
+    torch.cuda.synchronize()
+    three = U.double().cpu().numpy()
+    ctx.close()
+    e1 = rel_err(one, oracle_run(w, U0, 1, t0=0.3))
+    e3 = rel_err(three, oracle_run(w, U0, 3, t0=0.3))
+    print(f"{w.name} ({'pairs' if pairs else 'lines'}): FP32 tile kernels vs FP64 oracle: 1 step {e1:.3e}, "
+          f"3 steps {e3:.3e}")
+    assert e1 <= FP32_STEP_TOL and e3 <= 3 * FP32_STEP_TOL, (e1, e3)
+
+
+def test_tile_kernels_reject_misaligned_state(monkeypatch):
+    """A state that is not 16-byte aligned is refused before any launch."""
+    import ctypes
+    from paper_2001_11220_gb300 import _binding as B
+    w = TILE_CASES[0]
+    monkeypatch.setenv("ETD_TILES", "8:16:2:1,8:16:2:1")
+    ctx = _api().from_workload(w, "fp32")
+    buf = torch.zeros(W.initial_state(w).size + 4, device="cuda", dtype=torch.float32)
+    for call in (lambda p: ctx.lib.etd_step(ctx.ctx, ctypes.c_void_p(p), 0.0),
+                 lambda p: ctx.lib.etd_run(ctx.ctx, ctypes.c_void_p(p), 0.0, 2)):
+        with pytest.raises(B.EtdError, match="16-byte aligned"):
+            B.check(call(buf.data_ptr() + 4), ctx.ctx)
+    ctx.close()
