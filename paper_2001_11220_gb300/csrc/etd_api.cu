@@ -82,7 +82,6 @@ etd_status validate_problem(const etd_grid *grid, const double *D, const etd_rea
 
 // ------------------------------------------------------------ planning
 
-static int pick_pitch(int m) { return (m % 2 == 0) ? m + 1 : m; }
 
 static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -100,7 +99,7 @@ static StagePlan stage_plan(const Instance &I, const AxisPlan &P, int nlb, int n
   const long long n = P.nlines > 0 ? I.N / P.nlines : 1;
   const int nin = contig ? S : 3 * S;
   const int nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
-  const int pitch = pick_pitch(P.m);
+  const int pitch = exchange_pitch(P.m);
   const long long mL = (long long)P.m * P.L;  // positions per line incl. zero padding
   long long te = contig ? (long long)nlb * (mL + 1) : mL * nlb;
   te = (te + 3) & ~3LL;
@@ -143,7 +142,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   for (int b = 0; b < a; ++b) st *= I.n[b];
   P.st = st;
   P.nlines = I.N / n;
-  P.pitch = pick_pitch(P.m);
+  P.pitch = exchange_pitch(P.m);
   P.pk = 1;
   if (pack == 2) {
     // register kernel on line pairs (lo, lo + 1) of a strided FP32 axis with an even stride
@@ -235,7 +234,7 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
   P.kind = contig ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
   P.st = st;
   P.nlines = I.N / n;
-  P.pitch = pick_pitch(m);
+  P.pitch = exchange_pitch(m);
   P.pk = pk;
   const int S = I.S, nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
   StagePlan sp{};

@@ -44,7 +44,7 @@ bool plan_adjoint_axis(Instance &I, int a, int L) {
   for (int b = 0; b < a; ++b) st *= I.n[b];
   P.st = st;
   P.nlines = I.N / n;
-  P.pitch = (P.m % 2 == 0) ? P.m + 1 : P.m;
+  P.pitch = exchange_pitch(P.m);
   const long long avail = (a == 0) ? P.nlines : st;
   int nlb = pow2_floor_i(std::min<long long>(32, ETD_MAX_BLOCK_THREADS / P.m));
   while (nlb > 1 && nlb / 2 >= avail) nlb /= 2;

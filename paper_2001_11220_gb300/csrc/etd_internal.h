@@ -151,6 +151,12 @@ inline size_t adjoint_smem_bytes(int kind, int nspecies, int nlb, int pitch, siz
   return sums + (size_t)nq * nlb * sizeof(double) + 16 * sizeof(double) * 32;
 }
 
+// Row pitch of the chunk-summary exchange: odd (rows of neighbouring lines
+// fall on different banks) and at least m rounded up to 8, so the carry
+// chain can read whole batches of 8 chunks without bounds tests (chunk
+// tables are padded with zeros to the same multiple of 8).
+inline int exchange_pitch(int m) { return ((m + 7) & ~7) + 1; }
+
 // shared-memory bytes of one sweep block (pk = 2: nlb line pairs); the
 // Sherman-Morrison scalars take 8 bytes each (stored in the sweep's precision)
 inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes, int pk = 1) {

@@ -24,6 +24,8 @@
 // instructions, halving the instructions per point.
 #pragma once
 
+#include <climits>
+
 #include "etd_internal.h"
 
 namespace etd {
@@ -199,8 +201,20 @@ __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, l
       return;
     }
   }
+  const R *q = p + off;
+  if (st <= INT_MAX / L) {  // 32-bit offsets within the chunk; full chunks without per-element tests
+    const int s32 = (int)st;
+    if (cnt == L) {
 #pragma unroll
-  for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_nc(p + off + (long long)t * st) : R(0);
+      for (int t = 0; t < L; ++t) v[t] = ld_nc(q + t * s32);
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_nc(q + t * s32) : R(0);
+    }
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_nc(q + (long long)t * st) : R(0);
 }
 
 template <typename R, int L, bool CONTIG>
@@ -221,9 +235,22 @@ __device__ __forceinline__ void store_chunk(const R (&v)[L], R *__restrict__ p, 
       return;
     }
   }
+  R *q = p + off;
+  if (st <= INT_MAX / L) {
+    const int s32 = (int)st;
+    if (cnt == L) {
+#pragma unroll
+      for (int t = 0; t < L; ++t) q[t * s32] = v[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t)
+        if (t < cnt) q[t * s32] = v[t];
+    }
+    return;
+  }
 #pragma unroll
   for (int t = 0; t < L; ++t)
-    if (t < cnt) p[off + (long long)t * st] = v[t];
+    if (t < cnt) q[(long long)t * st] = v[t];
 }
 
 
@@ -401,8 +428,8 @@ __device__ __forceinline__ void load_rows(const float2 *__restrict__ p, float2 (
 // chunk summaries F = sum v b, Y = sum w b of one or two right-hand sides
 template <typename V, int L>
 __device__ __forceinline__ void pass1v(const MatTab<float> &M, int m, int j, const V (&b)[L], V &F, V &Y) {
-  const size_t ml = (size_t)m * L;
-  const V *row = rows_of(M, V()) + (size_t)j * L;
+  const int ml = m * L;
+  const V *row = rows_of(M, V()) + j * L;
   V v[L], w[L];
   load_rows<L>(row + 4 * ml, v);
   load_rows<L>(row + 5 * ml, w);
@@ -419,8 +446,8 @@ __device__ __forceinline__ void pass1v(const MatTab<float> &M, int m, int j, con
 template <typename V, int L>
 __device__ __forceinline__ void pass1x2v(const MatTab<float> &M, int m, int j, const V (&b0)[L], const V (&b1)[L],
                                          V &F0, V &Y0, V &F1, V &Y1) {
-  const size_t ml = (size_t)m * L;
-  const V *row = rows_of(M, V()) + (size_t)j * L;
+  const int ml = m * L;
+  const V *row = rows_of(M, V()) + j * L;
   V v[L], w[L];
   load_rows<L>(row + 4 * ml, v);
   load_rows<L>(row + 5 * ml, w);
@@ -447,9 +474,9 @@ template <typename V, int L, bool SAME, typename Epi>
 __device__ __forceinline__ void pass2x2v(const MatTab<float> &M0, const MatTab<float> &M1, int m, int j,
                                          const V (&b0)[L], const V (&b1)[L], Carry<V> c0, Carry<V> c1, V (&g0)[L],
                                          V (&g1)[L], Epi epi) {
-  const size_t ml = (size_t)m * L;
-  const V *r0 = rows_of(M0, V()) + (size_t)j * L;
-  const V *r1 = SAME ? r0 : rows_of(M1, V()) + (size_t)j * L;
+  const int ml = m * L;
+  const V *r0 = rows_of(M0, V()) + j * L;
+  const V *r1 = SAME ? r0 : rows_of(M1, V()) + j * L;
   {
     V ne0[L], e0[L];
     load_rows<L>(r0, ne0);
@@ -514,8 +541,8 @@ __device__ __forceinline__ void pass2x2v(const MatTab<float> &M0, const MatTab<f
 template <typename V, int L, typename Epi>
 __device__ __forceinline__ void pass2v(const MatTab<float> &M, int m, int j, const V (&b)[L], Carry<V> c, V (&g)[L],
                                        Epi epi) {
-  const size_t ml = (size_t)m * L;
-  const V *row = rows_of(M, V()) + (size_t)j * L;
+  const int ml = m * L;
+  const V *row = rows_of(M, V()) + j * L;
   {
     V ne[L], e[L];
     load_rows<L>(row, ne);
@@ -559,24 +586,53 @@ __device__ __forceinline__ double4 ld_chunk(const MatTab<double> &M, int j) {
 // Sequential carry chain of one (line, solve) over its m chunks: F[j] (chunk
 // summary) becomes the forward carry G_in[j], Y[j] the backward carry X[j+1];
 // G and X return the line's last forward value and first solution value.
+// The chain runs in batches of 8 chunks whose loads are all issued before
+// the batch's dependent FMAs (rows and chunk tables are padded to a multiple
+// of 8; padding entries may hold anything: the forward value is taken at
+// chunk m-1 and the backward carry is held at 0 past the end).
 template <typename R, typename V>
 __device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m, V &Gout, V &Xout) {
-  V G = Splat<V>::of(R(0));
-#pragma unroll 8
-  for (int j = 0; j < m; ++j) {
-    const V f = F[j];
-    F[j] = G;
-    G = vfma(Splat<V>::of(ld_chunk(M, j).x), G, f);
+  constexpr int SB = 8;
+  const V zero = Splat<V>::of(R(0));
+  const int nb = (m + SB - 1) / SB;
+  V G = zero, Gl = zero;
+  for (int b = 0; b < nb; ++b) {
+    const int j0 = b * SB;
+    V f[SB];
+    R a[SB];
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      f[k] = F[j0 + k];
+      a[k] = ld_chunk(M, j0 + k).x;
+    }
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      F[j0 + k] = G;
+      G = vfma(Splat<V>::of(a[k]), G, f[k]);
+      Gl = (j0 + k == m - 1) ? G : Gl;
+    }
   }
-  V X = Splat<V>::of(R(0));
-#pragma unroll 8
-  for (int j = m - 1; j >= 0; --j) {
-    const typename V4T<R>::T c = ld_chunk(M, j);
-    const V y = vfma(Splat<V>::of(c.y), F[j], Y[j]);
-    Y[j] = X;
-    X = vfma(Splat<V>::of(c.z), X, y);
+  V X = zero;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int j0 = b * SB;
+    V gi[SB], yv[SB];
+    R cy[SB], cz[SB];
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      const typename V4T<R>::T c = ld_chunk(M, j0 + k);
+      gi[k] = F[j0 + k];
+      yv[k] = Y[j0 + k];
+      cy[k] = c.y;
+      cz[k] = c.z;
+    }
+#pragma unroll
+    for (int k = SB - 1; k >= 0; --k) {
+      const V y = vfma(Splat<V>::of(cy[k]), gi[k], yv[k]);
+      Y[j0 + k] = X;
+      X = (j0 + k < m) ? vfma(Splat<V>::of(cz[k]), X, y) : zero;
+    }
   }
-  Gout = G;
+  Gout = Gl;
   Xout = X;
 }
 
@@ -613,8 +669,8 @@ __device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, V *sF, V 
     const int l = u % nlb;
     const int q = q0 + u / nlb;
     const MatTab<R> &M = mat(q);
-    V *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    V *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V *F = sF + (q * nlb + l) * pitch;  // shared-memory offsets in 32-bit arithmetic
+    V *Y = sY + (q * nlb + l) * pitch;
     // forward: block map G_out = a G_in + b
     V a = one, b = zero;
     for (int jj = j0; jj < j1; ++jj) {
@@ -664,7 +720,7 @@ __device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, V *sF, V 
       X = vfma(Splat<V>::of(ld_chunk(M, jj).z), X, yv);
     }
     const V X0 = v_shfl(X, 0);  // first position of the line
-    if (lane == 0) put_sigma(sSig + ((size_t)q * nlb + l) * PK, M, X0, Gtot);
+    if (lane == 0) put_sigma(sSig + (q * nlb + l) * PK, M, X0, Gtot);
   }
 }
 
@@ -688,12 +744,12 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, 
     int ms, mg;
     solve_matrix<R, S, KIND>(q, ms, mg);
     const MatTab<R> &M = A.mat[ms][mg];
-    V *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    V *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    V *F = sF + (q * nlb + l) * pitch;  // shared-memory offsets in 32-bit arithmetic
+    V *Y = sY + (q * nlb + l) * pitch;
     V G, X;
     chain_line<R, V>(M, F, Y, m, G, X);
     // cyclic line: y_0 = X, y_{p-1} = G
-    put_sigma(sSig + ((size_t)q * nlb + l) * PK, M, X, G);
+    put_sigma(sSig + (q * nlb + l) * PK, M, X, G);
   }
 }
 
@@ -765,19 +821,20 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     else pass1x2v<V, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
   };
   V *sF = reinterpret_cast<V *>(exch);
-  V *sY = sF + (size_t)NQ * nlb * pitch;
-  R *sSig = reinterpret_cast<R *>(exch + ((2 * (size_t)NQ * nlb * pitch * sizeof(V) + 15) & ~(size_t)15));
-  const size_t myidx = (size_t)l * pitch + j;
+  V *sY = sF + NQ * nlb * pitch;
+  R *sSig = reinterpret_cast<R *>(exch + ((2 * NQ * nlb * pitch * (int)sizeof(V) + 15) & ~15));
+  const int myidx = l * pitch + j;
+  const int qstride = nlb * pitch;
   auto put = [&](int q, V F, V Y) {
     if (thr_ok) {
-      sF[(size_t)q * nlb * pitch + myidx] = F;
-      sY[(size_t)q * nlb * pitch + myidx] = Y;
+      sF[q * qstride + myidx] = F;
+      sY[q * qstride + myidx] = Y;
     }
   };
   auto carries = [&](int q, V &Gin, V &Xr, V &sig) {
-    Gin = sF[(size_t)q * nlb * pitch + myidx];
-    Xr = sY[(size_t)q * nlb * pitch + myidx];
-    sig = get_sigma(sSig + ((size_t)q * nlb + l) * PK, zero);
+    Gin = sF[q * qstride + myidx];
+    Xr = sY[q * qstride + myidx];
+    sig = get_sigma(sSig + (q * nlb + l) * PK, zero);
   };
   auto carry = [&](int q) {  // FP32 form: ns = -sigma
     Carry<V> cq;

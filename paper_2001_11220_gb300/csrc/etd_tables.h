@@ -93,7 +93,7 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
   T.m = m;
   T.pos.assign((size_t)4 * L * m, 0.0);
   T.sum.assign((size_t)2 * L * m, 0.0);
-  T.chunk.assign((size_t)4 * m, 0.0);
+  T.chunk.assign((size_t)4 * ((m + 7) & ~7), 0.0);  // zero entries pad to a multiple of 8 chunks
   T.e1.assign((size_t)L * m, 1.0);
   T.v1.assign((size_t)L * m, 0.0);
   T.w1.assign((size_t)L * m, 0.0);

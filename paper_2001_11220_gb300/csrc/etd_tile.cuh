@@ -148,7 +148,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
     nvalid = (int)min((long long)NLB, A.st - lo0);
   }
   constexpr int NIN = CONTIG ? S : 3 * S;  // staged input fields (FIRST: U; else c_U, c_f, w)
-  auto tile_of = [&](int field, int s) { return tiles + (size_t)(field * S + s) * ft; };
+  auto tile_of = [&](int field, int s) { return tiles + (field * S + s) * ft; };  // 32-bit offsets
 #pragma unroll
   for (int f = 0; f < NIN; ++f) {
     const int field = CONTIG ? 0 : f / S, s = CONTIG ? f : f % S;
@@ -165,7 +165,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
       for (int q = tid; q < NF * NLB * npad; q += blockDim.x) {
         const int f = q / (NLB * npad), r = q - f * (NLB * npad);
         const int l = r / npad, i = n + (r - l * npad);
-        float *t = tiles + (size_t)f * ft;
+        float *t = tiles + f * ft;
         if constexpr (CONTIG) t[l * xp + i] = 0.f;
         else t[(i / L) * CS + (i % L) * NLB + l] = 0.f;
       }
@@ -220,20 +220,21 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
 
   // ---- exchange space (after the field tiles)
   V *sF = reinterpret_cast<V *>(smem + A.sp.off_sum);
-  V *sY = sF + (size_t)NQ * W * A.pitch;
+  V *sY = sF + NQ * W * A.pitch;
   float *sSig = reinterpret_cast<float *>(smem + A.sp.off_sig);
-  const size_t myidx = (size_t)u * A.pitch + j;
+  const int myidx = u * A.pitch + j;
+  const int qstride = W * A.pitch;
   auto put = [&](int q, V F, V Y) {
     if (thr_ok) {
-      sF[(size_t)q * W * A.pitch + myidx] = F;
-      sY[(size_t)q * W * A.pitch + myidx] = Y;
+      sF[q * qstride + myidx] = F;
+      sY[q * qstride + myidx] = Y;
     }
   };
   auto carry = [&](int q) {
     Carry<V> c;
-    c.G = sF[(size_t)q * W * A.pitch + myidx];
-    c.X = sY[(size_t)q * W * A.pitch + myidx];
-    c.ns = vneg(get_sigma(sSig + ((size_t)q * W + u) * PK, zero));
+    c.G = sF[q * qstride + myidx];
+    c.X = sY[q * qstride + myidx];
+    c.ns = vneg(get_sigma(sSig + (q * W + u) * PK, zero));
     return c;
   };
   const V k9 = Splat<V>::of(9.f), km8 = Splat<V>::of(-8.f);
