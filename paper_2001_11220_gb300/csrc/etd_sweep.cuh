@@ -771,6 +771,52 @@ __device__ __forceinline__ R source_of(const SweepArgs<R> &A, R q) {
   return A.rpR[0] * ((A.rpR[1] * A.src_lfR - R(1)) * q + rdiv(q, R(1) + q));
 }
 
+// Manufactured source at the L positions i0 .. i0+L-1 of a chunk of one line
+// (PK = 1) or line pair (PK = 2): zero without a source and past the end of
+// the line (cnt positions inside).  Full FP32 chunks read phi four at a time
+// (chunk starts are multiples of 4, the phi tables 16-byte aligned).
+template <typename R, int L, int PK>
+__device__ __forceinline__ void chunk_sources(const SweepArgs<R> &A, typename LaneT<R, PK>::T qbase, int i0, int cnt,
+                                              typename LaneT<R, PK>::T (&src)[L]) {
+  using V = typename LaneT<R, PK>::T;
+  const V zero = Splat<V>::of(R(0));
+  if (!v_nonzero(qbase)) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) src[t] = zero;
+    return;
+  }
+  const R *phia = A.phi[A.axis] + i0;
+  R ph[L];
+  bool full = false;
+  if constexpr (sizeof(R) == 4 && L % 4 == 0) {
+    if (cnt == L) {
+#pragma unroll
+      for (int t = 0; t < L; t += 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(phia + t));
+        ph[t] = q.x;
+        ph[t + 1] = q.y;
+        ph[t + 2] = q.z;
+        ph[t + 3] = q.w;
+      }
+      full = true;
+    }
+  }
+  if (!full) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) ph[t] = (t < cnt) ? __ldg(phia + t) : R(0);
+  }
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    if constexpr (PK == 1) src[t] = source_of(A, qbase * ph[t]);
+    else src[t] = make_float2(source_of(A, qbase.x * ph[t]), source_of(A, qbase.y * ph[t]));
+  }
+  if (cnt < L) {
+#pragma unroll
+    for (int t = 0; t < L; ++t)
+      if (t >= cnt) src[t] = zero;
+  }
+}
+
 // One fused sweep of one block on register-resident chunks.  load(f, s, v)
 // fills v with input field f (FIRST: 0 = U_n; MIDDLE/LAST: 0 = c_U, 1 = c_f,
 // 2 = w) of species s, zero past the end of the line; store(f, s, v) writes
@@ -786,16 +832,6 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
   const int l = c.l, j = c.j, cnt = c.cnt, i0 = c.i0;
   const bool thr_ok = c.thr_ok;
   const V zero = Splat<V>::of(R(0));
-  const R *phia = A.phi[A.axis];
-  auto src_at = [&](int t) -> V {  // manufactured source at position t of the chunk
-    if (!v_nonzero(c.qbase) || t >= cnt) return zero;
-    const R ph = __ldg(phia + i0 + t);
-    if constexpr (PK == 1) {
-      return source_of(A, c.qbase * ph);
-    } else {
-      return make_float2(source_of(A, c.qbase.x * ph), source_of(A, c.qbase.y * ph));
-    }
-  };
   auto react = [&](const V (&u)[S], V (&f)[S], V src) {
     if constexpr (PK == 1) {
       reaction_point<R, S>(A, u, f, src);
@@ -853,18 +889,28 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       const V kk = Splat<V>::of(A.kR);
 #pragma unroll
       for (int s = 0; s < S; ++s) load(0, s, cu[s]);
+      V src[L];
+      chunk_sources<R, L, PK>(A, c.qbase, i0, cnt, src);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         V u[S], f[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = cu[s][t];
-        react(u, f, src_at(t));
+        react(u, f, src[t]);
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          cf[s][t] = (t < cnt) ? f[s] : zero;
-          w[s][t] = vfma(kk, cf[s][t], cu[s][t]);
-        }
+        for (int s = 0; s < S; ++s) cf[s][t] = f[s];
       }
+      if (cnt < L) {  // F = 0 past the end of the line
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int t = 0; t < L; ++t)
+            if (t >= cnt) cf[s][t] = zero;
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int t = 0; t < L; ++t) w[s][t] = vfma(kk, cf[s][t], cu[s][t]);
     } else {
 #pragma unroll
       for (int s = 0; s < S; ++s) {
@@ -964,15 +1010,17 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     const R k = A.kR;
     const V k2 = Splat<V>::of(R(2) * k), kk = Splat<V>::of(k), k15 = Splat<V>::of(R(1.5) * k),
             k05 = Splat<V>::of(R(0.5) * k), k8 = Splat<V>::of(R(8));
+    V src[L];
+    chunk_sources<R, L, PK>(A, c.qbase, i0, cnt, src);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       V u[S], f[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) u[s] = w[s][t];
-      react(u, f, src_at(t));
+      react(u, f, src[t]);
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const V fs = (t < cnt) ? f[s] : zero;
+        const V fs = (cnt == L || t < cnt) ? f[s] : zero;
         const V a = cu[s][t], b = cf[s][t];
         cu[s][t] = vfma(k9, a, vfma(k2, b, vmul(kk, fs)));
         cf[s][t] = vfma(k8, a, vfma(k15, b, vmul(k05, fs)));

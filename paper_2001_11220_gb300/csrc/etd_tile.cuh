@@ -194,13 +194,6 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
                           line_source_base(A, false, 0, lo0 + lane_line + 1, hi, A.exp_mtR));
     }
   }
-  const float *phia = A.phi[A.axis];
-  auto src_at = [&](int t) -> V {
-    if (!v_nonzero(qbase) || t >= cnt) return zero;
-    const float ph = __ldg(phia + i0 + t);
-    if constexpr (PK == 1) return source_of(A, qbase * ph);
-    else return make_float2(source_of(A, qbase.x * ph), source_of(A, qbase.y * ph));
-  };
   auto react = [&](const V (&uu)[S], V (&ff)[S], V src) {
     if constexpr (PK == 1) {
       reaction_point<float, S>(A, uu, ff, src);
@@ -240,54 +233,82 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
   const V k9 = Splat<V>::of(9.f), km8 = Splat<V>::of(-8.f);
 
   if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
+    // pass 1: five solves per species share one exchange.  FIRST computes
+    // F(U_n, t_n) and w* = U_n + k F in registers, runs pass 1 on them and
+    // keeps F and w* in the c_f and w tiles for pass 2.
     if constexpr (CONTIG) {
-      // F(U_n, t_n) and w* = U_n + k F into the c_f and w tiles (the thread's own positions)
+      V uu[S][L], ff[S][L];
       if (thr_ok) {
-        V uu[S][L];
 #pragma unroll
         for (int s = 0; s < S; ++s) ref(0, s).get(uu[s]);
-        V ff[S][L];
+        V src[L];
+        chunk_sources<float, L, PK>(A, qbase, i0, cnt, src);
 #pragma unroll
         for (int t = 0; t < L; ++t) {
           V us[S], fs[S];
 #pragma unroll
           for (int s = 0; s < S; ++s) us[s] = uu[s][t];
-          react(us, fs, src_at(t));
+          react(us, fs, src[t]);
 #pragma unroll
-          for (int s = 0; s < S; ++s) ff[s][t] = (t < cnt) ? fs[s] : zero;
+          for (int s = 0; s < S; ++s) ff[s][t] = fs[s];
         }
-        const V kk = Splat<V>::of(A.kR);
+        if (cnt < L) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          ref(1, s).put(ff[s]);
+          for (int s = 0; s < S; ++s)
 #pragma unroll
-          for (int t = 0; t < L; ++t) uu[s][t] = vfma(kk, ff[s][t], uu[s][t]);
-          ref(2, s).put(uu[s]);
+            for (int t = 0; t < L; ++t)
+              if (t >= cnt) ff[s][t] = zero;
         }
-      }
-    }
-    // pass 1: five solves per species share one exchange
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      V b0[L], b1[L], b2[L];
-      if (thr_ok) {
-        ref(0, s).get(b0);
-        ref(1, s).get(b1);
-        ref(2, s).get(b2);
       } else {
 #pragma unroll
-        for (int t = 0; t < L; ++t) b0[t] = b1[t] = b2[t] = zero;
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int t = 0; t < L; ++t) uu[s][t] = ff[s][t] = zero;
       }
+      const V kk = Splat<V>::of(A.kR);
       const int jj = thr_ok ? j : 0;
-      V F0, Y0, F1, Y1;
-      pass1x2v<V, L>(A.mat[s][1], m, jj, b0, b1, F0, Y0, F1, Y1);
-      put(5 * s + 0, F0, Y0);
-      put(5 * s + 2, F1, Y1);
-      pass1x2v<V, L>(A.mat[s][2], m, jj, b0, b1, F0, Y0, F1, Y1);
-      put(5 * s + 1, F0, Y0);
-      put(5 * s + 3, F1, Y1);
-      pass1v<V, L>(A.mat[s][0], m, jj, b2, F0, Y0);
-      put(5 * s + 4, F0, Y0);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        V ww[L];
+#pragma unroll
+        for (int t = 0; t < L; ++t) ww[t] = vfma(kk, ff[s][t], uu[s][t]);
+        if (thr_ok) {
+          ref(1, s).put(ff[s]);
+          ref(2, s).put(ww);
+        }
+        V F0, Y0, F1, Y1;
+        pass1x2v<V, L>(A.mat[s][1], m, jj, uu[s], ff[s], F0, Y0, F1, Y1);
+        put(5 * s + 0, F0, Y0);
+        put(5 * s + 2, F1, Y1);
+        pass1x2v<V, L>(A.mat[s][2], m, jj, uu[s], ff[s], F0, Y0, F1, Y1);
+        put(5 * s + 1, F0, Y0);
+        put(5 * s + 3, F1, Y1);
+        pass1v<V, L>(A.mat[s][0], m, jj, ww, F0, Y0);
+        put(5 * s + 4, F0, Y0);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        V b0[L], b1[L], b2[L];
+        if (thr_ok) {
+          ref(0, s).get(b0);
+          ref(1, s).get(b1);
+          ref(2, s).get(b2);
+        } else {
+#pragma unroll
+          for (int t = 0; t < L; ++t) b0[t] = b1[t] = b2[t] = zero;
+        }
+        const int jj = thr_ok ? j : 0;
+        V F0, Y0, F1, Y1;
+        pass1x2v<V, L>(A.mat[s][1], m, jj, b0, b1, F0, Y0, F1, Y1);
+        put(5 * s + 0, F0, Y0);
+        put(5 * s + 2, F1, Y1);
+        pass1x2v<V, L>(A.mat[s][2], m, jj, b0, b1, F0, Y0, F1, Y1);
+        put(5 * s + 1, F0, Y0);
+        put(5 * s + 3, F1, Y1);
+        pass1v<V, L>(A.mat[s][0], m, jj, b2, F0, Y0);
+        put(5 * s + 4, F0, Y0);
+      }
     }
     __syncthreads();
     scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ);
@@ -359,15 +380,17 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
         ref(0, s).get(f1[s]);
         ref(1, s).get(f2[s]);
       }
+      V src[L];
+      chunk_sources<float, L, PK>(A, qbase, i0, cnt, src);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         V uu[S], ff[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) uu[s] = us[s][t];
-        react(uu, ff, src_at(t));
+        react(uu, ff, src[t]);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          const V fs = (t < cnt) ? ff[s] : zero;
+          const V fs = (cnt == L || t < cnt) ? ff[s] : zero;
           const V a = f1[s][t], b = f2[s][t];
           f1[s][t] = vfma(k9, a, vfma(k2, b, vmul(kk, fs)));
           f2[s][t] = vfma(k8, a, vfma(k15, b, vmul(k05, fs)));
