@@ -311,7 +311,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def timed(ctx, U, K, profile):
+    def timed(ctx, U, K, profile, tag="etd_timed_steps"):
         # warm-up (untimed), then K steps between a barrier + synchronize on both sides
         ctx.run(U, 0.0, W_)
         torch.cuda.synchronize()
@@ -326,7 +326,7 @@ def main():
             barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("etd_timed_steps")   # profilers can keep just these launches
+        torch.cuda.nvtx.range_push(tag)   # profilers can keep just these launches
         e0.record(stream)
         ctx.run(U, W_ * w.k, K)
         e1.record(stream)
@@ -385,7 +385,7 @@ def main():
             ctx64.autotune(Wk)
             del Wk
         K64 = max(3, K // 5)
-        ms64, _ = timed(ctx64, U64, K64, profile=False)
+        ms64, _ = timed(ctx64, U64, K64, profile=False, tag="etd_timed_steps_fp64")
         v64 = units_per_step * K64 / (ms64 / 1e3)
         # accuracy of FP32 against the FP64 path (which matches the FP64 oracle) after 5 steps
         with torch.cuda.stream(stream):

@@ -100,8 +100,8 @@ typedef struct {
   int64_t npoints;               /* points per species */
   int64_t state_bytes;           /* bytes of one state U */
   int64_t scratch_bytes;         /* device scratch the context owns */
-  int64_t algorithmic_bytes;     /* HBM bytes one step must move (sweep floor: (4d-2) fields
-                                    read or written per species per point) */
+  int64_t algorithmic_bytes;     /* HBM bytes one step must move (sweep floor: 6d-4 fields
+                                    read or written per species per point: 8 in 2D, 14 in 3D) */
   int32_t launches_per_step;     /* kernels one etd_step enqueues */
   int32_t chunk[3];              /* chunk length per axis (elements per thread) */
   int32_t lines_per_block[3];    /* lines per tile / block per axis */

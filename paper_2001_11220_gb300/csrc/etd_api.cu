@@ -654,7 +654,8 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   info->npoints = N;
   info->state_bytes = (int64_t)I.S * N * I.real_bytes;
   info->scratch_bytes = scratch;
-  info->algorithmic_bytes = (int64_t)(4 * I.dim - 2) * I.S * N * I.real_bytes;
+  // fused schedule: first sweep 1 in + 3 out, middle sweeps 3 + 3, last sweep 3 + 1
+  info->algorithmic_bytes = (int64_t)(6 * I.dim - 4) * I.S * N * I.real_bytes;
   info->launches_per_step = launches;
   for (int a = 0; a < I.dim; ++a) {
     info->chunk[a] = I.plan[a].L;
