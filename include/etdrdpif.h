@@ -106,9 +106,11 @@ typedef struct {
   int32_t chunk[3];              /* chunk length per axis (elements per thread) */
   int32_t lines_per_block[3];    /* lines per tile / block per axis */
   int32_t staged[3];             /* 0: register kernel, 1: persistent shared-memory-staged kernel,
-                                    2: FP32 tile kernel (lines_per_block then counts line units) */
+                                    2: FP32 tile kernel (lines_per_block then counts line units),
+                                    3: segmented register kernel (long lines split over blocks) */
   int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
-                                    (lines_per_block then counts pairs), 1: one line per thread */
+                                    (lines_per_block then counts pairs), 1: one line per thread;
+                                    segmented kernel: chunks per segment */
 } etd_info;
 
 /* Create a context for one problem.  Validates every argument

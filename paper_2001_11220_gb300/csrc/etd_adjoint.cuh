@@ -114,7 +114,7 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
     R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
     R G, X;
-    chain_line<R, R>(M, F, Y, m, G, X);
+    chain_line<R, R>(M, F, Y, m, 0, R(0), R(0), G, X);
     sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X + M.sm_c * (double)G) * M.sm_inv : 0.0;
   }
 }

@@ -2,6 +2,7 @@
 // launch planning and the forward step.  See include/etdrdpif.h.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstdarg>
@@ -144,6 +145,8 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   P.nlines = I.N / n;
   P.pitch = exchange_pitch(P.m);
   P.pk = 1;
+  P.mx = P.m;
+  P.nseg = 1;
   if (pack == 2) {
     // register kernel on line pairs (lo, lo + 1) of a strided FP32 axis with an even stride
     if (I.real_bytes != 4 || a == 0 || st % 2 != 0 || L != 8) return false;
@@ -236,6 +239,8 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
   P.nlines = I.N / n;
   P.pitch = exchange_pitch(m);
   P.pk = pk;
+  P.mx = m;
+  P.nseg = 1;
   const int S = I.S, nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
   StagePlan sp{};
   sp.staged = 2;
@@ -273,6 +278,43 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
   sp.ntiles = P.nblocks;
   P.sp = sp;
   return true;
+}
+
+// Segmented register kernel for long lines: blocks of nlb lines x mx chunks
+// (mx a multiple of 8, m > mx), nseg = ceil(m / mx) blocks along every line
+// (summary, carry and solve launches, see SegPhase)
+bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx) {
+  AxisPlan &P = I.plan[a];
+  const long long n = I.n[a];
+  const int m = (int)((n + L - 1) / L);
+  if ((L != 4 && L != 8 && L != 16) || mx < 8 || mx % 8 != 0 || m <= mx || nlb < 1 || nlb * mx > ETD_MAX_BLOCK_THREADS)
+    return false;
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  P.L = L;
+  P.m = m;
+  P.kind = (a == 0) ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
+  P.st = st;
+  P.nlines = I.N / n;
+  P.pk = 1;
+  P.sp = StagePlan{};
+  P.mx = mx;
+  P.nseg = (m + mx - 1) / mx;
+  P.pitch = exchange_pitch(mx);
+  P.nlb = nlb;
+  long long line_blocks;
+  if (a == 0) {
+    P.nlo_blocks = 1;
+    line_blocks = (P.nlines + nlb - 1) / nlb;
+  } else {
+    P.nlo_blocks = (int)((st + nlb - 1) / nlb);
+    line_blocks = (long long)P.nlo_blocks * (I.N / (st * n));
+  }
+  if (line_blocks * P.nseg > INT_MAX) return false;
+  P.nblocks = (int)(line_blocks * P.nseg);
+  P.nthreads = nlb * mx;
+  P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1);
+  return P.smem <= 200 * 1024;
 }
 
 // tile kernels move U with 16-byte copies
@@ -316,6 +358,11 @@ static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::
     M.rows1 = (const float *)arena.put(r1.data(), r1.size() * sizeof(float), err);
     M.rows2 = (const float2 *)arena.put(r2.data(), r2.size() * sizeof(float), err);
   }
+  M.segc = nullptr;
+  if (!T.segc.empty()) {
+    std::vector<R> sc(T.segc.begin(), T.segc.end());
+    M.segc = (const typename V4T<R>::T *)arena.put(sc.data(), sc.size() * sizeof(R), err);
+  }
   M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;
@@ -334,13 +381,32 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
         for (int tr = 0; tr < 2; ++tr) {
           const double r = (I.k / gammas[g]) * I.D[s] / (h * h);
           HostTab T;
-          build_tab((int)I.n[a], I.bc[a], r, tr != 0, I.plan[a].L, T);
+          build_tab((int)I.n[a], I.bc[a], r, tr != 0, I.plan[a].L, T, I.plan[a].mx, I.plan[a].nseg);
           if (I.real_bytes == 8)
             upload_tab<double>(I.arena, T, I.tab64[tr][a][s][g], I.owned, err);
           else
             upload_tab<float>(I.arena, T, I.tab32[tr][a][s][g], I.owned, err);
           if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
         }
+  }
+  AxisPlan &P = I.plan[a];
+  if (P.nseg > 1) {
+    // segment summaries and carries (2 values per solve, line and segment) and scalars
+    const int nq = (P.kind == SWEEP_LAST) ? 3 * I.S : 5 * I.S;
+    const size_t need = ((size_t)4 * nq * P.nlines * P.nseg + (size_t)nq * P.nlines) * I.real_bytes;
+    if (P.seg_bytes < need) {
+      if (P.seg_buf) {
+        cudaFree(P.seg_buf);
+        for (auto &o : I.owned)
+          if (o == P.seg_buf) o = nullptr;
+        P.seg_buf = nullptr;
+        P.seg_bytes = 0;
+      }
+      cudaError_t e = cudaMalloc(&P.seg_buf, need);
+      if (e != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "segment scratch of %zu bytes", need);
+      I.owned.push_back(P.seg_buf);
+      P.seg_bytes = need;
+    }
   }
   return ETD_OK;
 }
@@ -411,7 +477,47 @@ void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
   A.axis = a;
   A.pk = P.pk;
   A.sp = P.sp;
+  A.mx = P.mx;
+  A.nseg = P.nseg;
+  A.segphase = SEG_WHOLE;
+  if (P.nseg > 1) {
+    const int nq = (P.kind == SWEEP_LAST) ? 3 * I.S : 5 * I.S;
+    const size_t pairs = (size_t)2 * nq * P.nlines * P.nseg;
+    A.seg_sum = (R *)P.seg_buf;
+    A.seg_car = A.seg_sum + pairs;
+    A.seg_sig = A.seg_car + pairs;
+  }
 }
+
+// One sweep of axis a: a single launch, or for a segmented plan the summary,
+// carry and solve launches (LAST: P summaries, P carries, P solve + T/S
+// summaries, T/S carries, final solve).
+template <typename R>
+cudaError_t run_sweep(const Instance &I, int a, SweepArgs<R> &A, cudaStream_t s) {
+  const AxisPlan &P = I.plan[a];
+  if (P.nseg <= 1) return launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+  const int S = I.S;
+  auto sweep = [&](int phase) {
+    A.segphase = phase;
+    return launch_sweep(A, S, P.L, P.kind, P.nthreads, P.smem, s);
+  };
+  cudaError_t e = sweep(SEG_SUMMARY);
+  if (e != cudaSuccess) return e;
+  if (P.kind != SWEEP_LAST) {
+    e = launch_seg_carry(A, S, P.kind, 0, 5 * S, s);
+    if (e != cudaSuccess) return e;
+    return sweep(SEG_SOLVE);
+  }
+  e = launch_seg_carry(A, S, P.kind, 0, S, s);
+  if (e != cudaSuccess) return e;
+  e = sweep(SEG_SOLVE);
+  if (e != cudaSuccess) return e;
+  e = launch_seg_carry(A, S, P.kind, S, 2 * S, s);
+  if (e != cudaSuccess) return e;
+  return sweep(SEG_FINAL);
+}
+template cudaError_t run_sweep<float>(const Instance &, int, SweepArgs<float> &, cudaStream_t);
+template cudaError_t run_sweep<double>(const Instance &, int, SweepArgs<double> &, cudaStream_t);
 template void fill_args<float>(const Instance &, int, int, SweepArgs<float> &);
 template void fill_args<double>(const Instance &, int, int, SweepArgs<double> &);
 
@@ -464,7 +570,7 @@ static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t
     cudaEvent_t ev0;
     cudaError_t e = prof_begin(prof, s, ev0);
     if (e != cudaSuccess) return e;
-    e = launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+    e = run_sweep<R>(I, a, A, s);
     if (e != cudaSuccess) return e;
     e = prof_end(prof, s, P.kind, ev0);
     if (e != cudaSuccess) return e;
@@ -496,7 +602,8 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   for (int j = 0; j < 8; ++j) I.rp[j] = rx->params[j];
   I.real_bytes = precision == ETD_FP64 ? 8 : 4;
   // ETD_TILES="L:nlb:kernel[:pack],..." (one entry per axis; kernel 0
-  // register, 1 staged, 2 tile with nlb lines per block) forces tile shapes,
+  // register, 1 staged, 2 tile with nlb lines per block, 3 segmented register
+  // kernel with the fourth field = chunks per segment) forces tile shapes,
   // e.g. to reproduce an autotuned configuration in a profiler run
   const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
@@ -509,9 +616,10 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
         if (p) ++p;
       }
       if (p && sscanf(p, "%d:%d:%d:%d", &fl, &fn, &fs, &fp) >= 3 && (fl == 4 || fl == 8 || fl == 16)) {
-        if (fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)
-                    : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1))
-          continue;
+        const bool ok = fs == 3   ? plan_axis_seg(I, a, fl, fn, fp)
+                        : fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)
+                                  : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1);
+        if (ok) continue;
       }
     }
     while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
@@ -650,7 +758,13 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     N += J.N;
     scratch += 3LL * J.S * J.N * J.real_bytes;
   }
-  launches = ctx->batched ? I.dim : I.dim;
+  // one launch per sweep; a segmented sweep takes 3 (LAST: 5)
+  launches = 0;
+  for (int a = 0; a < I.dim; ++a)
+    launches += ctx->batched || I.plan[a].nseg <= 1 ? 1 : (I.plan[a].kind == SWEEP_LAST ? 5 : 3);
+  for (const Instance &J : ctx->inst)
+    for (int a = 0; a < J.dim; ++a)
+      if (J.plan[a].nseg > 1) scratch += (long long)J.plan[a].seg_bytes;
   info->npoints = N;
   info->state_bytes = (int64_t)I.S * N * I.real_bytes;
   info->scratch_bytes = scratch;
@@ -660,8 +774,8 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   for (int a = 0; a < I.dim; ++a) {
     info->chunk[a] = I.plan[a].L;
     info->lines_per_block[a] = I.plan[a].nlb;
-    info->staged[a] = I.plan[a].sp.staged;
-    info->pack[a] = I.plan[a].pk;
+    info->staged[a] = I.plan[a].nseg > 1 ? 3 : I.plan[a].sp.staged;
+    info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
   }
   return ETD_OK;
 }

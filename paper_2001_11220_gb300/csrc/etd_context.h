@@ -60,6 +60,10 @@ struct AxisPlan {
   long long nlines = 1;
   size_t smem = 0;     // register kernel: shared memory bytes
   int pk = 1;          // 2: register kernel on FP32 line pairs (nlb counts pairs)
+  int mx = 1;          // chunks per block along the line (= m unless segmented)
+  int nseg = 1;        // segments per line (> 1: segmented sweep, see SegPhase)
+  void *seg_buf = nullptr;  // segmented sweeps: summaries, carries, scalars (owned)
+  size_t seg_bytes = 0;
   StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel
 };
 
@@ -90,6 +94,10 @@ struct Instance {
   DeviceArena arena;
   std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
 };
+
+// one sweep of axis a (segmented plans: all of its launches), stream-ordered
+template <typename R>
+cudaError_t run_sweep(const Instance &I, int a, SweepArgs<R> &A, cudaStream_t s);
 
 struct GraphKey {
   const void *U;

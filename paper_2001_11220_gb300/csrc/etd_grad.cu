@@ -125,6 +125,8 @@ void geometry(const AxisPlan &P, const Instance &I, int a, SweepArgs<R> &A) {
   A.n = (int)I.n[a];
   A.nlo_blocks = P.nlo_blocks;
   A.m = P.m;
+  A.mx = P.m;  // adjoint sweeps keep whole lines in one block
+  A.nseg = 1;
   A.nlb = P.nlb;
   A.pitch = P.pitch;
   A.nblocks = P.nblocks;
@@ -165,8 +167,7 @@ cudaError_t forward_intermediates(const Instance &I, const R *Un, double t, R *f
     A.t_eval = t;
     A.exp_mt = std::exp(-t);
     A.exp_mtR = (R)A.exp_mt;
-    const AxisPlan &P = I.plan[a];
-    cudaError_t e = launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+    cudaError_t e = run_sweep<R>(I, a, A, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

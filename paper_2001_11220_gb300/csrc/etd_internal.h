@@ -55,6 +55,9 @@ template <typename R> struct MatTab {
   const R *e1, *v1, *w1, *z1;
   const R *rows1;
   const typename V2T<R>::T *rows2;
+  // segmented sweeps: per segment of mx chunks (A_seg, K_seg, B_seg, 0) with
+  // G_out = A_seg G_in + F_seg and X_start = Y_seg + K_seg G_in + B_seg X_end
+  const typename V4T<R>::T *segc;
   double r;       // interior off-diagonal magnitude
   double sm_c;    // v_{p-1} of the Sherman-Morrison rank-one term (periodic)
   double sm_inv;  // 1 / (1 + v.z)                                  (periodic)
@@ -102,6 +105,16 @@ template <typename R> struct SweepArgs {
   R rpR[8];
   int axis;        // swept axis
   int pk;          // 2: register kernel on line pairs (nlb counts pairs), else 1
+  // Segmented sweeps: a line longer than one block's mx chunks is split over
+  // nseg blocks.  Summary launches write each segment's zero-carry chunk-chain
+  // values, a carry launch chains the segments of every line, and solve
+  // launches start their chunk chains from those carries (SegPhase).
+  int mx;          // chunks per block along the line (= m for whole-line blocks)
+  int nseg;        // segments per line (1: whole lines)
+  int segphase;    // SegPhase of this launch
+  R *seg_sum;      // [solve][line][segment] (F_seg, Y_seg), zero carries
+  R *seg_car;      // [solve][line][segment] (G_in, X_end)
+  R *seg_sig;      // [solve][line] Sherman-Morrison scalar of the whole line
   StagePlan sp;    // staged-kernel plan
   // adjoint sweeps only
   MatTab<R> matT[MAX_SPECIES][3];  // tables of the transposed line matrices
@@ -109,6 +122,13 @@ template <typename R> struct SweepArgs {
   double *acc;                     // device accumulators: dL/dD[MAX_SPECIES], dL/dparams[8]
   double invD[MAX_SPECIES];        // 1 / D_s
 };
+
+// Launch phases of a segmented sweep.  FIRST/MIDDLE: SEG_SUMMARY writes the
+// segment summaries of all solves, SEG_SOLVE solves from the carries.  LAST:
+// SEG_SUMMARY covers the P solves; SEG_SOLVE solves P from its carries, forms
+// U*, F* and f1, f2 and writes the summaries of the T and S solves; SEG_FINAL
+// solves everything from its carries.  SEG_WHOLE: lines are not split.
+enum SegPhase { SEG_WHOLE = 0, SEG_SUMMARY = 1, SEG_SOLVE = 2, SEG_FINAL = 3 };
 
 enum AdjKind { ADJ_FIRST = 0, ADJ_MIDDLE = 1, ADJ_LAST = 2 };
 
@@ -134,6 +154,10 @@ cudaError_t launch_tile_middle(const SweepArgs<float> &a, int nspecies, int L, i
                                size_t smem, cudaStream_t s);
 cudaError_t launch_tile_last(const SweepArgs<float> &a, int nspecies, int L, int NLB, int pk, int nthreads,
                              size_t smem, cudaStream_t s);
+
+// carries of the segments of every line for solves q0 .. q0+nq-1 (segmented sweeps)
+cudaError_t launch_seg_carry(const SweepArgs<float> &a, int nspecies, int kind, int q0, int nq, cudaStream_t s);
+cudaError_t launch_seg_carry(const SweepArgs<double> &a, int nspecies, int kind, int q0, int nq, cudaStream_t s);
 
 cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);

@@ -583,19 +583,22 @@ __device__ __forceinline__ double4 ld_chunk(const MatTab<double> &M, int j) {
   return make_double4(a.x, a.y, b.x, b.y);
 }
 
-// Sequential carry chain of one (line, solve) over its m chunks: F[j] (chunk
-// summary) becomes the forward carry G_in[j], Y[j] the backward carry X[j+1];
-// G and X return the line's last forward value and first solution value.
-// The chain runs in batches of 8 chunks whose loads are all issued before
-// the batch's dependent FMAs (rows and chunk tables are padded to a multiple
-// of 8; padding entries may hold anything: the forward value is taken at
-// chunk m-1 and the backward carry is held at 0 past the end).
+// Sequential carry chain of one (line, solve) over m chunks (chunk-table
+// entries jb .. jb+m-1): F[j] (chunk summary) becomes the forward carry
+// G_in[j], Y[j] the backward carry X[j+1], starting from the forward carry G0
+// into the first chunk and the solution value X0 after the last (0 and 0 for
+// a whole line); G and X return the forward value after the last chunk and
+// the solution value at the first position.  The chain runs in batches of 8
+// chunks whose loads are all issued before the batch's dependent FMAs (rows
+// and chunk tables are padded to a multiple of 8; padding entries may hold
+// anything: the forward value is taken at chunk m-1 and the backward carry is
+// held at X0 past the end).
 template <typename R, typename V>
-__device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m, V &Gout, V &Xout) {
+__device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m, int jb, V G0, V X0, V &Gout,
+                                           V &Xout) {
   constexpr int SB = 8;
-  const V zero = Splat<V>::of(R(0));
   const int nb = (m + SB - 1) / SB;
-  V G = zero, Gl = zero;
+  V G = G0, Gl = G0;
   for (int b = 0; b < nb; ++b) {
     const int j0 = b * SB;
     V f[SB];
@@ -603,7 +606,7 @@ __device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m
 #pragma unroll
     for (int k = 0; k < SB; ++k) {
       f[k] = F[j0 + k];
-      a[k] = ld_chunk(M, j0 + k).x;
+      a[k] = ld_chunk(M, jb + j0 + k).x;
     }
 #pragma unroll
     for (int k = 0; k < SB; ++k) {
@@ -612,14 +615,14 @@ __device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m
       Gl = (j0 + k == m - 1) ? G : Gl;
     }
   }
-  V X = zero;
+  V X = X0;
   for (int b = nb - 1; b >= 0; --b) {
     const int j0 = b * SB;
     V gi[SB], yv[SB];
     R cy[SB], cz[SB];
 #pragma unroll
     for (int k = 0; k < SB; ++k) {
-      const typename V4T<R>::T c = ld_chunk(M, j0 + k);
+      const typename V4T<R>::T c = ld_chunk(M, jb + j0 + k);
       gi[k] = F[j0 + k];
       yv[k] = Y[j0 + k];
       cy[k] = c.y;
@@ -629,11 +632,29 @@ __device__ __forceinline__ void chain_line(const MatTab<R> &M, V *F, V *Y, int m
     for (int k = SB - 1; k >= 0; --k) {
       const V y = vfma(Splat<V>::of(cy[k]), gi[k], yv[k]);
       Y[j0 + k] = X;
-      X = (j0 + k < m) ? vfma(Splat<V>::of(cz[k]), X, y) : zero;
+      X = (j0 + k < m) ? vfma(Splat<V>::of(cz[k]), X, y) : X;
     }
   }
   Gout = Gl;
   Xout = X;
+}
+
+__device__ __forceinline__ float4 ld_segc(const MatTab<float> &M, int k) { return __ldg(M.segc + k); }
+__device__ __forceinline__ double4 ld_segc(const MatTab<double> &M, int k) {
+  const double2 *p = reinterpret_cast<const double2 *>(M.segc + k);
+  const double2 a = __ldg(p), b = __ldg(p + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// lane k of a lane value (one line or a pair)
+__device__ __forceinline__ float v_get(float a, int) { return a; }
+__device__ __forceinline__ double v_get(double a, int) { return a; }
+__device__ __forceinline__ float v_get(float2 a, int k) { return k ? a.y : a.x; }
+__device__ __forceinline__ void v_set(float &a, int, float x) { a = x; }
+__device__ __forceinline__ void v_set(double &a, int, double x) { a = x; }
+__device__ __forceinline__ void v_set(float2 &a, int k, float x) {
+  if (k) a.y = x;
+  else a.x = x;
 }
 
 // solve q of a sweep -> (species, matrix index)
@@ -724,13 +745,29 @@ __device__ __forceinline__ void scan_lines_warp(const SweepArgs<R> &A, V *sF, V 
   }
 }
 
+// Where a block's chunks sit in their lines, for the carry chains.
+struct SegCtx {
+  int phase;       // SEG_WHOLE: whole lines; SEG_SUMMARY: zero-carry chains, segment summaries
+                   // to global memory; SEG_SOLVE: chains start from the segment carries
+  int seg;         // segment of this block
+  int jb;          // first chunk of the segment (chunk-table offset)
+  int mv;          // chunks of the segment inside the line
+  long long gl0;   // global index of the block's line (unit) 0
+  int nvalid;      // lines (units) of the block inside the grid
+};
+
+__device__ __forceinline__ SegCtx whole_lines(int m) { return SegCtx{SEG_WHOLE, 0, 0, m, 0, 0}; }
+
 // Chain the chunk summaries of solves q0..q0+nq-1 for every line (or line
 // pair) of the block.  sF/sY hold F_j / Y_j on entry and the carries G_in[j]
-// / X[j+1] on return; sSig the FP64 Sherman-Morrison scalars.
+// / X[j+1] on return; sSig the Sherman-Morrison scalars.  Segmented sweeps:
+// see SegCtx (segment summaries and carries are stored per line, pairs as two
+// lines).
 template <typename R, typename V, int PK, int S, int KIND>
-__device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq) {
-  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
-  if (m > 32) {
+__device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq,
+                                           const SegCtx &sc) {
+  const int nlb = A.nlb, pitch = A.pitch;
+  if (sc.phase == SEG_WHOLE && A.mx > 32) {
     scan_lines_warp<R, V, PK>(A, sF, sY, sSig, q0, nq, [&](int q) -> const MatTab<R> & {
       int ms, mg;
       solve_matrix<R, S, KIND>(q, ms, mg);
@@ -738,6 +775,7 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, 
     });
     return;
   }
+  const V zero = Splat<V>::of(R(0));
   for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
     const int l = u % nlb;
     const int q = q0 + u / nlb;
@@ -747,9 +785,65 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, 
     V *F = sF + (q * nlb + l) * pitch;  // shared-memory offsets in 32-bit arithmetic
     V *Y = sY + (q * nlb + l) * pitch;
     V G, X;
-    chain_line<R, V>(M, F, Y, m, G, X);
-    // cyclic line: y_0 = X, y_{p-1} = G
-    put_sigma(sSig + (q * nlb + l) * PK, M, X, G);
+    if (sc.phase == SEG_WHOLE) {
+      chain_line<R, V>(M, F, Y, sc.mv, 0, zero, zero, G, X);
+      put_sigma(sSig + (q * nlb + l) * PK, M, X, G);  // cyclic line: y_0 = X, y_{p-1} = G
+      continue;
+    }
+    const bool ok = l < sc.nvalid;
+    const long long nl = A.nlines;
+    V G0 = zero, X0 = zero;
+    if (sc.phase == SEG_SOLVE && ok) {
+#pragma unroll
+      for (int k = 0; k < PK; ++k) {
+        const long long gi = ((q * nl + sc.gl0 + (long long)l * PK + k) * A.nseg + sc.seg) * 2;
+        v_set(G0, k, A.seg_car[gi]);
+        v_set(X0, k, A.seg_car[gi + 1]);
+        sSig[(q * nlb + l) * PK + k] = A.seg_sig[q * nl + sc.gl0 + (long long)l * PK + k];
+      }
+    }
+    chain_line<R, V>(M, F, Y, sc.mv, sc.jb, G0, X0, G, X);
+    if (sc.phase == SEG_SUMMARY && ok) {
+#pragma unroll
+      for (int k = 0; k < PK; ++k) {
+        const long long gi = ((q * nl + sc.gl0 + (long long)l * PK + k) * A.nseg + sc.seg) * 2;
+        A.seg_sum[gi] = v_get(G, k);
+        A.seg_sum[gi + 1] = v_get(X, k);
+      }
+    }
+  }
+}
+
+// Chains the segments of every line for solves q0 .. q0+nq-1: from the
+// zero-carry summaries (F_seg, Y_seg) and the segment coefficients, the
+// forward carry into each segment and the solution value after it, and the
+// line's Sherman-Morrison scalar (FP64) from its first and last values.
+template <typename R, int S, int KIND>
+__global__ void seg_carry_kernel(const __grid_constant__ SweepArgs<R> A, int q0, int nq) {
+  const long long nl = A.nlines;
+  const int ns = A.nseg;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nq * nl;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = q0 + (int)(idx / nl);
+    const long long gl = idx - (long long)(q - q0) * nl;
+    int ms, mg;
+    solve_matrix<R, S, KIND>(q, ms, mg);
+    const MatTab<R> &M = A.mat[ms][mg];
+    const long long base = (q * nl + gl) * ns * 2;
+    const R *sum = A.seg_sum + base;
+    R *car = A.seg_car + base;
+    R G = R(0);
+    for (int k = 0; k < ns; ++k) {
+      car[2 * k] = G;
+      G = fma(ld_segc(M, k).x, G, sum[2 * k]);
+    }
+    R X = R(0);
+    for (int k = ns - 1; k >= 0; --k) {
+      const typename V4T<R>::T c = ld_segc(M, k);
+      car[2 * k + 1] = X;
+      X = fma(c.z, X, fma(c.y, car[2 * k], sum[2 * k + 1]));
+    }
+    put_sigma(A.seg_sig + q * nl + gl, M, X, G);
   }
 }
 
@@ -759,10 +853,12 @@ __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, 
 template <typename R, int PK = 1>
 struct ChunkPos {
   using V = typename LaneT<R, PK>::T;
-  int l, j;      // line (pair) within the block/tile, chunk index
+  int l, j;      // line (pair) within the block/tile, chunk index within the block
+  int jt;        // chunk index within the line (line tables; = j unless segmented)
   int i0, cnt;   // first position of the chunk, positions inside the line
   bool thr_ok;   // the thread owns a chunk (false for padding threads)
   V qbase;       // manufactured-source factor of the line(s) (0: none)
+  SegCtx sc;     // where the block's chunks sit in their lines
 };
 
 // per-lane manufactured source p0 ((p1 lf - 1) q + q/(1+q)) at q = qbase phi_axis[i]
@@ -829,7 +925,7 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
   using V = typename LaneT<R, PK>::T;
   constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
-  const int l = c.l, j = c.j, cnt = c.cnt, i0 = c.i0;
+  const int l = c.l, j = c.j, jt = c.jt, cnt = c.cnt, i0 = c.i0;
   const bool thr_ok = c.thr_ok;
   const V zero = Splat<V>::of(R(0));
   auto react = [&](const V (&u)[S], V (&f)[S], V src) {
@@ -849,12 +945,12 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     }
   };
   auto p1 = [&](const MatTab<R> &M, const V (&b)[L], V &F, V &Y) {
-    if constexpr (sizeof(R) == 8) pass1<R, L>(M, m, j, b, F, Y);
-    else pass1v<V, L>(M, m, j, b, F, Y);
+    if constexpr (sizeof(R) == 8) pass1<R, L>(M, m, jt, b, F, Y);
+    else pass1v<V, L>(M, m, jt, b, F, Y);
   };
   auto p1x2 = [&](const MatTab<R> &M, const V (&b0)[L], const V (&b1)[L], V &F0, V &Y0, V &F1, V &Y1) {
-    if constexpr (sizeof(R) == 8) pass1x2<R, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
-    else pass1x2v<V, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+    if constexpr (sizeof(R) == 8) pass1x2<R, L>(M, m, jt, b0, b1, F0, Y0, F1, Y1);
+    else pass1x2v<V, L>(M, m, jt, b0, b1, F0, Y0, F1, Y1);
   };
   V *sF = reinterpret_cast<V *>(exch);
   V *sY = sF + NQ * nlb * pitch;
@@ -880,6 +976,11 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     return cq;
   };
   const V k9 = Splat<V>::of(R(9)), km8 = Splat<V>::of(R(-8));
+  auto scx = [&](int ph) {
+    SegCtx x = c.sc;
+    x.phase = ph;
+    return x;
+  };
   // solve q -> (species, matrix): FIRST/MIDDLE: q = 5s + {0: T.cU, 1: S.cU, 2: T.cf, 3: S.cf, 4: P.w}
   //                               LAST: q = s (P.w), S + 2s (T.f1), S + 2s + 1 (S.f2)
   if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
@@ -933,7 +1034,9 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(5 * s + 4, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
+                                                          : A.segphase == SEG_SUMMARY ? SEG_SUMMARY : SEG_SOLVE));
+    if (A.segphase == SEG_SUMMARY) return;  // segment summaries written
     __syncthreads();
     // pass 2: c_U <- 9 T c_U - 8 S c_U, c_f likewise, w <- P w
 #pragma unroll
@@ -941,38 +1044,38 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       if constexpr (sizeof(R) == 4) {
         // T on (c_U, c_f) into (xa, xc); S on (c_U, c_f) in place, folded into 9 T - 8 S
         V xa[L], xc[L];
-        pass2x2v<V, L, true>(A.mat[s][1], A.mat[s][1], m, j, cu[s], cf[s], carry(5 * s + 0), carry(5 * s + 2), xa,
+        pass2x2v<V, L, true>(A.mat[s][1], A.mat[s][1], m, jt, cu[s], cf[s], carry(5 * s + 0), carry(5 * s + 2), xa,
                              xc, [&](int t, int k, V x) {
                                if (k == 0) xa[t] = x;
                                else xc[t] = x;
                              });
-        pass2x2v<V, L, true>(A.mat[s][2], A.mat[s][2], m, j, cu[s], cf[s], carry(5 * s + 1), carry(5 * s + 3),
+        pass2x2v<V, L, true>(A.mat[s][2], A.mat[s][2], m, jt, cu[s], cf[s], carry(5 * s + 1), carry(5 * s + 3),
                              cu[s], cf[s], [&](int t, int k, V x) {
                                if (k == 0) xa[t] = vfma(k9, xa[t], vmul(km8, x));
                                else xc[t] = vfma(k9, xc[t], vmul(km8, x));
                              });
         store(0, s, xa);
         store(1, s, xc);
-        pass2v<V, L>(A.mat[s][0], m, j, w[s], carry(5 * s + 4), w[s], [&](int t, V x) { w[s][t] = x; });
+        pass2v<V, L>(A.mat[s][0], m, jt, w[s], carry(5 * s + 4), w[s], [&](int t, V x) { w[s][t] = x; });
         store(2, s, w[s]);
       } else {
         V xa[L], xb[L], G, X, sg;
         carries(5 * s + 0, G, X, sg);
-        pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
+        pass2<R, L>(A.mat[s][1], m, jt, cu[s], G, X, sg, xa);
         carries(5 * s + 1, G, X, sg);
-        pass2<R, L>(A.mat[s][2], m, j, cu[s], G, X, sg, xb);
+        pass2<R, L>(A.mat[s][2], m, jt, cu[s], G, X, sg, xb);
 #pragma unroll
         for (int t = 0; t < L; ++t) xa[t] = vfma(k9, xa[t], vmul(km8, xb[t]));
         store(0, s, xa);
         carries(5 * s + 2, G, X, sg);
-        pass2<R, L>(A.mat[s][1], m, j, cf[s], G, X, sg, xa);
+        pass2<R, L>(A.mat[s][1], m, jt, cf[s], G, X, sg, xa);
         carries(5 * s + 3, G, X, sg);
-        pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
+        pass2<R, L>(A.mat[s][2], m, jt, cf[s], G, X, sg, xb);
 #pragma unroll
         for (int t = 0; t < L; ++t) xa[t] = vfma(k9, xa[t], vmul(km8, xb[t]));
         store(1, s, xa);
         carries(5 * s + 4, G, X, sg);
-        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, xa);
+        pass2<R, L>(A.mat[s][0], m, jt, w[s], G, X, sg, xa);
         store(2, s, xa);
       }
     }
@@ -981,8 +1084,10 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     V cu[S][L], cf[S][L], w[S][L];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      load(0, s, cu[s]);
-      load(1, s, cf[s]);
+      if (A.segphase != SEG_SUMMARY) {  // the P summaries need w only
+        load(0, s, cu[s]);
+        load(1, s, cf[s]);
+      }
       load(2, s, w[s]);
     }
 #pragma unroll
@@ -992,16 +1097,18 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(s, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, S);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, S, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
+                                                         : A.segphase == SEG_SUMMARY ? SEG_SUMMARY : SEG_SOLVE));
+    if (A.segphase == SEG_SUMMARY) return;  // P summaries written
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if constexpr (sizeof(R) == 4) {
-        pass2v<V, L>(A.mat[s][0], m, j, w[s], carry(s), w[s], [&](int t, V x) { w[s][t] = x; });  // w <- U*
+        pass2v<V, L>(A.mat[s][0], m, jt, w[s], carry(s), w[s], [&](int t, V x) { w[s][t] = x; });  // w <- U*
       } else {
         V x[L], G, X, sg;
         carries(s, G, X, sg);
-        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, x);
+        pass2<R, L>(A.mat[s][0], m, jt, w[s], G, X, sg, x);
 #pragma unroll
         for (int t = 0; t < L; ++t) w[s][t] = x[t];  // w now holds U*
       }
@@ -1035,13 +1142,15 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(S + 2 * s + 1, F1, Y1);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S);
+    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
+                                                             : A.segphase == SEG_SOLVE ? SEG_SUMMARY : SEG_SOLVE));
+    if (A.segphase == SEG_SOLVE) return;  // T and S summaries written
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if constexpr (sizeof(R) == 4) {
         // T f1 and S f2 interleaved in place; c_U <- T f1 - S f2
-        pass2x2v<V, L, false>(A.mat[s][1], A.mat[s][2], m, j, cu[s], cf[s], carry(S + 2 * s), carry(S + 2 * s + 1),
+        pass2x2v<V, L, false>(A.mat[s][1], A.mat[s][2], m, jt, cu[s], cf[s], carry(S + 2 * s), carry(S + 2 * s + 1),
                               cu[s], cf[s], [&](int t, int k, V x) {
                                 if (k == 0) cu[s][t] = x;
                                 else cu[s][t] = vsub(cu[s][t], x);
@@ -1050,9 +1159,9 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       } else {
         V xa[L], xb[L], G, X, sg;
         carries(S + 2 * s, G, X, sg);
-        pass2<R, L>(A.mat[s][1], m, j, cu[s], G, X, sg, xa);
+        pass2<R, L>(A.mat[s][1], m, jt, cu[s], G, X, sg, xa);
         carries(S + 2 * s + 1, G, X, sg);
-        pass2<R, L>(A.mat[s][2], m, j, cf[s], G, X, sg, xb);
+        pass2<R, L>(A.mat[s][2], m, jt, cf[s], G, X, sg, xb);
 #pragma unroll
         for (int t = 0; t < L; ++t) xa[t] = vsub(xa[t], xb[t]);
         store(0, s, xa);
@@ -1086,35 +1195,50 @@ __device__ __forceinline__ void store_pairs(const float2 (&v)[L], float2 *__rest
 }
 
 // Register kernel: one block per group of nlb lines (nlb line pairs for
-// PK = 2), inputs loaded straight from global memory (vector loads on x,
-// coalesced row segments on strided axes).
+// PK = 2) and, for segmented sweeps, per segment of mx chunks of those lines;
+// inputs loaded straight from global memory (vector loads on x, coalesced row
+// segments on strided axes).
 template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1>
 __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
                                             R exp_mt) {
   (void)t_eval;
-  const int m = A.m, nlb = A.nlb;
+  const int m = A.m, mx = A.mx, nlb = A.nlb, nseg = A.nseg;
+  const int seg = bid % nseg;
+  const int lb = bid / nseg;  // line block
   const int tid = threadIdx.x;
-  // threads past nlb*m (batched launches size blocks for the largest
+  // threads past nlb*mx (batched launches size blocks for the largest
   // instance) own no chunk but still take part in every barrier and scan
-  const bool thr_ok = tid < nlb * m;
+  const bool thr_ok = tid < nlb * mx;
   int l = tid % nlb, j = tid / nlb;
   if (!thr_ok) { l = 0; j = 0; }
+  const int jg = seg * mx + j;  // chunk within the line
+  const bool chunk_in = jg < m;
+  SegCtx sc;
+  sc.phase = SEG_WHOLE;
+  sc.seg = seg;
+  sc.jb = seg * mx;
+  sc.mv = min(mx, m - seg * mx);
   const long long N = A.N;
   if constexpr (PK == 2) {
     // strided axis, even stride: pair l covers lines lo, lo + 1 of one row
     static_assert(!CONTIG && sizeof(R) == 4, "line pairs: FP32 strided sweeps");
-    const long long lo = (long long)(bid % A.nlo_blocks) * nlb * 2 + 2 * l;
-    const long long hi = bid / A.nlo_blocks;
+    const long long lo0 = (long long)(lb % A.nlo_blocks) * nlb * 2;
+    const long long lo = lo0 + 2 * l;
+    const long long hi = lb / A.nlo_blocks;
     const bool line_ok = thr_ok && lo < A.st;
+    sc.gl0 = hi * A.st + lo0;
+    sc.nvalid = (int)min((long long)nlb, (A.st - lo0) / 2);
     ChunkPos<R, 2> c;
     c.qbase = line_ok ? make_float2(line_source_base(A, false, 0, lo, hi, exp_mt),
                                     line_source_base(A, false, 0, lo + 1, hi, exp_mt))
                       : make_float2(0.f, 0.f);
     c.l = l;
     c.j = j;
-    c.i0 = j * L;
-    c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
+    c.jt = chunk_in ? jg : m - 1;
+    c.i0 = jg * L;
+    c.cnt = (line_ok && chunk_in) ? max(0, min(L, A.n - c.i0)) : 0;
     c.thr_ok = thr_ok;
+    c.sc = sc;
     const long long off0 = (lo + hi * A.st * A.n + (long long)c.i0 * A.st) >> 1;  // in pairs
     const int st2 = (int)(A.st >> 1);
     const int cnt = c.cnt;
@@ -1130,23 +1254,31 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     bool line_ok;
     ChunkPos<R> c;
     if constexpr (CONTIG) {
-      const long long line = (long long)bid * nlb + l;
+      const long long line0 = (long long)lb * nlb;
+      const long long line = line0 + l;
       line_ok = thr_ok && line < A.nlines;
       base = line * A.n;
       c.qbase = line_ok ? line_source_base(A, true, line, 0, 0, exp_mt) : R(0);
+      sc.gl0 = line0;
+      sc.nvalid = (int)min((long long)nlb, A.nlines - line0);
     } else {
-      const long long lo = (long long)(bid % A.nlo_blocks) * nlb + l;
-      const long long hi = bid / A.nlo_blocks;
+      const long long lo0 = (long long)(lb % A.nlo_blocks) * nlb;
+      const long long lo = lo0 + l;
+      const long long hi = lb / A.nlo_blocks;
       line_ok = thr_ok && lo < A.st;
       base = lo + hi * A.st * A.n;
       c.qbase = line_ok ? line_source_base(A, false, 0, lo, hi, exp_mt) : R(0);
+      sc.gl0 = hi * A.st + lo0;
+      sc.nvalid = (int)min((long long)nlb, A.st - lo0);
     }
     const long long st = CONTIG ? 1 : A.st;
     c.l = l;
     c.j = j;
-    c.i0 = j * L;
-    c.cnt = line_ok ? max(0, min(L, A.n - c.i0)) : 0;
+    c.jt = chunk_in ? jg : m - 1;
+    c.i0 = jg * L;
+    c.cnt = (line_ok && chunk_in) ? max(0, min(L, A.n - c.i0)) : 0;
     c.thr_ok = thr_ok;
+    c.sc = sc;
     const long long off0 = base + (long long)c.i0 * st;
     const int cnt = c.cnt;
     auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG>(v, A.in[f] + s * N, off0, st, cnt); };

@@ -18,4 +18,8 @@ cudaError_t launch_sweep_batched(const SweepArgs<float> *args, const int *bs, in
 #undef CALL
 }
 
+cudaError_t launch_seg_carry(const SweepArgs<float> &a, int nspecies, int kind, int q0, int nq, cudaStream_t s) {
+  return launch_seg_carry_t<float>(a, nspecies, kind, q0, nq, s);
+}
+
 }  // namespace etd

@@ -17,4 +17,8 @@ cudaError_t launch_sweep_batched(const SweepArgs<double> *args, const int *bs, i
 #undef CALL
 }
 
+cudaError_t launch_seg_carry(const SweepArgs<double> &a, int nspecies, int kind, int q0, int nq, cudaStream_t s) {
+  return launch_seg_carry_t<double>(a, nspecies, kind, q0, nq, s);
+}
+
 }  // namespace etd

@@ -99,6 +99,28 @@ cudaError_t launch_one_batched(const SweepArgs<R> *args, const int *bs, int nins
   return cudaGetLastError();
 }
 
+template <typename R, int S, int KIND>
+cudaError_t launch_seg_carry_one(const SweepArgs<R> &a, int q0, int nq, cudaStream_t s) {
+  const long long work = (long long)nq * a.nlines;
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>((work + threads - 1) / threads, 152LL * 16);
+  seg_carry_kernel<R, S, KIND><<<std::max(blocks, 1), threads, 0, s>>>(a, q0, nq);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_seg_carry_t(const SweepArgs<R> &a, int nspecies, int kind, int q0, int nq, cudaStream_t s) {
+  switch (nspecies * 10 + kind) {
+    case 10: return launch_seg_carry_one<R, 1, SWEEP_FIRST>(a, q0, nq, s);
+    case 11: return launch_seg_carry_one<R, 1, SWEEP_MIDDLE>(a, q0, nq, s);
+    case 12: return launch_seg_carry_one<R, 1, SWEEP_LAST>(a, q0, nq, s);
+    case 20: return launch_seg_carry_one<R, 2, SWEEP_FIRST>(a, q0, nq, s);
+    case 21: return launch_seg_carry_one<R, 2, SWEEP_MIDDLE>(a, q0, nq, s);
+    case 22: return launch_seg_carry_one<R, 2, SWEEP_LAST>(a, q0, nq, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 #define ETD_DISPATCH(CALL)                                                        \
   switch (nspecies * 1000 + L * 10 + kind) {                                      \
     case 1040: return CALL(1, 4, SWEEP_FIRST);                                    \

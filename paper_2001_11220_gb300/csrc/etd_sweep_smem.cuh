@@ -171,6 +171,8 @@ __device__ __forceinline__ void compute_tile(const SweepArgs<R> &A, const TileCo
   p.i0 = j * L;
   p.cnt = lvalid ? max(0, min(L, n - j * L)) : 0;
   p.thr_ok = thr_ok;
+  p.jt = j;
+  p.sc = whole_lines(A.m);
   p.qbase = source_base<R, CONTIG>(A, c, l);
   const int off0 = CONTIG ? l * cp + j * L : (j * L) * nlb + l;
   const int pstep = CONTIG ? 1 : nlb;

@@ -19,6 +19,8 @@ struct HostTab {
   // interior-chunk arrays (chunk-major, one value per position): pivot
   // reciprocal e, summary weights v and w, Sherman-Morrison vector z
   std::vector<double> e1, v1, w1, z1;
+  // segmented sweeps: per segment of mx chunks (A_seg, K_seg, B_seg, 0)
+  std::vector<double> segc;
   double r = 0.0;  // interior off-diagonal magnitude: l_i = u_i = -r
   double sm_c = 0.0, sm_inv = 0.0;
 };
@@ -28,7 +30,10 @@ struct HostTab {
 // transpose: the matrix of the adjoint solve.  Periodic lines are split as
 // M = M' + u v^T with u = (g, 0, .., 0, bl), v = (1, 0, .., 0, tr/g), g = -d_0
 // (Sherman-Morrison); M' is tridiagonal and is what the tables factorise.
-inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T) {
+// mx, nseg > 1: the line is split into nseg segments of mx chunks (segmented
+// sweeps); the chunk table is then padded to nseg * mx entries and segc holds
+// the segment coefficients.
+inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T, int mx = 0, int nseg = 1) {
   std::vector<double> lo(p), di(p), up(p);
   for (int i = 0; i < p; ++i) {
     di[i] = 1.0 + 2.0 * r;
@@ -93,7 +98,8 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
   T.m = m;
   T.pos.assign((size_t)4 * L * m, 0.0);
   T.sum.assign((size_t)2 * L * m, 0.0);
-  T.chunk.assign((size_t)4 * ((m + 7) & ~7), 0.0);  // zero entries pad to a multiple of 8 chunks
+  // zero entries pad to a multiple of 8 chunks (and to whole segments)
+  T.chunk.assign((size_t)4 * std::max((m + 7) & ~7, nseg > 1 ? nseg * mx : 0), 0.0);
   T.e1.assign((size_t)L * m, 1.0);
   T.v1.assign((size_t)L * m, 0.0);
   T.w1.assign((size_t)L * m, 0.0);
@@ -144,6 +150,28 @@ inline void build_tab(int p, int bc, double r, bool transpose, int L, HostTab &T
     T.chunk[4 * j + 1] = kap;
     T.chunk[4 * j + 2] = bst;
     T.chunk[4 * j + 3] = 0.0;
+  }
+  // Segment of chunks j0 .. j1-1 with forward carry G in and solution value
+  // X_end after it: G_in[j] = P_j G + p_j (P_j = prod_{j0<=i<j} A_i), so
+  //   G_out   = A_seg G + F_seg,                A_seg = prod A_j,
+  //   X_start = Y_seg + K_seg G + B_seg X_end,  B_seg = prod B_j,
+  //   K_seg   = sum_j (prod_{j0<=i<j} B_i) kappa_j P_j,
+  // where F_seg, Y_seg are the zero-carry values of the block's chain.
+  T.segc.clear();
+  if (nseg > 1) {
+    T.segc.assign((size_t)4 * nseg, 0.0);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int j0 = sg * mx, j1 = std::min(m, j0 + mx);
+      double Pp = 1.0, Bp = 1.0, K = 0.0;
+      for (int j = j0; j < j1; ++j) {
+        K += Bp * T.chunk[4 * j + 1] * Pp;
+        Bp *= T.chunk[4 * j + 2];
+        Pp *= T.chunk[4 * j + 0];
+      }
+      T.segc[4 * sg + 0] = Pp;
+      T.segc[4 * sg + 1] = K;
+      T.segc[4 * sg + 2] = Bp;
+    }
   }
 }
 

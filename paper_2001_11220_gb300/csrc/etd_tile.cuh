@@ -311,7 +311,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
       }
     }
     __syncthreads();
-    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ);
+    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ, whole_lines(m));
     __syncthreads();
     if (thr_ok) {
 #pragma unroll
@@ -360,7 +360,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
       put(s, F0, Y0);
     }
     __syncthreads();
-    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, 0, S);
+    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, 0, S, whole_lines(m));
     __syncthreads();
     // U*, F(U*, t_{n+1}); f1 = 9 c_U + 2k c_f + k F*, f2 = 8 c_U + 3k/2 c_f + k/2 F* into the c_U, c_f tiles
     if (thr_ok) {
@@ -408,7 +408,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<float> &A, unsigned c
       }
     }
     __syncthreads();
-    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S);
+    scan_lines<float, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S, whole_lines(m));
     __syncthreads();
     if (thr_ok) {
 #pragma unroll

@@ -353,3 +353,50 @@ def test_tile_kernels_reject_misaligned_state(monkeypatch):
         with pytest.raises(B.EtdError, match="16-byte aligned"):
             B.check(call(buf.data_ptr() + 4), ctx.ctx)
     ctx.close()
+
+
+# Segmented sweeps (long lines split over several blocks: segment summaries,
+# a carry pass over the segments of every line, then the carried solves),
+# forced through ETD_TILES ("L:lines:3:chunks per segment") on the long axes
+SEG_CASES = [
+    (case("seg_per_y", (6, 1100), (W.NEUMANN, W.PERIODIC), (0.5, 2.0), "schnakenberg", (0.1, 0.9, 10.0), k=0.01,
+          ic="uniform", ic_args=((1.0, 0.9), 1e-2)), ["{L}:0:0:1", "{L}:8:3:16"]),
+    (case("seg_per_x", (1301, 7), (W.PERIODIC, W.DIRICHLET), (0.5, 2.0), "gray_scott", (0.04, 0.06), k=0.01),
+     ["{L}:8:3:16", "{L}:0:0:1"]),
+    (case("seg_neu_dir_ragged", (517, 301), (W.NEUMANN, W.DIRICHLET), (0.5, 0.1), "brusselator", (1.0, 3.4)),
+     ["{L}:8:3:8", "{L}:16:3:8"]),
+    (case("seg_3d_middle", (8, 300, 6), (W.NEUMANN, W.PERIODIC, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+          (0.04, 0.06), k=0.5), ["{L}:0:0:1", "{L}:8:3:16", "{L}:0:0:1"]),
+    (case("seg_3d_last_src", (12, 10, 270), W.DIRICHLET, (1.0,), "enzyme", (1.0, 1.0), k=1 / 17, ic="sine"),
+     ["{L}:0:0:1", "{L}:0:0:1", "{L}:4:3:16"]),
+]
+
+
+def seg_tiles(spec, L):
+    return ",".join(x.format(L=L) for x in spec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("w,spec", SEG_CASES, ids=[c[0].name for c in SEG_CASES])
+def test_segmented_sweeps_vs_oracle(w, spec, prec, monkeypatch):
+    monkeypatch.setenv("ETD_TILES", seg_tiles(spec, 4 if prec == "fp64" else 8))
+    ctx = _api().from_workload(w, prec)
+    inf = ctx.info()
+    seg_axes = [a for a, x in enumerate(spec) if ":3:" in x]
+    assert all(inf["staged"][a] == 3 for a in seg_axes), inf
+    U0 = W.initial_state(w)
+    U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+    ctx.run(U, 0.3, 1)
+    torch.cuda.synchronize()
+    one = U.double().cpu().numpy()
+    ctx.run(U, 0.3 + w.k, 2)
+    torch.cuda.synchronize()
+    three = U.double().cpu().numpy()
+    ctx.close()
+    e1 = rel_err(one, oracle_run(w, U0, 1, t0=0.3))
+    e3 = rel_err(three, oracle_run(w, U0, 3, t0=0.3))
+    print(f"{w.name} {prec} segmented: 1 step {e1:.3e}, 3 steps {e3:.3e}")
+    if prec == "fp64":
+        assert e1 <= FP64_TOL and e3 <= FP64_TOL, (e1, e3)
+    else:
+        assert e1 <= FP32_STEP_TOL and e3 <= 3 * FP32_STEP_TOL, (e1, e3)
