@@ -33,7 +33,7 @@ int pow2_floor_i(long long v) {
   return p;
 }
 
-bool plan_adjoint_axis(Instance &I, int a, int L) {
+bool plan_adjoint_axis(Instance &I, int a, int L, int nlb_force = 0) {
   AxisPlan &P = I.aplan[a];
   const long long n = I.n[a];
   P.L = L;
@@ -47,6 +47,7 @@ bool plan_adjoint_axis(Instance &I, int a, int L) {
   P.pitch = exchange_pitch(P.m);
   const long long avail = (a == 0) ? P.nlines : st;
   int nlb = pow2_floor_i(std::min<long long>(32, ETD_MAX_BLOCK_THREADS / P.m));
+  if (nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
   while (nlb > 1 && nlb / 2 >= avail) nlb /= 2;
   while (nlb > 1 && adjoint_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes) > 200 * 1024) nlb /= 2;
   P.nlb = nlb;
@@ -85,10 +86,27 @@ void upload(DeviceArena &arena, const HostTab &T, MatTab<R> &M, cudaError_t &err
 etd_status prepare_adjoint(etd_ctx *ctx, Instance &I) {
   if (!I.adj_ready) {
     static const double gammas[3] = {1.0, 3.0, 4.0};
+    // ETD_ADJ_TILES="L:nlb,..." (one entry per axis) forces the adjoint chunk
+    // length and lines per block, e.g. to compare shapes in a profiler run
+    const char *forced = std::getenv("ETD_ADJ_TILES");
     for (int a = 0; a < I.dim; ++a) {
-      int L = (I.real_bytes == 4 && I.S == 1) ? 8 : 4;
-      while (!plan_adjoint_axis(I, a, L) && L < 8) L *= 2;
-      if (!plan_adjoint_axis(I, a, L))
+      // FP32: 8 positions per thread (32 chunks on 256-node lines: the serial carry chain, measured
+      // faster than 4 with the warp scan); FP64: 4 (register pressure)
+      int L = (I.real_bytes == 4) ? 8 : 4;
+      int fl = 0, fn = 0;
+      if (forced) {
+        const char *p = forced;
+        for (int b = 0; b < a && p; ++b) {
+          p = strchr(p, ',');
+          if (p) ++p;
+        }
+        if (p && sscanf(p, "%d:%d", &fl, &fn) >= 1 && (fl == 4 || fl == 8) && plan_adjoint_axis(I, a, fl, fn)) L = fl;
+      }
+      if (L != fl) {
+        fn = 0;
+        while (!plan_adjoint_axis(I, a, L) && L < 8) L *= 2;
+      }
+      if (!plan_adjoint_axis(I, a, L, fn))
         return fail(ctx, ETD_ERR_UNSUPPORTED, "adjoint: axis %d with n = %lld does not fit one block", a,
                     (long long)I.n[a]);
       const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
