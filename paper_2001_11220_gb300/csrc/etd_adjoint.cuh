@@ -99,23 +99,50 @@ __device__ __forceinline__ R mms_q(const SweepArgs<R> &A, long long pidx) {
 }
 
 // chain the chunk summaries of solves q0 .. q0+nq-1; mat(q) gives the solve's tables
+// Line-solve passes of the adjoint sweeps: FP64 keeps the operation order of
+// Section 7 (pass1 / pass2), FP32 uses the coefficient rows and the one-FMA
+// forward chain of the forward sweeps (pass1v / pass2v).
+template <typename R, int L>
+__device__ __forceinline__ void apass1(const MatTab<R> &M, int m, int j, const R (&b)[L], R &F, R &Y) {
+  if constexpr (sizeof(R) == 8) pass1<R, L>(M, m, j, b, F, Y);
+  else pass1v<R, L>(M, m, j, b, F, Y);
+}
+template <typename R, int L>
+__device__ __forceinline__ void apass1x2(const MatTab<R> &M, int m, int j, const R (&b0)[L], const R (&b1)[L], R &F0,
+                                         R &Y0, R &F1, R &Y1) {
+  if constexpr (sizeof(R) == 8) pass1x2<R, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+  else pass1x2v<R, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+}
+template <typename R, int L>
+__device__ __forceinline__ void apass2(const MatTab<R> &M, int m, int j, const R (&b)[L], R G, R X, R sg, R (&x)[L]) {
+  if constexpr (sizeof(R) == 8) {
+    pass2<R, L>(M, m, j, b, G, X, sg, x);
+  } else {
+    Carry<R> c;
+    c.G = G;
+    c.X = X;
+    c.ns = -sg;
+    pass2v<R, L>(M, m, j, b, c, x, [&](int t, R v) { x[t] = v; });
+  }
+}
+// (the Sherman-Morrison scalars are formed in FP64 and stored in the sweep's precision)
 template <typename R, typename GetMat>
-__device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY, double *sSig, int q0, int nq,
+__device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY, R *sSig, int q0, int nq,
                                             GetMat mat) {
   const int m = A.m, nlb = A.nlb, pitch = A.pitch;
   if (m > 32) {
-    scan_lines_warp<R, R, 1, double>(A, sF, sY, sSig, q0, nq, mat);
+    scan_lines_warp<R, R, 1, R>(A, sF, sY, sSig, q0, nq, mat);
     return;
   }
   for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
     const int l = u % nlb;
     const int q = q0 + u / nlb;
     const MatTab<R> &M = mat(q);
-    R *F = sF + (size_t)q * nlb * pitch + (size_t)l * pitch;
-    R *Y = sY + (size_t)q * nlb * pitch + (size_t)l * pitch;
+    R *F = sF + (q * nlb + l) * pitch;  // 32-bit shared-memory offsets
+    R *Y = sY + (q * nlb + l) * pitch;
     R G, X;
     chain_line<R, R>(M, F, Y, m, 0, R(0), R(0), G, X);
-    sSig[(size_t)q * nlb + l] = (M.sm_inv != 0.0) ? ((double)X + M.sm_c * (double)G) * M.sm_inv : 0.0;
+    put_sigma(sSig + q * nlb + l, M, X, G);
   }
 }
 
@@ -164,18 +191,20 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
   const R k = (R)A.k;
 
   R *sF = reinterpret_cast<R *>(smem);
-  R *sY = sF + (size_t)NQ * nlb * pitch;
-  double *sSig = reinterpret_cast<double *>(smem + ((2 * (size_t)NQ * nlb * pitch * sizeof(R) + 15) & ~(size_t)15));
-  double *red = sSig + (size_t)NQ * nlb;
-  const size_t myidx = (size_t)l * pitch + j;
+  R *sY = sF + NQ * nlb * pitch;
+  unsigned char *sig_base = smem + ((2 * NQ * nlb * pitch * (int)sizeof(R) + 15) & ~15);
+  R *sSig = reinterpret_cast<R *>(sig_base);  // NQ * nlb scalars (8-byte slots reserved)
+  double *red = reinterpret_cast<double *>(sig_base) + NQ * nlb;
+  const int myidx = l * pitch + j;  // 32-bit shared-memory offsets
+  const int qstride = nlb * pitch;
   auto put = [&](int q, R F, R Y) {
-    sF[(size_t)q * nlb * pitch + myidx] = F;
-    sY[(size_t)q * nlb * pitch + myidx] = Y;
+    sF[q * qstride + myidx] = F;
+    sY[q * qstride + myidx] = Y;
   };
   auto carries = [&](int q, R &G, R &X, R &sg) {
-    G = sF[(size_t)q * nlb * pitch + myidx];
-    X = sY[(size_t)q * nlb * pitch + myidx];
-    sg = (R)sSig[(size_t)q * nlb + l];
+    G = sF[q * qstride + myidx];
+    X = sY[q * qstride + myidx];
+    sg = sSig[q * nlb + l];
   };
   auto qsrc = [&](int t) -> R {
     return (A.phi[0] != nullptr && t < cnt) ? mms_q(A, off0 + (long long)t * st) : R(0);
@@ -215,11 +244,11 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         R F0, Y0, F1, Y1;
-        pass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
+        apass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
         put(3 * s, F0, Y0);
-        pass1<R, L>(A.matT[s][1], m, j, ub[s], F1, Y1);
+        apass1<R, L>(A.matT[s][1], m, j, ub[s], F1, Y1);
         put(3 * s + 1, F1, Y1);
-        pass1<R, L>(A.matT[s][2], m, j, ub[s], F1, Y1);
+        apass1<R, L>(A.matT[s][2], m, j, ub[s], F1, Y1);
         put(3 * s + 2, F1, Y1);
       }
       __syncthreads();
@@ -229,11 +258,11 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       for (int s = 0; s < S; ++s) {
         R G, X, sg;
         carries(3 * s, G, X, sg);
-        pass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, Us[s]);
+        apass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, Us[s]);
         carries(3 * s + 1, G, X, sg);
-        pass2<R, L>(A.matT[s][1], m, j, ub[s], G, X, sg, a1[s]);
+        apass2<R, L>(A.matT[s][1], m, j, ub[s], G, X, sg, a1[s]);
         carries(3 * s + 2, G, X, sg);
-        pass2<R, L>(A.matT[s][2], m, j, ub[s], G, X, sg, a2[s]);
+        apass2<R, L>(A.matT[s][2], m, j, ub[s], G, X, sg, a2[s]);
 #pragma unroll
         for (int t = 0; t < L; ++t) a2[s][t] = -a2[s][t];  // f2bar = S^T (-Ubar)
       }
@@ -279,11 +308,11 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       R F0, Y0;
-      pass1<R, L>(A.mat[s][1], m, j, f1[s], F0, Y0);
+      apass1<R, L>(A.mat[s][1], m, j, f1[s], F0, Y0);
       put(3 * S + 3 * s, F0, Y0);
-      pass1<R, L>(A.mat[s][2], m, j, f2[s], F0, Y0);
+      apass1<R, L>(A.mat[s][2], m, j, f2[s], F0, Y0);
       put(3 * S + 3 * s + 1, F0, Y0);
-      pass1<R, L>(A.matT[s][0], m, j, usb[s], F0, Y0);
+      apass1<R, L>(A.matT[s][0], m, j, usb[s], F0, Y0);
       put(3 * S + 3 * s + 2, F0, Y0);
     }
     __syncthreads();
@@ -293,13 +322,13 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
     for (int s = 0; s < S; ++s) {
       R x[L], G, X, sg;
       carries(3 * S + 3 * s, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, f1[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][1], m, j, f1[s], G, X, sg, x);
       dterm(s, a1[s], f1[s], x, R(1));
       carries(3 * S + 3 * s + 1, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, f2[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][2], m, j, f2[s], G, X, sg, x);
       dterm(s, a2[s], f2[s], x, R(1));
       carries(3 * S + 3 * s + 2, G, X, sg);
-      pass2<R, L>(A.matT[s][0], m, j, usb[s], G, X, sg, x);  // wbar
+      apass2<R, L>(A.matT[s][0], m, j, usb[s], G, X, sg, x);  // wbar
       dterm(s, x, w[s], Us[s], R(1));
       store_chunk<R, L, CONTIG>(x, A.out[2] + s * N, off0, st, cnt);
     }
@@ -351,22 +380,22 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       R F0, Y0, F1, Y1, xw[L];
-      pass1x2<R, L>(A.matT[s][1], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
+      apass1x2<R, L>(A.matT[s][1], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
       put(10 * s + 0, F0, Y0);
       put(10 * s + 2, F1, Y1);
-      pass1x2<R, L>(A.matT[s][2], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
+      apass1x2<R, L>(A.matT[s][2], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
       put(10 * s + 1, F0, Y0);
       put(10 * s + 3, F1, Y1);
-      pass1<R, L>(A.matT[s][0], m, j, wb[s], F0, Y0);
+      apass1<R, L>(A.matT[s][0], m, j, wb[s], F0, Y0);
       put(10 * s + 4, F0, Y0);
-      pass1x2<R, L>(A.mat[s][1], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
+      apass1x2<R, L>(A.mat[s][1], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
       put(10 * s + 5, F0, Y0);
       put(10 * s + 7, F1, Y1);
-      pass1x2<R, L>(A.mat[s][2], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
+      apass1x2<R, L>(A.mat[s][2], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
       put(10 * s + 6, F0, Y0);
       put(10 * s + 8, F1, Y1);
       xw_at(s, xw);
-      pass1<R, L>(A.mat[s][0], m, j, xw, F0, Y0);
+      apass1<R, L>(A.mat[s][0], m, j, xw, F0, Y0);
       put(10 * s + 9, F0, Y0);
     }
     __syncthreads();
@@ -377,27 +406,27 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       R aT[L], aS[L], x[L], G, X, sg;
       // cbar_U: lambda_T = 9 T^T cb, lambda_S = -8 S^T cb
       carries(10 * s + 0, G, X, sg);
-      pass2<R, L>(A.matT[s][1], m, j, cb[s], G, X, sg, aT);
+      apass2<R, L>(A.matT[s][1], m, j, cb[s], G, X, sg, aT);
       carries(10 * s + 5, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, xu[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][1], m, j, xu[s], G, X, sg, x);
       dterm(s, aT, xu[s], x, R(9));
       carries(10 * s + 1, G, X, sg);
-      pass2<R, L>(A.matT[s][2], m, j, cb[s], G, X, sg, aS);
+      apass2<R, L>(A.matT[s][2], m, j, cb[s], G, X, sg, aS);
       carries(10 * s + 6, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, xu[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][2], m, j, xu[s], G, X, sg, x);
       dterm(s, aS, xu[s], x, R(-8));
 #pragma unroll
       for (int t = 0; t < L; ++t) cb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
       // cbar_f
       carries(10 * s + 2, G, X, sg);
-      pass2<R, L>(A.matT[s][1], m, j, fb[s], G, X, sg, aT);
+      apass2<R, L>(A.matT[s][1], m, j, fb[s], G, X, sg, aT);
       carries(10 * s + 7, G, X, sg);
-      pass2<R, L>(A.mat[s][1], m, j, xf[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][1], m, j, xf[s], G, X, sg, x);
       dterm(s, aT, xf[s], x, R(9));
       carries(10 * s + 3, G, X, sg);
-      pass2<R, L>(A.matT[s][2], m, j, fb[s], G, X, sg, aS);
+      apass2<R, L>(A.matT[s][2], m, j, fb[s], G, X, sg, aS);
       carries(10 * s + 8, G, X, sg);
-      pass2<R, L>(A.mat[s][2], m, j, xf[s], G, X, sg, x);
+      apass2<R, L>(A.mat[s][2], m, j, xf[s], G, X, sg, x);
       dterm(s, aS, xf[s], x, R(-8));
 #pragma unroll
       for (int t = 0; t < L; ++t) fb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
@@ -405,9 +434,9 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       R xw[L];
       xw_at(s, xw);
       carries(10 * s + 4, G, X, sg);
-      pass2<R, L>(A.matT[s][0], m, j, wb[s], G, X, sg, aT);
+      apass2<R, L>(A.matT[s][0], m, j, wb[s], G, X, sg, aT);
       carries(10 * s + 9, G, X, sg);
-      pass2<R, L>(A.mat[s][0], m, j, xw, G, X, sg, x);
+      apass2<R, L>(A.mat[s][0], m, j, xw, G, X, sg, x);
       dterm(s, aT, xw, x, R(1));
 #pragma unroll
       for (int t = 0; t < L; ++t) wb[s][t] = aT[t];

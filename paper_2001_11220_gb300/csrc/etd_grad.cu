@@ -78,6 +78,11 @@ void upload(DeviceArena &arena, const HostTab &T, MatTab<R> &M, cudaError_t &err
   M.z1 = (const R *)arena.put(z1.data(), z1.size() * sizeof(R), err);
   M.rows1 = nullptr;
   M.rows2 = nullptr;  // adjoint sweeps run one line per thread
+  M.segc = nullptr;
+  if constexpr (sizeof(R) == 4) {
+    const std::vector<float> r1 = fp32_rows(T);
+    M.rows1 = (const float *)arena.put(r1.data(), r1.size() * sizeof(float), err);
+  }
   M.r = T.r;
   M.sm_c = T.sm_c;
   M.sm_inv = T.sm_inv;

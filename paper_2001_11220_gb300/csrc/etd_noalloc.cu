@@ -88,6 +88,7 @@ void stage_tab(const HostTab &T, MatTab<R> &M, Carve &cv, std::vector<std::pair<
   M.z1 = (const R *)up.back().first;
   M.rows1 = nullptr;
   M.rows2 = nullptr;  // the no-allocation step plans one line per thread
+  M.segc = nullptr;   // and whole lines per block
   if constexpr (sizeof(R) == 4) {
     const std::vector<float> r1 = fp32_rows(T);
     up.push_back({cv.take(r1.size() * sizeof(R)), std::vector<R>(r1.begin(), r1.end())});
