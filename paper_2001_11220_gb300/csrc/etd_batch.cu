@@ -4,6 +4,9 @@
 // multi-step runs are captured into a CUDA graph.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -89,7 +92,15 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
   };
   // common chunk length per axis (kernel template parameter), per-instance tiles
   int Lax[3];
-  for (int a = 0; a < dim; ++a) Lax[a] = (rb == 4) ? (a == 0 ? 8 : 16) : (a == 0 ? 4 : 8);
+  // FP32: 16 positions per thread on every axis (measured fastest for the 64..512 ensemble)
+  for (int a = 0; a < dim; ++a) Lax[a] = (rb == 4) ? 16 : (a == 0 ? 4 : 8);
+  // ETD_BATCH_CHUNK="L0,L1[,L2]" forces the chunk lengths (to compare shapes)
+  if (const char *f = std::getenv("ETD_BATCH_CHUNK")) {
+    int v[3] = {0, 0, 0};
+    if (sscanf(f, "%d,%d,%d", &v[0], &v[1], &v[2]) >= dim)
+      for (int a = 0; a < dim; ++a)
+        if (v[a] == 4 || v[a] == 8 || v[a] == 16) Lax[a] = v[a];
+  }
   size_t scratch_elems = 0;
   for (int i = 0; i < ninst; ++i) {
     Instance &I = ctx->inst[i];
@@ -114,6 +125,33 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
     const size_t F = (size_t)I.S * I.N;
     for (int f = 0; f < 3; ++f) I.scratch[f] = (unsigned char *)ctx->batch_scratch + (off + f * F) * rb;
     off += 3 * F;
+  }
+  // Blocks are as large as the largest instance needs; give every instance as
+  // many lines per block as fit that size (small instances would otherwise
+  // leave most of each block idle)
+  const char *nofill = std::getenv("ETD_BATCH_NOFILL");
+  for (int a = 0; a < dim && !(nofill && nofill[0] == '1'); ++a) {
+    int T = 0;
+    for (int i = 0; i < ninst; ++i) T = std::max(T, ctx->inst[i].plan[a].nthreads);
+    for (int i = 0; i < ninst; ++i) {
+      Instance &I = ctx->inst[i];
+      AxisPlan &P = I.plan[a];
+      const long long avail = (a == 0) ? P.nlines : P.st;
+      int nlb = P.nlb;
+      while (nlb * 2 * P.m <= T && nlb * 2 <= avail &&
+             sweep_smem_bytes(P.kind, I.S, nlb * 2, P.pitch, I.real_bytes) <= 200 * 1024)
+        nlb *= 2;
+      if (nlb == P.nlb) continue;
+      P.nlb = nlb;
+      P.nthreads = nlb * P.m;
+      P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes);
+      if (a == 0) {
+        P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
+      } else {
+        P.nlo_blocks = (int)((P.st + nlb - 1) / nlb);
+        P.nblocks = (int)((long long)P.nlo_blocks * (I.N / (P.st * I.n[a])));
+      }
+    }
   }
   for (int a = 0; a < dim; ++a) {
     std::vector<int> bs(ninst + 1, 0);
