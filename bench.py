@@ -228,6 +228,7 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
     with torch.cuda.stream(stream):
         ens = EtdEnsemble(ws, "fp32", stream=stream)
         states = [torch.tensor(W.initial_state(x), device="cuda", dtype=torch.float32) for x in ws]
+        ens.autotune([U.clone() for U in states])   # line-block shapes timed on scratch copies
     barrier()
     ms = _timed(lambda: ens.run(states, 0.0, 20), stream)
     units = sum(x.npoints * x.nspecies for x in ws) * 20

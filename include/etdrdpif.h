@@ -174,6 +174,15 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
                             void *stream, etd_ctx **out);
 etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps);
 
+/* Choose the ensemble's line-block shapes (the chunk length of every axis,
+ * shared by all instances; each instance then fills the common block size
+ * with as many lines as fit) by timing every candidate on the context's
+ * stream with CUDA events.  U_work: ninst device states of the instances'
+ * shapes, used as scratch (overwritten).  Synchronises; captured graphs are
+ * dropped.  ETD_ERR_INVALID_ARG on a single-problem context or null
+ * pointers. */
+etd_status etd_batch_autotune(etd_ctx *ctx, void *const *U_work);
+
 /* Re-tune the per-axis chunk lengths by timing every candidate on the
  * context's stream with CUDA events (work buffer: a device state of the
  * context's shape, overwritten).  Synchronises. */

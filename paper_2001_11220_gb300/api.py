@@ -185,15 +185,25 @@ class EtdEnsemble:
         self.ctx = ctx
         self.n = n
 
-    def run(self, states, t0: float, nsteps: int):
+    def _check_states(self, states):
         if len(states) != self.n:
             raise ValueError(f"expected {self.n} states")
         for U, shp in zip(states, self.shapes):
             if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous() and tuple(U.shape) == shp):
                 raise ValueError("every state must be a contiguous CUDA tensor of its instance's shape and dtype")
+
+    def run(self, states, t0: float, nsteps: int):
+        self._check_states(states)
         ptrs = (ctypes.c_void_p * self.n)(*[U.data_ptr() for U in states])
         B.check(self.lib.etd_batch_run(self.ctx, ptrs, float(t0), int(nsteps)), self.ctx)
         return states
+
+    def autotune(self, work_states):
+        """Pick the line-block shapes by timing candidates; work_states are scratch
+        device states of the instances' shapes (overwritten)."""
+        self._check_states(work_states)
+        ptrs = (ctypes.c_void_p * self.n)(*[U.data_ptr() for U in work_states])
+        B.check(self.lib.etd_batch_autotune(self.ctx, ptrs), self.ctx)
 
     def info(self) -> dict:
         inf = B.etd_info()

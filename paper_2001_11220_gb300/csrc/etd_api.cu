@@ -334,8 +334,24 @@ int default_chunk(const Instance &I, int a) {
 
 // ------------------------------------------------------------ tables
 
-template <typename R>
-static void upload_tab(DeviceArena &arena, const HostTab &T, MatTab<R> &M, std::vector<void *> &owned,
+// Places a set of tables in one device block: a sizing pass (no device
+// block yet; the returned pointers are placeholders), then a pass with the
+// block allocated, whose host image goes up in one copy.
+struct StagedArena {
+  unsigned char *dev = nullptr;
+  std::vector<unsigned char> host;
+  size_t used = 0;
+  void *put(const void *src, size_t bytes, cudaError_t &) {
+    const size_t off = used;
+    used += (bytes + 255) & ~(size_t)255;
+    if (host.size() < used) host.resize(used);
+    memcpy(host.data() + off, src, bytes);
+    return dev ? dev + off : nullptr;
+  }
+};
+
+template <typename R, typename Arena>
+static void upload_tab(Arena &arena, const HostTab &T, MatTab<R> &M, std::vector<void *> &owned,
                        cudaError_t &err) {
   std::vector<R> pos(T.pos.begin(), T.pos.end()), sum(T.sum.begin(), T.sum.end()),
       chunk(T.chunk.begin(), T.chunk.end());
@@ -375,19 +391,36 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
   cudaError_t err = cudaSuccess;
   static const double gammas[3] = {1.0, 3.0, 4.0};
   {
+    // every table of the axis in one device block (replaced when the axis is re-planned)
     const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+    std::vector<HostTab> tabs;
     for (int s = 0; s < I.S; ++s)
       for (int g = 0; g < 3; ++g)
         for (int tr = 0; tr < 2; ++tr) {
           const double r = (I.k / gammas[g]) * I.D[s] / (h * h);
-          HostTab T;
-          build_tab((int)I.n[a], I.bc[a], r, tr != 0, I.plan[a].L, T, I.plan[a].mx, I.plan[a].nseg);
-          if (I.real_bytes == 8)
-            upload_tab<double>(I.arena, T, I.tab64[tr][a][s][g], I.owned, err);
-          else
-            upload_tab<float>(I.arena, T, I.tab32[tr][a][s][g], I.owned, err);
-          if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
+          tabs.emplace_back();
+          build_tab((int)I.n[a], I.bc[a], r, tr != 0, I.plan[a].L, tabs.back(), I.plan[a].mx, I.plan[a].nseg);
         }
+    StagedArena st;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) {
+        if (I.axis_tables[a]) cudaFree(I.axis_tables[a]);
+        I.axis_tables[a] = nullptr;
+        err = cudaMalloc((void **)&I.axis_tables[a], st.used);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "line table allocation");
+        st.dev = (unsigned char *)I.axis_tables[a];
+        st.used = 0;
+      }
+      int q = 0;
+      for (int s = 0; s < I.S; ++s)
+        for (int g = 0; g < 3; ++g)
+          for (int tr = 0; tr < 2; ++tr, ++q) {
+            if (I.real_bytes == 8) upload_tab<double>(st, tabs[q], I.tab64[tr][a][s][g], I.owned, err);
+            else upload_tab<float>(st, tabs[q], I.tab32[tr][a][s][g], I.owned, err);
+          }
+    }
+    err = cudaMemcpy(I.axis_tables[a], st.host.data(), st.used, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
   }
   AxisPlan &P = I.plan[a];
   if (P.nseg > 1) {
@@ -788,6 +821,10 @@ void etd_destroy(etd_ctx *ctx) {
     for (void *p : I.owned) cudaFree(p);
     I.owned.clear();
     I.arena.release();
+    for (void *&p : I.axis_tables) {
+      if (p) cudaFree(p);
+      p = nullptr;
+    }
   }
   if (ctx->host_state) cudaFree(ctx->host_state);
   if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);

@@ -61,6 +61,82 @@ etd_status upload_batch_args(etd_ctx *ctx, void *const *U) {
   return ETD_OK;
 }
 
+// Plan every instance's sweeps with chunk length Lax[a] on axis a, rebuild
+// their line tables, let instances fill the common block size with more
+// lines, and (re)build the block prefix sums of the launches.
+etd_status plan_batch(etd_ctx *ctx, const int *Lax) {
+  const int ninst = (int)ctx->inst.size();
+  const int dim = ctx->inst[0].dim;
+  const int rb = ctx->inst[0].real_bytes;
+  for (int i = 0; i < ninst; ++i) {
+    Instance &I = ctx->inst[i];
+    for (int a = 0; a < dim; ++a) {
+      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true, 1))
+        return fail(ctx, ETD_ERR_UNSUPPORTED, "instance %d axis %d does not fit one block", i, a);
+    }
+  }
+  // Blocks are as large as the largest instance needs; give every instance as
+  // many lines per block as fit that size (small instances would otherwise
+  // leave most of each block idle)
+  const char *nofill = std::getenv("ETD_BATCH_NOFILL");
+  for (int a = 0; a < dim && !(nofill && nofill[0] == '1'); ++a) {
+    int T = 0;
+    for (int i = 0; i < ninst; ++i) T = std::max(T, ctx->inst[i].plan[a].nthreads);
+    for (int i = 0; i < ninst; ++i) {
+      Instance &I = ctx->inst[i];
+      AxisPlan &P = I.plan[a];
+      const long long avail = (a == 0) ? P.nlines : P.st;
+      int nlb = P.nlb;
+      while (nlb * 2 * P.m <= T && nlb * 2 <= avail &&
+             sweep_smem_bytes(P.kind, I.S, nlb * 2, P.pitch, I.real_bytes) <= 200 * 1024)
+        nlb *= 2;
+      if (nlb == P.nlb) continue;
+      P.nlb = nlb;
+      P.nthreads = nlb * P.m;
+      P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes);
+      if (a == 0) {
+        P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
+      } else {
+        P.nlo_blocks = (int)((P.st + nlb - 1) / nlb);
+        P.nblocks = (int)((long long)P.nlo_blocks * (I.N / (P.st * I.n[a])));
+      }
+    }
+  }
+  for (int i = 0; i < ninst; ++i)
+    for (int a = 0; a < dim; ++a) {
+      etd_status st = build_axis_tables(ctx, ctx->inst[i], a);
+      if (st != ETD_OK) return st;
+    }
+  for (int a = 0; a < dim; ++a) {
+    std::vector<int> bs(ninst + 1, 0);
+    int thr = 0;
+    size_t smem = 0;
+    for (int i = 0; i < ninst; ++i) {
+      const AxisPlan &P = ctx->inst[i].plan[a];
+      bs[i + 1] = bs[i] + P.nblocks;
+      thr = std::max(thr, P.nthreads);
+      smem = std::max(smem, P.smem);
+    }
+    ctx->batch_total_blocks[a] = bs[ninst];
+    ctx->batch_threads[a] = thr;
+    ctx->batch_smem[a] = smem;
+    ctx->batch_L[a] = Lax[a];
+    const size_t argb = (rb == 8 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>)) * ninst;
+    if (!ctx->batch_args[a] && cudaMalloc(&ctx->batch_args[a], argb) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "ensemble launch tables");
+    if (!ctx->batch_block_start[a] && cudaMalloc((void **)&ctx->batch_block_start[a], sizeof(int) * (ninst + 1)) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "ensemble launch tables");
+    if (cudaMemcpy(ctx->batch_block_start[a], bs.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return fail(ctx, ETD_ERR_CUDA, "ensemble launch tables upload");
+  }
+  // arguments and captured graphs refer to the old plan: rebuild on the next run
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  ctx->batch_states.clear();
+  return ETD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -106,14 +182,6 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
     Instance &I = ctx->inst[i];
     etd_status st = init_instance(ctx, I, &grids[i], D + (size_t)i * S, &reactions[i], k, precision, false);
     if (st != ETD_OK) return abort_create(st);
-    for (int a = 0; a < dim; ++a) {
-      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true, 1)) {
-        fail(ctx, ETD_ERR_UNSUPPORTED, "instance %d axis %d does not fit one block", i, a);
-        return abort_create(ETD_ERR_UNSUPPORTED);
-      }
-      st = build_axis_tables(ctx, I, a);
-      if (st != ETD_OK) return abort_create(st);
-    }
     scratch_elems += (size_t)3 * I.S * I.N;
   }
   if (cudaMalloc(&ctx->batch_scratch, scratch_elems * rb) != cudaSuccess) {
@@ -126,59 +194,8 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
     for (int f = 0; f < 3; ++f) I.scratch[f] = (unsigned char *)ctx->batch_scratch + (off + f * F) * rb;
     off += 3 * F;
   }
-  // Blocks are as large as the largest instance needs; give every instance as
-  // many lines per block as fit that size (small instances would otherwise
-  // leave most of each block idle)
-  const char *nofill = std::getenv("ETD_BATCH_NOFILL");
-  for (int a = 0; a < dim && !(nofill && nofill[0] == '1'); ++a) {
-    int T = 0;
-    for (int i = 0; i < ninst; ++i) T = std::max(T, ctx->inst[i].plan[a].nthreads);
-    for (int i = 0; i < ninst; ++i) {
-      Instance &I = ctx->inst[i];
-      AxisPlan &P = I.plan[a];
-      const long long avail = (a == 0) ? P.nlines : P.st;
-      int nlb = P.nlb;
-      while (nlb * 2 * P.m <= T && nlb * 2 <= avail &&
-             sweep_smem_bytes(P.kind, I.S, nlb * 2, P.pitch, I.real_bytes) <= 200 * 1024)
-        nlb *= 2;
-      if (nlb == P.nlb) continue;
-      P.nlb = nlb;
-      P.nthreads = nlb * P.m;
-      P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes);
-      if (a == 0) {
-        P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
-      } else {
-        P.nlo_blocks = (int)((P.st + nlb - 1) / nlb);
-        P.nblocks = (int)((long long)P.nlo_blocks * (I.N / (P.st * I.n[a])));
-      }
-    }
-  }
-  for (int a = 0; a < dim; ++a) {
-    std::vector<int> bs(ninst + 1, 0);
-    int thr = 0;
-    size_t smem = 0;
-    for (int i = 0; i < ninst; ++i) {
-      const AxisPlan &P = ctx->inst[i].plan[a];
-      bs[i + 1] = bs[i] + P.nblocks;
-      thr = std::max(thr, P.nthreads);
-      smem = std::max(smem, P.smem);
-    }
-    ctx->batch_total_blocks[a] = bs[ninst];
-    ctx->batch_threads[a] = thr;
-    ctx->batch_smem[a] = smem;
-    ctx->batch_L[a] = Lax[a];
-    const size_t argb = (rb == 8 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>)) * ninst;
-    if (cudaMalloc(&ctx->batch_args[a], argb) != cudaSuccess ||
-        cudaMalloc((void **)&ctx->batch_block_start[a], sizeof(int) * (ninst + 1)) != cudaSuccess) {
-      fail(ctx, ETD_ERR_OOM, "ensemble launch tables");
-      return abort_create(ETD_ERR_OOM);
-    }
-    if (cudaMemcpy(ctx->batch_block_start[a], bs.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
-      fail(ctx, ETD_ERR_CUDA, "ensemble launch tables upload");
-      return abort_create(ETD_ERR_CUDA);
-    }
-  }
+  etd_status st = plan_batch(ctx, Lax);
+  if (st != ETD_OK) return abort_create(st);
   *out = ctx;
   return ETD_OK;
 }
@@ -221,6 +238,48 @@ etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps
     return cudaSuccess;
   };
   return run_steps(ctx, enqueue, GraphKey{ctx->batch_states.data(), nullptr, t0, nsteps}, nsteps);
+}
+
+etd_status etd_batch_autotune(etd_ctx *ctx, void *const *U_work) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_batch_autotune on a single-problem context");
+  if (!U_work) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work is NULL");
+  const int ninst = (int)ctx->inst.size();
+  for (int i = 0; i < ninst; ++i)
+    if (!U_work[i]) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work[%d] is NULL", i);
+  const int dim = ctx->inst[0].dim;
+  const bool fp32 = ctx->precision != ETD_FP64;
+  const int choices[2] = {fp32 ? 8 : 4, fp32 ? 16 : 8};
+  int keep[3] = {ctx->batch_L[0], ctx->batch_L[1], ctx->batch_L[2]};
+  int best[3] = {keep[0], keep[1], keep[2]};
+  double best_ms = 1e30;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(ctx, ETD_ERR_CUDA, "autotune events");
+  etd_status st = ETD_OK;
+  for (int c = 0; c < (1 << dim) && st == ETD_OK; ++c) {
+    int Lax[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) Lax[a] = choices[(c >> a) & 1];
+    if (plan_batch(ctx, Lax) != ETD_OK) continue;  // this shape does not fit every instance
+    st = etd_batch_run(ctx, U_work, 0.0, 2);       // warm-up (arguments, graph)
+    if (st != ETD_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    st = etd_batch_run(ctx, U_work, 0.0, 2);
+    cudaEventRecord(e1, ctx->stream);
+    if (st != ETD_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (std::getenv("ETD_TUNE_VERBOSE"))
+      fprintf(stderr, "etd_batch_autotune L = %d,%d,%d -> %.4f ms/step\n", Lax[0], Lax[1], Lax[2], ms / 2);
+    if (ms < best_ms) {
+      best_ms = ms;
+      for (int a = 0; a < 3; ++a) best[a] = Lax[a];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ETD_OK) return st;
+  return plan_batch(ctx, best_ms < 1e30 ? best : keep);
 }
 
 }  // extern "C"

@@ -91,7 +91,8 @@ struct Instance {
   AxisPlan aplan[3];
   MatTab<float> atab32[2][3][MAX_SPECIES][3];
   MatTab<double> atab64[2][3][MAX_SPECIES][3];
-  DeviceArena arena;
+  DeviceArena arena;                               // source tables, adjoint tables
+  void *axis_tables[3] = {nullptr, nullptr, nullptr};  // forward line tables of each axis (one block)
   std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
 };
 

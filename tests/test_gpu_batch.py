@@ -27,14 +27,17 @@ def small_ensemble(n=14, seed=5):
     return ws
 
 
+@pytest.mark.parametrize("tuned", [False, True], ids=["planned", "autotuned"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_ensemble_matches_oracle_per_instance(prec):
+def test_ensemble_matches_oracle_per_instance(prec, tuned):
     from paper_2001_11220_gb300.api import EtdEnsemble
     ws = small_ensemble()
     dt = torch.float64 if prec == "fp64" else torch.float32
     U0 = [W.initial_state(w) for w in ws]
     states = [torch.tensor(u, device="cuda", dtype=dt) for u in U0]
     ens = EtdEnsemble(ws, prec)
+    if tuned:  # shapes picked by timing candidates on scratch copies
+        ens.autotune([U.clone() for U in states])
     ens.run(states, 0.1, 3)
     torch.cuda.synchronize()
     worst = 0.0
@@ -43,7 +46,8 @@ def test_ensemble_matches_oracle_per_instance(prec):
         e = rel(U.double().cpu().numpy(), ref)
         worst = max(worst, e)
         assert e <= (FP64_TOL if prec == "fp64" else 3 * FP32_STEP_TOL), (w.name, w.n, w.bc, e)
-    print(f"ensemble {prec}: worst per-instance error vs oracle after 3 steps {worst:.3e}")
+    print(f"ensemble {prec} ({'autotuned' if tuned else 'planned'}): worst per-instance error vs oracle "
+          f"after 3 steps {worst:.3e}")
     ens.close()
 
 
