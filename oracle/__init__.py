@@ -29,13 +29,19 @@ ZERO, LINEAR, BRUSSELATOR, SCHNAKENBERG, GRAY_SCOTT, ENZYME = range(6)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/liboracle.so (gcc, -O2, no -march)."""
+    """Compile the oracle into oracle/liboracle.so (gcc, -O2, no -march).
+
+    Built with OpenMP where gcc has it (independent lines and points are
+    shared among host threads; each is computed exactly as in the serial
+    loop), else serially.
+    """
     newest = max(os.path.getmtime(p) for p in _SRC + [_HDR])
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp] + _SRC
+    if subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.run(base + ["-lm"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -141,8 +147,24 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
+        lib.oracle_get_threads.argtypes = []
+        lib.oracle_get_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the oracle's line and point loops; returns the count
+    now in use (1 for a serial build)."""
+    lib = _load()
+    lib.oracle_set_threads(int(n))
+    return lib.oracle_get_threads()
+
+
+def get_threads() -> int:
+    return _load().oracle_get_threads()
 
 
 def _arr(x, shape=None) -> np.ndarray:

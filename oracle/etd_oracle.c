@@ -8,6 +8,10 @@
  */
 #include "etd_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -180,21 +184,44 @@ int oracle_axis_solve(const oracle_problem *P, int a, double gamma, int transpos
   long st = axis_stride(P, a);
   long nhigh = N / (st * p);
   double h = oracle_h(P, a);
-  double *line = (double *)malloc(sizeof(double) * p);
   for (int s = 0; s < P->nspecies; ++s) {
     double r = (P->k / gamma) * P->D[s] / (h * h);
     const double *src = in + s * N;
     double *dst = out + s * N;
-    for (long hi = 0; hi < nhigh; ++hi)
-      for (long lo = 0; lo < st; ++lo) {
+    /* lines are independent: with OpenMP they are shared among host threads
+     * (each with its own line buffer); the arithmetic per line is unchanged */
+#pragma omp parallel
+    {
+      double *line = (double *)malloc(sizeof(double) * p);
+#pragma omp for schedule(static)
+      for (long q = 0; q < nhigh * st; ++q) {
+        long hi = q / st, lo = q % st;
         long base = lo + hi * st * p;
         for (int i = 0; i < p; ++i) line[i] = src[base + i * st];
         oracle_line_solve(p, P->bc[a], r, transpose, line, line);
         for (int i = 0; i < p; ++i) dst[base + i * st] = line[i];
       }
+      free(line);
+    }
   }
-  free(line);
   return 0;
+}
+
+/* host threads for the line loops (OpenMP builds; ignored otherwise) */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int oracle_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* out = B_a in per species (no D): the -Laplacian along axis a, Example 1. */
@@ -341,9 +368,11 @@ static void reaction_point(const oracle_problem *P, const double *u, const int *
 int oracle_reaction(const oracle_problem *P, const double *U, double t, double *F) {
   if (check_problem(P)) return -1;
   long N = npoints(P);
-  int S = P->nspecies, idx[3];
-  double u[4], f[4], J[4][4], G[4][8];
+  int S = P->nspecies;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < N; ++i) {
+    int idx[3];
+    double u[4], f[4], J[4][4], G[4][8];
     point_index(P, i, idx);
     for (int s = 0; s < S; ++s) u[s] = U[s * N + i];
     reaction_point(P, u, idx, t, f, J, G);
@@ -448,6 +477,7 @@ static void step_forward(const oracle_problem *P, const double *Un, double t, st
   int d = P->dim;
   double k = P->k;
   oracle_reaction(P, Un, t, W->f0);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < M; ++i) {
     W->cU[0][i] = Un[i];
     W->cf[0][i] = W->f0[i];
@@ -459,6 +489,7 @@ static void step_forward(const oracle_problem *P, const double *Un, double t, st
     oracle_axis_solve(P, a, 3.0, 0, W->cf[a], W->xT_f[a]);
     oracle_axis_solve(P, a, 4.0, 0, W->cf[a], W->xS_f[a]);
     oracle_axis_solve(P, a, 1.0, 0, W->w[a], W->w[a + 1]);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < M; ++i) {
       W->cU[a + 1][i] = 9.0 * W->xT_U[a][i] - 8.0 * W->xS_U[a][i];
       W->cf[a + 1][i] = 9.0 * W->xT_f[a][i] - 8.0 * W->xS_f[a][i];
@@ -466,12 +497,14 @@ static void step_forward(const oracle_problem *P, const double *Un, double t, st
   }
   oracle_axis_solve(P, d - 1, 1.0, 0, W->w[d - 1], W->Ustar);
   oracle_reaction(P, W->Ustar, t + k, W->fstar);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < M; ++i) {
     W->f1[i] = 9.0 * W->cU[d - 1][i] + 2.0 * k * W->cf[d - 1][i] + k * W->fstar[i];
     W->f2[i] = 8.0 * W->cU[d - 1][i] + 1.5 * k * W->cf[d - 1][i] + 0.5 * k * W->fstar[i];
   }
   oracle_axis_solve(P, d - 1, 3.0, 0, W->f1, W->d1);
   oracle_axis_solve(P, d - 1, 4.0, 0, W->f2, W->d2);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < M; ++i) Unext[i] = W->d1[i] - W->d2[i];
 }
 

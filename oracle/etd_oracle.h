@@ -94,6 +94,11 @@ int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
 int oracle_grad(const oracle_problem *P, const double *U0, double t0, const double *target,
                 long nsteps, double *loss, double *dU0, double *dD, double *dparams);
 
+/* host threads for the line and point loops of an OpenMP build (each line and
+ * each point is computed exactly as in the serial loop; set 1 for one core). */
+void oracle_set_threads(int n);
+int oracle_get_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -412,3 +412,21 @@ def test_grad_multistep_vs_finite_differences():
         Dm[s] -= eps
         fdD = (L(dr.oracle_problem(w.with_(D=tuple(Dp))), U0) - L(dr.oracle_problem(w.with_(D=tuple(Dm))), U0)) / (2 * eps)
         assert abs(fdD - dD[s]) < 1e-5 * max(1, abs(fdD))
+
+
+def test_threads_do_not_change_results():
+    """The OpenMP loops share out independent lines and points; every value
+    must be bit-identical to the one-thread result."""
+    import oracle
+    P = oracle.Problem(n=(9, 7, 11), bc=(0, 2, 1), D=(0.7, 0.2), reaction=oracle.BRUSSELATOR,
+                       params=(1.0, 3.0), k=0.01)
+    U0 = 1.0 + 0.1 * np.random.default_rng(3).standard_normal(P.shape)
+    prev = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        a = oracle.run(P, U0, 0.0, 3)
+        oracle.set_threads(4)
+        b = oracle.run(P, U0, 0.0, 3)
+    finally:
+        oracle.set_threads(prev)
+    assert np.array_equal(a, b)
