@@ -107,10 +107,12 @@ typedef struct {
   int32_t lines_per_block[3];    /* lines per tile / block per axis */
   int32_t staged[3];             /* 0: register kernel, 1: persistent shared-memory-staged kernel,
                                     2: FP32 tile kernel (lines_per_block then counts line units),
-                                    3: segmented register kernel (long lines split over blocks) */
+                                    3: segmented register kernel (long lines split over blocks;
+                                    summary, carry and solve launches), 4: the same in one launch,
+                                    the blocks of a line group forming a thread-block cluster */
   int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
                                     (lines_per_block then counts pairs), 1: one line per thread;
-                                    segmented kernel: chunks per segment */
+                                    segmented kernels: chunks per segment */
 } etd_info;
 
 /* Create a context for one problem.  Validates every argument

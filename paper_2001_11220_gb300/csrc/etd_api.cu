@@ -147,6 +147,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   P.pk = 1;
   P.mx = P.m;
   P.nseg = 1;
+  P.cluster = false;
   if (pack == 2) {
     // register kernel on line pairs (lo, lo + 1) of a strided FP32 axis with an even stride
     if (I.real_bytes != 4 || a == 0 || st % 2 != 0 || L != 8) return false;
@@ -241,6 +242,7 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
   P.pk = pk;
   P.mx = m;
   P.nseg = 1;
+  P.cluster = false;
   const int S = I.S, nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
   StagePlan sp{};
   sp.staged = 2;
@@ -282,13 +284,17 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
 
 // Segmented register kernel for long lines: blocks of nlb lines x mx chunks
 // (mx a multiple of 8, m > mx), nseg = ceil(m / mx) blocks along every line
-// (summary, carry and solve launches, see SegPhase)
-bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx) {
+// (summary, carry and solve launches, see SegPhase).  cluster: the nseg
+// blocks of a line group form one thread-block cluster and the sweep is one
+// launch (nseg <= ETD_MAX_CLUSTER; whether the device can hold such a cluster
+// is checked by cluster_plan_fits).
+bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster) {
   AxisPlan &P = I.plan[a];
   const long long n = I.n[a];
   const int m = (int)((n + L - 1) / L);
   if ((L != 4 && L != 8 && L != 16) || mx < 8 || mx % 8 != 0 || m <= mx || nlb < 1 || nlb * mx > ETD_MAX_BLOCK_THREADS)
     return false;
+  if (cluster && (m + mx - 1) / mx > ETD_MAX_CLUSTER) return false;
   long long st = 1;
   for (int b = 0; b < a; ++b) st *= I.n[b];
   P.L = L;
@@ -313,8 +319,33 @@ bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx) {
   if (line_blocks * P.nseg > INT_MAX) return false;
   P.nblocks = (int)(line_blocks * P.nseg);
   P.nthreads = nlb * mx;
-  P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1);
+  P.cluster = cluster;
+  P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1, cluster);
   return P.smem <= 200 * 1024;
+}
+
+// a cluster-segmented plan of axis a can launch on the current device
+bool cluster_plan_fits(const Instance &I, int a) {
+  const AxisPlan &P = I.plan[a];
+  if (!P.cluster) return true;
+  int nclusters = 0;
+  cudaError_t e;
+  if (I.real_bytes == 8) {
+    SweepArgs<double> A;
+    fill_args<double>(I, a, 0, A);
+    A.segphase = SEG_CLUSTER;
+    e = sweep_cluster_capacity(A, I.S, P.L, P.kind, P.nthreads, P.smem, nclusters);
+  } else {
+    SweepArgs<float> A;
+    fill_args<float>(I, a, 0, A);
+    A.segphase = SEG_CLUSTER;
+    e = sweep_cluster_capacity(A, I.S, P.L, P.kind, P.nthreads, P.smem, nclusters);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // a refused configuration is not a sticky error
+    return false;
+  }
+  return nclusters > 0;
 }
 
 // tile kernels move U with 16-byte copies
@@ -423,7 +454,7 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
     if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
   }
   AxisPlan &P = I.plan[a];
-  if (P.nseg > 1) {
+  if (P.nseg > 1 && !P.cluster) {
     // segment summaries and carries (2 values per solve, line and segment) and scalars
     const int nq = (P.kind == SWEEP_LAST) ? 3 * I.S : 5 * I.S;
     const size_t need = ((size_t)4 * nq * P.nlines * P.nseg + (size_t)nq * P.nlines) * I.real_bytes;
@@ -513,7 +544,7 @@ void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
   A.mx = P.mx;
   A.nseg = P.nseg;
   A.segphase = SEG_WHOLE;
-  if (P.nseg > 1) {
+  if (P.nseg > 1 && P.seg_buf) {
     const int nq = (P.kind == SWEEP_LAST) ? 3 * I.S : 5 * I.S;
     const size_t pairs = (size_t)2 * nq * P.nlines * P.nseg;
     A.seg_sum = (R *)P.seg_buf;
@@ -529,6 +560,10 @@ template <typename R>
 cudaError_t run_sweep(const Instance &I, int a, SweepArgs<R> &A, cudaStream_t s) {
   const AxisPlan &P = I.plan[a];
   if (P.nseg <= 1) return launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+  if (P.cluster) {
+    A.segphase = SEG_CLUSTER;
+    return launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
+  }
   const int S = I.S;
   auto sweep = [&](int phase) {
     A.segphase = phase;
@@ -636,8 +671,9 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   I.real_bytes = precision == ETD_FP64 ? 8 : 4;
   // ETD_TILES="L:nlb:kernel[:pack],..." (one entry per axis; kernel 0
   // register, 1 staged, 2 tile with nlb lines per block, 3 segmented register
-  // kernel with the fourth field = chunks per segment) forces tile shapes,
-  // e.g. to reproduce an autotuned configuration in a profiler run
+  // kernel with the fourth field = chunks per segment, 4 the same as one
+  // cluster launch) forces tile shapes, e.g. to reproduce an autotuned
+  // configuration in a profiler run
   const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
     int L = default_chunk(I, a);
@@ -649,7 +685,8 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
         if (p) ++p;
       }
       if (p && sscanf(p, "%d:%d:%d:%d", &fl, &fn, &fs, &fp) >= 3 && (fl == 4 || fl == 8 || fl == 16)) {
-        const bool ok = fs == 3   ? plan_axis_seg(I, a, fl, fn, fp)
+        const bool ok = fs == 4   ? plan_axis_seg(I, a, fl, fn, fp, true) && cluster_plan_fits(I, a)
+                        : fs == 3 ? plan_axis_seg(I, a, fl, fn, fp, false)
                         : fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)
                                   : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1);
         if (ok) continue;
@@ -791,13 +828,14 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     N += J.N;
     scratch += 3LL * J.S * J.N * J.real_bytes;
   }
-  // one launch per sweep; a segmented sweep takes 3 (LAST: 5)
+  // one launch per sweep; a segmented sweep takes 3 (LAST: 5) unless it is
+  // one cluster launch
   launches = 0;
   for (int a = 0; a < I.dim; ++a)
-    launches += ctx->batched || I.plan[a].nseg <= 1 ? 1 : (I.plan[a].kind == SWEEP_LAST ? 5 : 3);
+    launches += ctx->batched || I.plan[a].nseg <= 1 || I.plan[a].cluster ? 1 : (I.plan[a].kind == SWEEP_LAST ? 5 : 3);
   for (const Instance &J : ctx->inst)
     for (int a = 0; a < J.dim; ++a)
-      if (J.plan[a].nseg > 1) scratch += (long long)J.plan[a].seg_bytes;
+      if (J.plan[a].nseg > 1 && J.plan[a].seg_buf) scratch += (long long)J.plan[a].seg_bytes;
   info->npoints = N;
   info->state_bytes = (int64_t)I.S * N * I.real_bytes;
   info->scratch_bytes = scratch;
@@ -807,7 +845,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   for (int a = 0; a < I.dim; ++a) {
     info->chunk[a] = I.plan[a].L;
     info->lines_per_block[a] = I.plan[a].nlb;
-    info->staged[a] = I.plan[a].nseg > 1 ? 3 : I.plan[a].sp.staged;
+    info->staged[a] = I.plan[a].nseg > 1 ? (I.plan[a].cluster ? 4 : 3) : I.plan[a].sp.staged;
     info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
   }
   return ETD_OK;

@@ -62,6 +62,7 @@ struct AxisPlan {
   int pk = 1;          // 2: register kernel on FP32 line pairs (nlb counts pairs)
   int mx = 1;          // chunks per block along the line (= m unless segmented)
   int nseg = 1;        // segments per line (> 1: segmented sweep, see SegPhase)
+  bool cluster = false;  // segmented in one launch: the segments of a line group form a cluster
   void *seg_buf = nullptr;  // segmented sweeps: summaries, carries, scalars (owned)
   size_t seg_bytes = 0;
   StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel

@@ -128,7 +128,13 @@ template <typename R> struct SweepArgs {
 // SEG_SUMMARY covers the P solves; SEG_SOLVE solves P from its carries, forms
 // U*, F* and f1, f2 and writes the summaries of the T and S solves; SEG_FINAL
 // solves everything from its carries.  SEG_WHOLE: lines are not split.
-enum SegPhase { SEG_WHOLE = 0, SEG_SUMMARY = 1, SEG_SOLVE = 2, SEG_FINAL = 3 };
+// SEG_CLUSTER: one launch; the nseg blocks of a line group form a thread-block
+// cluster and exchange their segment summaries through distributed shared
+// memory (one exchange per dependent group of solves: FIRST/MIDDLE one, LAST two).
+enum SegPhase { SEG_WHOLE = 0, SEG_SUMMARY = 1, SEG_SOLVE = 2, SEG_FINAL = 3, SEG_CLUSTER = 4 };
+
+// largest cluster of a cluster-segmented sweep (16 needs the non-portable size)
+constexpr int ETD_MAX_CLUSTER = 16;
 
 enum AdjKind { ADJ_FIRST = 0, ADJ_MIDDLE = 1, ADJ_LAST = 2 };
 
@@ -144,6 +150,18 @@ cudaError_t launch_sweep_batched(const SweepArgs<float> *args_dev, const int *bl
 cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *block_start_dev, int ninst,
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
                                  size_t smem, cudaStream_t s, double t_eval);
+
+// cluster-segmented register sweeps (a.segphase = SEG_CLUSTER; FP32 L = 8 or
+// 16, FP64 L = 4 or 8): the launch, and the clusters that fit on the device
+// at once (0: the configuration cannot launch)
+cudaError_t launch_sweep_cluster(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                 cudaStream_t s);
+cudaError_t launch_sweep_cluster(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads,
+                                 size_t smem, cudaStream_t s);
+cudaError_t sweep_cluster_capacity(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads,
+                                   size_t smem, int &nclusters);
+cudaError_t sweep_cluster_capacity(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads,
+                                   size_t smem, int &nclusters);
 
 // FP32 tile kernels: NLB lines per block, pk = 1 or 2 (line pairs, strided axes)
 cudaError_t launch_tile(const SweepArgs<float> &a, int nspecies, int L, int NLB, int kind, int pk, int nthreads,
@@ -183,11 +201,15 @@ inline int exchange_pitch(int m) { return ((m + 7) & ~7) + 1; }
 
 // shared-memory bytes of one sweep block (pk = 2: nlb line pairs); the
 // Sherman-Morrison scalars take 8 bytes each (stored in the sweep's precision)
-inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes, int pk = 1) {
+// cluster-segmented sweeps add the segment summaries (G, X) of every
+// (solve, line unit), read by the other blocks of the cluster
+inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes, int pk = 1,
+                               bool cluster = false) {
   int nq = (kind == SWEEP_LAST) ? 3 * nspecies : 5 * nspecies;
   size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes * pk;
   sums = (sums + 15) & ~(size_t)15;
-  return sums + (size_t)nq * nlb * pk * sizeof(double);
+  size_t sig = ((size_t)nq * nlb * pk * sizeof(double) + 15) & ~(size_t)15;
+  return sums + sig + (cluster ? (size_t)2 * nq * nlb * pk * real_bytes : 0);
 }
 
 }  // namespace etd

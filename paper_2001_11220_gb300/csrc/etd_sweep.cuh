@@ -758,15 +758,152 @@ struct SegCtx {
 
 __device__ __forceinline__ SegCtx whole_lines(int m) { return SegCtx{SEG_WHOLE, 0, 0, m, 0, 0}; }
 
+// ---- thread-block clusters (cluster-segmented sweeps)
+// Split cluster barrier: arrive publishes this thread's shared-memory writes
+// (release), wait returns once every thread of the cluster has arrived
+// (acquire).  Hardware barriers: no spinning in software.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory"); }
+__device__ __forceinline__ unsigned cluster_nranks() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+  return r;
+}
+// address of the same shared-memory object in block `rank` of the cluster
+__device__ __forceinline__ unsigned dsmem_map(unsigned cta_addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(cta_addr), "r"(rank));
+  return r;
+}
+// a segment summary (G, X) from distributed shared memory
+__device__ __forceinline__ void ld_dsmem_pair(unsigned a, float &g, float &x) {
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(g), "=f"(x) : "r"(a));
+}
+__device__ __forceinline__ void ld_dsmem_pair(unsigned a, double &g, double &x) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];\n" : "=d"(g), "=d"(x) : "r"(a));
+}
+__device__ __forceinline__ void ld_dsmem_pair(unsigned a, float2 &g, float2 &x) {
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(g.x), "=f"(g.y), "=f"(x.x), "=f"(x.y)
+               : "r"(a));
+}
+
+// Zero-carry summary of one segment of one (line, solve) without touching
+// F/Y: the forward value after the segment, G = sum_j (prod_{i>j} A_i) F_j,
+// and the solution value at its first position with zero carries,
+// X = sum_j (prod_{i<j} B_i) (Y_j + kappa_j G_in[j]) (chunk maps of the
+// segment: forward G -> A G + F, backward X -> B X + Y + kappa G_in).
+template <typename R, typename V>
+__device__ __forceinline__ void segment_summary(const MatTab<R> &M, const V *F, const V *Y, int m, int jb, V &Gout,
+                                                V &Xout) {
+  V G = Splat<V>::of(R(0)), X = G;
+  R pb = R(1);
+  for (int j = 0; j < m; ++j) {
+    const typename V4T<R>::T c = ld_chunk(M, jb + j);
+    const V y = vfma(Splat<V>::of(c.y), G, Y[j]);
+    X = vfma(Splat<V>::of(pb), y, X);
+    pb *= c.z;
+    G = vfma(Splat<V>::of(c.x), G, F[j]);
+  }
+  Gout = G;
+  Xout = X;
+}
+
+// Cluster-segmented chaining of solves q0..q0+nq-1 (block = segment sc.seg
+// of nlb lines; the cluster's blocks hold the line's other segments, block
+// rank = segment).  Every (line, solve) unit publishes its zero-carry segment
+// summary in shared memory; after a cluster barrier it reads the summaries of
+// all segments, chains them with the segment coefficients (A_seg, K_seg,
+// B_seg) into its forward carry G0, the solution value X0 after its segment
+// and the line's first value and last forward value (Sherman-Morrison
+// scalar), then runs its own chunk chain from (G0, X0).  The summary slots
+// follow the Sherman-Morrison scalars; distinct solves use distinct slots,
+// so the two exchanges of a LAST sweep never overwrite a slot still being
+// read.  Barrier protocol per thread: [wait (closes the previous exchange's
+// trailing arrive)] publish, arrive, wait, read + chain, arrive; the block's
+// last wait (after its stores) keeps its shared memory alive until every
+// block has finished reading it.
+template <typename R, typename V, int PK, int S, int KIND>
+__device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq,
+                                                   const SegCtx &sc) {
+  constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
+  constexpr int SB = 8;  // segment summaries requested per batch
+  const int nlb = A.nlb, pitch = A.pitch;
+  V *sSum = reinterpret_cast<V *>(reinterpret_cast<unsigned char *>(sSig) +
+                                  ((NQ * nlb * PK * (int)sizeof(double) + 15) & ~15));
+  // a launch whose cluster does not span the line's segments must not map
+  // ranks it does not have: it reads no remote summary (and gives wrong
+  // results, which the host never asks for)
+  const int ns = ((int)cluster_nranks() == A.nseg) ? A.nseg : 1;
+  if (q0 > 0) cluster_wait();
+  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    int ms, mg;
+    solve_matrix<R, S, KIND>(q, ms, mg);
+    V G, X;
+    segment_summary<R, V>(A.mat[ms][mg], sF + (q * nlb + l) * pitch, sY + (q * nlb + l) * pitch, sc.mv, sc.jb, G,
+                          X);
+    sSum[2 * (q * nlb + l)] = G;
+    sSum[2 * (q * nlb + l) + 1] = X;
+  }
+  cluster_arrive();
+  cluster_wait();
+  const V zero = Splat<V>::of(R(0));
+  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    int ms, mg;
+    solve_matrix<R, S, KIND>(q, ms, mg);
+    const MatTab<R> &M = A.mat[ms][mg];
+    const unsigned slot = (unsigned)__cvta_generic_to_shared(sSum + 2 * (q * nlb + l));
+    V G = zero, G0 = zero, Xf = zero, Xa = zero;
+    R pbf = R(1), pba = R(1);
+    for (int k0 = 0; k0 < ns; k0 += SB) {
+      V sg[SB], sx[SB];
+#pragma unroll
+      for (int k = 0; k < SB; ++k) {
+        sg[k] = zero;
+        sx[k] = zero;
+        if (k0 + k < ns) ld_dsmem_pair(dsmem_map(slot, (unsigned)(k0 + k)), sg[k], sx[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < SB; ++k) {
+        const int kk = k0 + k;
+        if (kk < ns) {
+          const typename V4T<R>::T c = ld_segc(M, kk);
+          if (kk == sc.seg) G0 = G;
+          const V y = vfma(Splat<V>::of(c.y), G, sx[k]);  // segment kk's first value minus B_seg X_after
+          Xf = vfma(Splat<V>::of(pbf), y, Xf);
+          pbf *= c.z;
+          if (kk > sc.seg) {
+            Xa = vfma(Splat<V>::of(pba), y, Xa);
+            pba *= c.z;
+          }
+          G = vfma(Splat<V>::of(c.x), G, sg[k]);
+        }
+      }
+    }
+    put_sigma(sSig + (q * nlb + l) * PK, M, Xf, G);  // cyclic line: y_0 = Xf, y_{p-1} = G
+    V Gd, Xd;
+    chain_line<R, V>(M, sF + (q * nlb + l) * pitch, sY + (q * nlb + l) * pitch, sc.mv, sc.jb, G0, Xa, Gd, Xd);
+  }
+  cluster_arrive();
+}
+
 // Chain the chunk summaries of solves q0..q0+nq-1 for every line (or line
 // pair) of the block.  sF/sY hold F_j / Y_j on entry and the carries G_in[j]
 // / X[j+1] on return; sSig the Sherman-Morrison scalars.  Segmented sweeps:
 // see SegCtx (segment summaries and carries are stored per line, pairs as two
 // lines).
-template <typename R, typename V, int PK, int S, int KIND>
+template <typename R, typename V, int PK, int S, int KIND, bool CL = false>
 __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq,
                                            const SegCtx &sc) {
   const int nlb = A.nlb, pitch = A.pitch;
+  if constexpr (CL) {  // cluster-segmented kernels (compiled separately)
+    scan_lines_cluster<R, V, PK, S, KIND>(A, sF, sY, sSig, q0, nq, sc);
+    return;
+  }
   if (sc.phase == SEG_WHOLE && A.mx > 32) {
     scan_lines_warp<R, V, PK>(A, sF, sY, sSig, q0, nq, [&](int q) -> const MatTab<R> & {
       int ms, mg;
@@ -919,7 +1056,7 @@ __device__ __forceinline__ void chunk_sources(const SweepArgs<R> &A, typename La
 // output field f (FIRST/MIDDLE: c_U, c_f, w; LAST: 0 = U_{n+1}).  exch is the
 // block's exchange space (chunk summaries, carries, Sherman-Morrison scalars).
 // PK = 2: every value is a float2 holding a pair of neighbouring lines.
-template <typename R, int S, int L, int KIND, int PK, typename LoadF, typename StoreF>
+template <typename R, int S, int L, int KIND, int PK, bool CL = false, typename LoadF, typename StoreF>
 __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPos<R, PK> &c, unsigned char *exch,
                                             LoadF load, StoreF store) {
   using V = typename LaneT<R, PK>::T;
@@ -1034,8 +1171,10 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(5 * s + 4, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, NQ, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
-                                                          : A.segphase == SEG_SUMMARY ? SEG_SUMMARY : SEG_SOLVE));
+    scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, 0, NQ,
+                                  scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
+                                      : A.segphase == SEG_SUMMARY                           ? SEG_SUMMARY
+                                                                                            : SEG_SOLVE));
     if (A.segphase == SEG_SUMMARY) return;  // segment summaries written
     __syncthreads();
     // pass 2: c_U <- 9 T c_U - 8 S c_U, c_f likewise, w <- P w
@@ -1097,8 +1236,10 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(s, F0, Y0);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, 0, S, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
-                                                         : A.segphase == SEG_SUMMARY ? SEG_SUMMARY : SEG_SOLVE));
+    scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, 0, S,
+                                  scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
+                                      : A.segphase == SEG_SUMMARY                           ? SEG_SUMMARY
+                                                                                            : SEG_SOLVE));
     if (A.segphase == SEG_SUMMARY) return;  // P summaries written
     __syncthreads();
 #pragma unroll
@@ -1142,8 +1283,10 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       put(S + 2 * s + 1, F1, Y1);
     }
     __syncthreads();
-    scan_lines<R, V, PK, S, KIND>(A, sF, sY, sSig, S, 2 * S, scx(A.segphase == SEG_WHOLE ? SEG_WHOLE
-                                                             : A.segphase == SEG_SOLVE ? SEG_SUMMARY : SEG_SOLVE));
+    scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, S, 2 * S,
+                                  scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
+                                      : A.segphase == SEG_SOLVE                             ? SEG_SUMMARY
+                                                                                            : SEG_SOLVE));
     if (A.segphase == SEG_SOLVE) return;  // T and S summaries written
     __syncthreads();
 #pragma unroll
@@ -1198,7 +1341,7 @@ __device__ __forceinline__ void store_pairs(const float2 (&v)[L], float2 *__rest
 // PK = 2) and, for segmented sweeps, per segment of mx chunks of those lines;
 // inputs loaded straight from global memory (vector loads on x, coalesced row
 // segments on strided axes).
-template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1>
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
                                             R exp_mt) {
   (void)t_eval;
@@ -1248,7 +1391,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     auto store = [&](int f, int s, const float2 (&v)[L]) {
       store_pairs<L>(v, reinterpret_cast<float2 *>(A.out[f] + s * N) + off0, st2, cnt);
     };
-    chunk_sweep<R, S, L, KIND, 2>(A, c, smem, load, store);
+    chunk_sweep<R, S, L, KIND, 2, CL>(A, c, smem, load, store);
   } else {
     long long base;
     bool line_ok;
@@ -1285,14 +1428,17 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     auto store = [&](int f, int s, const R (&v)[L]) {
       store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt);
     };
-    chunk_sweep<R, S, L, KIND, 1>(A, c, smem, load, store);
+    chunk_sweep<R, S, L, KIND, 1, CL>(A, c, smem, load, store);
   }
 }
 
-template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1>
+// CL: cluster-segmented (launched with nseg-block clusters, A.segphase = SEG_CLUSTER)
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) sweep_kernel(const __grid_constant__ SweepArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  sweep_block<R, S, L, CONTIG, KIND, PK>(A, blockIdx.x, smem, A.t_eval, A.exp_mtR);
+  sweep_block<R, S, L, CONTIG, KIND, PK, CL>(A, blockIdx.x, smem, A.t_eval, A.exp_mtR);
+  // the other blocks of the cluster may still read this block's summaries
+  if constexpr (CL) cluster_wait();
 }
 
 // Batched ensemble: one launch covers every instance; block b belongs to the

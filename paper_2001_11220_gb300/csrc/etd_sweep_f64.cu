@@ -5,6 +5,7 @@ namespace etd {
 
 cudaError_t launch_sweep(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                          cudaStream_t s) {
+  if (a.segphase == SEG_CLUSTER) return launch_sweep_cluster(a, nspecies, L, kind, nthreads, smem, s);
 #define CALL(S_, L_, K_) launch_one<double, S_, L_, K_>(a, nthreads, smem, s)
   ETD_DISPATCH(CALL)
 #undef CALL

@@ -57,6 +57,15 @@ inline cudaError_t persistent_grid(const void *fn, int nthreads, size_t smem, in
   return cudaSuccess;
 }
 
+template <typename R>
+inline cudaError_t launch_register(void (*fn)(const SweepArgs<R>), const SweepArgs<R> &a, int nthreads, size_t smem,
+                                   cudaStream_t s) {
+  cudaError_t e = ensure_smem((const void *)fn, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<a.nblocks, nthreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename R, int S, int L, int KIND>
 cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStream_t s) {
   constexpr bool CONTIG = (KIND == SWEEP_FIRST);
@@ -72,20 +81,10 @@ cudaError_t launch_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStr
     return cudaGetLastError();
   }
   if constexpr (sizeof(R) == 4 && !CONTIG && L == 8) {
-    if (a.pk == 2) {
-      auto fp = sweep_kernel<R, S, L, false, KIND, 2>;
-      cudaError_t e = ensure_smem((const void *)fp, smem);
-      if (e != cudaSuccess) return e;
-      fp<<<a.nblocks, nthreads, smem, s>>>(a);
-      return cudaGetLastError();
-    }
+    if (a.pk == 2) return launch_register<R>(sweep_kernel<R, S, L, false, KIND, 2>, a, nthreads, smem, s);
   }
   if (a.pk != 1) return cudaErrorInvalidValue;
-  auto fn = sweep_kernel<R, S, L, CONTIG, KIND>;
-  cudaError_t e = ensure_smem((const void *)fn, smem);
-  if (e != cudaSuccess) return e;
-  fn<<<a.nblocks, nthreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_register<R>(sweep_kernel<R, S, L, CONTIG, KIND>, a, nthreads, smem, s);
 }
 
 template <typename R, int S, int L, int KIND>

@@ -14,7 +14,8 @@
 namespace etd {
 bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, bool reg_force, int pack);
 bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk);
-bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx);
+bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster);
+bool cluster_plan_fits(const Instance &I, int a);
 etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
 }  // namespace etd
 
@@ -28,10 +29,11 @@ struct Cand {
   int pack;
   bool tile = false;  // FP32 tile kernel with nlb lines per block
   int seg = 0;        // > 0: segmented register kernel with seg chunks per segment
+  bool cluster = false;  // segmented as one cluster launch
 };
 
 bool plan_cand(Instance &I, int a, const Cand &c) {
-  if (c.seg) return plan_axis_seg(I, a, c.L, c.nlb, c.seg);
+  if (c.seg) return plan_axis_seg(I, a, c.L, c.nlb, c.seg, c.cluster) && cluster_plan_fits(I, a);
   if (c.tile) return plan_axis_tile(I, a, c.L, c.nlb, c.pack);
   return plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg, c.pack);
 }
@@ -90,12 +92,13 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
           for (int pk : {1, 2}) cands.push_back({L, nlb, false, pk, true});  // tile kernels
       if ((I.n[a] + L - 1) / L > 32)  // long lines: segmented blocks (planner checks the shape)
         for (int mx : {16, 32})
-          for (int nlb : {8, 16, 32}) cands.push_back({L, nlb, true, 1, false, mx});
+          for (int nlb : {8, 16, 32})
+            for (bool cl : {false, true}) cands.push_back({L, nlb, true, 1, false, mx, cl});
     }
     const AxisPlan keep = I.plan[a];
     double best = 1e30;
     Cand pick{keep.L, keep.sp.staged || keep.pk == 2 ? keep.nlb : 0, !keep.sp.staged, keep.pk,
-              keep.sp.staged == 2, keep.nseg > 1 ? keep.mx : 0};
+              keep.sp.staged == 2, keep.nseg > 1 ? keep.mx : 0, keep.cluster};
     if (pick.tile) pick.nlb = keep.nlb * keep.pk;
     if (pick.seg) pick.nlb = keep.nlb;
     for (const Cand &c : cands) {
@@ -108,7 +111,8 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       if (st != ETD_OK) return st;
       if (std::getenv("ETD_TUNE_VERBOSE"))
         fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d %s%s -> %.4f ms\n", a, c.L, I.plan[a].nlb,
-                I.plan[a].nseg > 1 ? "segmented" : I.plan[a].sp.staged == 2 ? "tile"
+                I.plan[a].nseg > 1 ? (I.plan[a].cluster ? "cluster-segmented" : "segmented")
+                : I.plan[a].sp.staged == 2 ? "tile"
                                                  : (I.plan[a].sp.staged ? "staged" : "register"),
                 I.plan[a].pk == 2 ? " pairs" : "", ms);
       if (ms < best) {

@@ -200,17 +200,18 @@ def test_autograd_simulate_matches_oracle_adjoint():
     assert rel(pt.grad.numpy(), dp[:2]) <= 1e-9
 
 
-def test_grad_with_segmented_forward_sweeps(monkeypatch):
+@pytest.mark.parametrize("kernel", [3, 4], ids=["segmented", "cluster"])
+def test_grad_with_segmented_forward_sweeps(kernel, monkeypatch):
     """The gradient's forward recomputation runs segmented sweeps (a long
-    periodic middle axis split over blocks): the FP64 gradient still matches
-    the oracle's."""
+    periodic middle axis split over blocks; 4: the blocks of a line group as
+    one thread-block cluster): the FP64 gradient still matches the oracle's."""
     w = case("seg_grad", (8, 300, 6), (W.NEUMANN, W.PERIODIC, W.DIRICHLET), (0.02, 0.01), "gray_scott",
              (0.04, 0.06), 0.5, ((0.8, 0.2), 0.05))
-    monkeypatch.setenv("ETD_TILES", "4:0:0:1,4:8:3:16,4:0:0:1")
+    monkeypatch.setenv("ETD_TILES", f"4:0:0:1,4:8:{kernel}:16,4:0:0:1")
     U0 = W.initial_state(w)
     target = W.initial_state(w, seed=99) * 0.9
     ctx = _ctx(w, "fp64")
-    assert ctx.info()["staged"][1] == 3
+    assert ctx.info()["staged"][1] == kernel
     loss, dU0, dD, dp = ctx.grad(torch.tensor(U0, device="cuda"), 0.0, torch.tensor(target, device="cuda"), 3, 2)
     rloss, rdU0, rdD, rdp = oracle.grad(oracle_problem(w), U0, 0.0, target, 3)
     ctx.close()

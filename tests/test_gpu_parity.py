@@ -373,7 +373,7 @@ SEG_CASES = [
 
 
 def seg_tiles(spec, L):
-    return ",".join(x.format(L=L) for x in spec)
+    return ",".join(x.format(L=L, M=128 // L) for x in spec)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -396,6 +396,54 @@ def test_segmented_sweeps_vs_oracle(w, spec, prec, monkeypatch):
     e1 = rel_err(one, oracle_run(w, U0, 1, t0=0.3))
     e3 = rel_err(three, oracle_run(w, U0, 3, t0=0.3))
     print(f"{w.name} {prec} segmented: 1 step {e1:.3e}, 3 steps {e3:.3e}")
+    if prec == "fp64":
+        assert e1 <= FP64_TOL and e3 <= FP64_TOL, (e1, e3)
+    else:
+        assert e1 <= FP32_STEP_TOL and e3 <= 3 * FP32_STEP_TOL, (e1, e3)
+
+
+# Cluster-segmented sweeps ("L:lines:4:chunks per segment"): the segments of a
+# line group run as one thread-block cluster (2 to 16 blocks, 9 and more on
+# the non-portable cluster size) and exchange their summaries through
+# distributed shared memory in a single launch per sweep
+CLUSTER_CASES = [
+    (case("clu_per_y", (6, 1100), (W.NEUMANN, W.PERIODIC), (0.5, 2.0), "schnakenberg", (0.1, 0.9, 10.0), k=0.01,
+          ic="uniform", ic_args=((1.0, 0.9), 1e-2)), ["{L}:0:0:1", "{L}:8:4:32"]),
+    (case("clu_per_x", (1301, 7), (W.PERIODIC, W.DIRICHLET), (0.5, 2.0), "gray_scott", (0.04, 0.06), k=0.01),
+     ["{L}:8:4:32", "{L}:0:0:1"]),
+    (case("clu_neu_dir_ragged", (517, 301), (W.NEUMANN, W.DIRICHLET), (0.5, 0.1), "brusselator", (1.0, 3.4)),
+     ["{L}:8:4:16", "{L}:16:4:8"]),
+    (case("clu_16_blocks", (2048, 5), (W.PERIODIC, W.NEUMANN), (0.5, 2.0), "schnakenberg", (0.1, 0.9, 10.0),
+          k=0.01, ic="uniform", ic_args=((1.0, 0.9), 1e-2)), ["{L}:8:4:{M}", "{L}:0:0:1"]),
+    (case("clu_3d_middle", (8, 300, 6), (W.NEUMANN, W.PERIODIC, W.DIRICHLET), (0.02, 0.01), "gray_scott",
+          (0.04, 0.06), k=0.5), ["{L}:0:0:1", "{L}:8:4:16", "{L}:0:0:1"]),
+    (case("clu_3d_last_src", (12, 10, 270), W.DIRICHLET, (1.0,), "enzyme", (1.0, 1.0), k=1 / 17, ic="sine"),
+     ["{L}:0:0:1", "{L}:0:0:1", "{L}:4:4:16"]),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("w,spec", CLUSTER_CASES, ids=[c[0].name for c in CLUSTER_CASES])
+def test_cluster_segmented_sweeps_vs_oracle(w, spec, prec, monkeypatch):
+    L = 4 if prec == "fp64" else 8
+    monkeypatch.setenv("ETD_TILES", seg_tiles(spec, L))
+    ctx = _api().from_workload(w, prec)
+    inf = ctx.info()
+    seg_axes = [a for a, x in enumerate(spec) if ":4:" in x]
+    assert all(inf["staged"][a] == 4 for a in seg_axes), inf
+    assert inf["launches_per_step"] == w.dim, inf  # one launch per sweep
+    U0 = W.initial_state(w)
+    U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+    ctx.run(U, 0.3, 1)
+    torch.cuda.synchronize()
+    one = U.double().cpu().numpy()
+    ctx.run(U, 0.3 + w.k, 2)
+    torch.cuda.synchronize()
+    three = U.double().cpu().numpy()
+    ctx.close()
+    e1 = rel_err(one, oracle_run(w, U0, 1, t0=0.3))
+    e3 = rel_err(three, oracle_run(w, U0, 3, t0=0.3))
+    print(f"{w.name} {prec} cluster-segmented ({seg_tiles(spec, L)}): 1 step {e1:.3e}, 3 steps {e3:.3e}")
     if prec == "fp64":
         assert e1 <= FP64_TOL and e3 <= FP64_TOL, (e1, e3)
     else:
