@@ -1121,10 +1121,17 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
   // solve q -> (species, matrix): FIRST/MIDDLE: q = 5s + {0: T.cU, 1: S.cU, 2: T.cf, 3: S.cf, 4: P.w}
   //                               LAST: q = s (P.w), S + 2s (T.f1), S + 2s + 1 (S.f2)
   if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
-    V cu[S][L], cf[S][L], w[S][L];
+    // FIRST keeps U_n and F(U_n) and forms w = U_n + k F(U_n) where a solve
+    // reads it (one FMA per value instead of S*L live registers)
+    constexpr bool WREG = (KIND == SWEEP_MIDDLE);
+    V cu[S][L], cf[S][L], w[WREG ? S : 1][L];
+    const V kk = Splat<V>::of(A.kR);
+    auto wfirst = [&](int s, V (&o)[L]) {
+#pragma unroll
+      for (int t = 0; t < L; ++t) o[t] = vfma(kk, cf[s][t], cu[s][t]);
+    };
     if constexpr (KIND == SWEEP_FIRST) {
-      // U_n, F(U_n, t_n), w* = U_n + k F(U_n)
-      const V kk = Splat<V>::of(A.kR);
+      // U_n, F(U_n, t_n)
 #pragma unroll
       for (int s = 0; s < S; ++s) load(0, s, cu[s]);
       V src[L];
@@ -1145,10 +1152,6 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
           for (int t = 0; t < L; ++t)
             if (t >= cnt) cf[s][t] = zero;
       }
-#pragma unroll
-      for (int s = 0; s < S; ++s)
-#pragma unroll
-        for (int t = 0; t < L; ++t) w[s][t] = vfma(kk, cf[s][t], cu[s][t]);
     } else {
 #pragma unroll
       for (int s = 0; s < S; ++s) {
@@ -1167,7 +1170,13 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
       p1x2(A.mat[s][2], cu[s], cf[s], F0, Y0, F1, Y1);
       put(5 * s + 1, F0, Y0);
       put(5 * s + 3, F1, Y1);
-      p1(A.mat[s][0], w[s], F0, Y0);
+      if constexpr (WREG) {
+        p1(A.mat[s][0], w[s], F0, Y0);
+      } else {
+        V wt[L];
+        wfirst(s, wt);
+        p1(A.mat[s][0], wt, F0, Y0);
+      }
       put(5 * s + 4, F0, Y0);
     }
     __syncthreads();
@@ -1177,10 +1186,20 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
                                                                                             : SEG_SOLVE));
     if (A.segphase == SEG_SUMMARY) return;  // segment summaries written
     __syncthreads();
-    // pass 2: c_U <- 9 T c_U - 8 S c_U, c_f likewise, w <- P w
+    // pass 2: w <- P w (first: FIRST forms w from c_U, c_f before they are
+    // overwritten), c_U <- 9 T c_U - 8 S c_U, c_f likewise
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if constexpr (sizeof(R) == 4) {
+        if constexpr (WREG) {
+          pass2v<V, L>(A.mat[s][0], m, jt, w[s], carry(5 * s + 4), w[s], [&](int t, V x) { w[s][t] = x; });
+          store(2, s, w[s]);
+        } else {
+          V wt[L];
+          wfirst(s, wt);
+          pass2v<V, L>(A.mat[s][0], m, jt, wt, carry(5 * s + 4), wt, [&](int t, V x) { wt[t] = x; });
+          store(2, s, wt);
+        }
         // T on (c_U, c_f) into (xa, xc); S on (c_U, c_f) in place, folded into 9 T - 8 S
         V xa[L], xc[L];
         pass2x2v<V, L, true>(A.mat[s][1], A.mat[s][1], m, jt, cu[s], cf[s], carry(5 * s + 0), carry(5 * s + 2), xa,
@@ -1195,10 +1214,16 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
                              });
         store(0, s, xa);
         store(1, s, xc);
-        pass2v<V, L>(A.mat[s][0], m, jt, w[s], carry(5 * s + 4), w[s], [&](int t, V x) { w[s][t] = x; });
-        store(2, s, w[s]);
       } else {
         V xa[L], xb[L], G, X, sg;
+        carries(5 * s + 4, G, X, sg);
+        if constexpr (WREG) {
+          pass2<R, L>(A.mat[s][0], m, jt, w[s], G, X, sg, xa);
+        } else {
+          wfirst(s, xb);
+          pass2<R, L>(A.mat[s][0], m, jt, xb, G, X, sg, xa);
+        }
+        store(2, s, xa);
         carries(5 * s + 0, G, X, sg);
         pass2<R, L>(A.mat[s][1], m, jt, cu[s], G, X, sg, xa);
         carries(5 * s + 1, G, X, sg);
@@ -1213,22 +1238,14 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
 #pragma unroll
         for (int t = 0; t < L; ++t) xa[t] = vfma(k9, xa[t], vmul(km8, xb[t]));
         store(1, s, xa);
-        carries(5 * s + 4, G, X, sg);
-        pass2<R, L>(A.mat[s][0], m, jt, w[s], G, X, sg, xa);
-        store(2, s, xa);
       }
     }
   } else {
     // LAST: phase A  U* = P_d w ; phase B  U_{n+1} = T_d f1 - S_d f2
+    // c_U and c_f are read once U* is known (fewer live registers in phase A)
     V cu[S][L], cf[S][L], w[S][L];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      if (A.segphase != SEG_SUMMARY) {  // the P summaries need w only
-        load(0, s, cu[s]);
-        load(1, s, cf[s]);
-      }
-      load(2, s, w[s]);
-    }
+    for (int s = 0; s < S; ++s) load(2, s, w[s]);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       V F0, Y0;
@@ -1253,6 +1270,11 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
 #pragma unroll
         for (int t = 0; t < L; ++t) w[s][t] = x[t];  // w now holds U*
       }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      load(0, s, cu[s]);
+      load(1, s, cf[s]);
     }
     // F(U*, t_{n+1}); f1, f2 overwrite c_U, c_f
     const R k = A.kR;
