@@ -177,9 +177,40 @@ __device__ __forceinline__ R line_source_base(const SweepArgs<R> &A, bool contig
 
 // ------------------------------------------------------------ chunk loads
 
+// 32-byte global accesses (sm_100+): one instruction moves a whole sector per
+// thread, so a warp's chunk loads and stores on contiguous lines fill every
+// sector they touch (16-byte accesses leave each sector half written per
+// instruction); the address must be 32-byte aligned
+__device__ __forceinline__ void ld32B(const float *p, float *v) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ld32B(const double *p, double *v) {
+  asm volatile("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];\n"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p));
+}
+__device__ __forceinline__ void st32B(float *p, const float *v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void st32B(double *p, const double *v) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+
 template <typename R, int L, bool CONTIG>
 __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, long long off, long long st,
                                            int cnt) {
+  if constexpr (CONTIG && L % (32 / sizeof(R)) == 0) {
+    if (cnt == L && ((reinterpret_cast<uintptr_t>(p + off) & 31) == 0)) {
+#pragma unroll
+      for (int t = 0; t < L; t += 32 / sizeof(R)) ld32B(p + off + t, v + t);
+      return;
+    }
+  }
   if constexpr (CONTIG) {
     constexpr int VW = 16 / sizeof(R);
     if (L % VW == 0 && cnt == L && ((reinterpret_cast<uintptr_t>(p + off) & 15) == 0)) {
@@ -220,6 +251,13 @@ __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, l
 template <typename R, int L, bool CONTIG>
 __device__ __forceinline__ void store_chunk(const R (&v)[L], R *__restrict__ p, long long off, long long st,
                                             int cnt) {
+  if constexpr (CONTIG && L % (32 / sizeof(R)) == 0) {
+    if (cnt == L && ((reinterpret_cast<uintptr_t>(p + off) & 31) == 0)) {
+#pragma unroll
+      for (int t = 0; t < L; t += 32 / sizeof(R)) st32B(p + off + t, v + t);
+      return;
+    }
+  }
   if constexpr (CONTIG) {
     constexpr int VW = 16 / sizeof(R);
     if (L % VW == 0 && cnt == L && ((reinterpret_cast<uintptr_t>(p + off) & 15) == 0)) {

@@ -110,7 +110,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       st = time_axis(ctx, I, a, U_work, 5, ms);
       if (st != ETD_OK) return st;
       if (std::getenv("ETD_TUNE_VERBOSE"))
-        fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d %s%s -> %.4f ms\n", a, c.L, I.plan[a].nlb,
+        fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d mx=%d %s%s -> %.4f ms\n", a, c.L, I.plan[a].nlb, I.plan[a].mx,
                 I.plan[a].nseg > 1 ? (I.plan[a].cluster ? "cluster-segmented" : "segmented")
                 : I.plan[a].sp.staged == 2 ? "tile"
                                                  : (I.plan[a].sp.staged ? "staged" : "register"),
