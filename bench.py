@@ -52,7 +52,7 @@ def _peaks():
 # sources that compile into the forward sweep kernels (their DRAM traffic
 # depends on nothing else but the tile shapes, recorded beside each entry)
 SWEEP_SOURCES = ("etd_internal.h", "etd_tables.h", "etd_sweep.cuh", "etd_sweep_smem.cuh", "etd_sweep_launch.cuh",
-                 "etd_sweep_f32.cu", "etd_sweep_f64.cu")
+                 "etd_sweep_f32.cu", "etd_sweep_f64.cu", "etd_sweep_cluster.cu")
 
 
 def _csrc_hash() -> str:
@@ -65,9 +65,9 @@ def _csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, workload: str, tiles: str):
+def _traffic(kernel: str, workload: str, tile: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel sources or the tile shapes changed since it was captured."""
+    kernel sources or that sweep's tile shape changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -75,7 +75,7 @@ def _traffic(kernel: str, workload: str, tiles: str):
     except Exception:
         return None
     ent = tab.get(workload, {}).get(kernel)
-    if not ent or ent.get("csrc_hash") != _csrc_hash() or ent.get("tiles") != tiles:
+    if not ent or ent.get("csrc_hash") != _csrc_hash() or ent.get("tile") != tile:
         return None
     return float(ent["dram_bytes_per_launch"])
 
@@ -237,10 +237,27 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
     c, U = mk(w, "fp32")
     ms = _timed(lambda: c.run(U, 0.0, 20), stream)
     inf = c.info()
+    tiles = [f"{inf['chunk'][a]}:{inf['lines_per_block'][a]}:{inf['staged'][a]}:{inf['pack'][a]}" for a in range(2)]
+    # per-sweep device times (CUDA events around each sweep, a separate run) against the HBM peak
+    c.profile(True)
+    c.profile_read()
+    c.run(U, 0.0, 20)
+    torch.cuda.synchronize()
+    sweep_ms, sweep_n = c.profile_read()
+    c.profile(False)
+    peak, _ = _peaks()
+    fld = w.nspecies * w.npoints * 4
+    per_sweep = {}
+    for name, kind, a in (("sweep_first_x", 0, 0), ("sweep_last_y", 2, 1)):
+        t = sweep_ms[kind] / max(1, sweep_n[kind]) / 1e3
+        per_sweep[name] = {"ms": t * 1e3, "achieved_gbs": 4 * fld / t / 1e9, "frac": 4 * fld / t / 1e9 / peak,
+                           "traffic": _traffic(name, "schnakenberg2d_4096_fp32", tiles[a])}
     out["schnakenberg2d_4096_fp32"] = {"value": w.npoints * w.nspecies * 20 / (ms / 1e3), "unit": UNIT,
-                                       "ms_per_step": ms / 20,
-                                       "tiles": ",".join(f"{inf['chunk'][a]}:{inf['lines_per_block'][a]}:"
-                                                         f"{inf['staged'][a]}:{inf['pack'][a]}" for a in range(2))}
+                                       "ms_per_step": ms / 20, "tiles": ",".join(tiles),
+                                       "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak,
+                                                    "step_frac": inf["algorithmic_bytes"] / (ms / 20 / 1e3) / 1e9 / peak,
+                                                    "algorithmic_bytes_per_step": inf["algorithmic_bytes"],
+                                                    "per_sweep": per_sweep}}
     c.close()
     del U
     # batched ensemble: 512 Brusselator instances 64^2 .. 512^2, FP32, one launch per sweep
@@ -393,7 +410,7 @@ def main():
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_src = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(kinds[dom], f"mms3d_{P_BENCH}_{args.precision}", tiles),
+            "traffic": _traffic(kinds[dom], f"mms3d_{P_BENCH}_{args.precision}", tiles.split(",")[dom]),
             "kernel": kinds[dom], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": alg_bytes,
             "per_sweep_ms": {kinds[i]: sweep_ms[i] / max(1, sweep_launches[i]) for i in range(3)},
