@@ -774,6 +774,8 @@ etd_status etd_run_host(etd_ctx *ctx, void *U_host, double t0, int64_t nsteps) {
   if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_run_host on a batched context");
   if (!U_host) return fail(ctx, ETD_ERR_INVALID_ARG, "U_host is NULL");
+  if (nsteps < 0) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0");
+  if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
   const Instance &I = ctx->inst[0];
   const size_t bytes = (size_t)I.S * I.N * I.real_bytes;
   if (!ctx->host_state) {

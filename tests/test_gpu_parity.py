@@ -181,6 +181,26 @@ def test_run_host_matches_device_run():
     ctx.close()
 
 
+@pytest.mark.parametrize("prec,steps,pinned", [("fp32", 1, True), ("fp32", 2, True), ("fp64", 3, False),
+                                               ("fp32", 1, False)])
+def test_run_host_direct_and_copied(prec, steps, pinned):
+    """etd_run_host on pinned and pageable host buffers, one and several
+    steps, FP32 and FP64: bit-identical to the same run on a device state."""
+    w = W.gray_scott_3d(24, steps=steps)
+    U0 = W.initial_state(w)
+    EtdRdpIf = _api()
+    ctx = EtdRdpIf.from_workload(w, prec)
+    U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+    ctx.run(U, 0.25, steps)
+    H = torch.tensor(U0, dtype=ctx.dtype)
+    if pinned:
+        H = H.pin_memory()
+    ctx.run_host(H, 0.25, steps)
+    torch.cuda.synchronize()
+    assert torch.equal(U.cpu(), H)
+    ctx.close()
+
+
 def test_graph_replay_matches_direct_launches():
     w = W.brusselator_2d(p=48, steps=9)
     U0 = W.initial_state(w)
