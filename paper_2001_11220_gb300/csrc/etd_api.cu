@@ -320,7 +320,7 @@ bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster) {
   P.nblocks = (int)(line_blocks * P.nseg);
   P.nthreads = nlb * mx;
   P.cluster = cluster;
-  P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1, cluster);
+  P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1, cluster, P.nseg);
   return P.smem <= 200 * 1024;
 }
 

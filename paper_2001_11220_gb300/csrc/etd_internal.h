@@ -201,15 +201,24 @@ inline int exchange_pitch(int m) { return ((m + 7) & ~7) + 1; }
 
 // shared-memory bytes of one sweep block (pk = 2: nlb line pairs); the
 // Sherman-Morrison scalars take 8 bytes each (stored in the sweep's precision)
+// chunk-table cache of a cluster-segmented sweep block: the chunk entries
+// (A_j, kappa_j, B_j) of its chunks for the 3 matrices of every species
+// (pitch - 1 entries each, the padded chunk count) and the nseg segment
+// entries of each matrix
+inline size_t chunk_cache_bytes(int nspecies, int pitch, size_t real_bytes, int nseg = 0) {
+  return (size_t)3 * nspecies * ((size_t)(pitch - 1) + (size_t)nseg) * 4 * real_bytes;
+}
+
 // cluster-segmented sweeps add the segment summaries (G, X) of every
 // (solve, line unit), read by the other blocks of the cluster
 inline size_t sweep_smem_bytes(int kind, int nspecies, int nlb, int pitch, size_t real_bytes, int pk = 1,
-                               bool cluster = false) {
+                               bool cluster = false, int nseg = 1) {
   int nq = (kind == SWEEP_LAST) ? 3 * nspecies : 5 * nspecies;
   size_t sums = (size_t)2 * nq * nlb * pitch * real_bytes * pk;
   sums = (sums + 15) & ~(size_t)15;
   size_t sig = ((size_t)nq * nlb * pk * sizeof(double) + 15) & ~(size_t)15;
-  return sums + sig + (cluster ? (size_t)2 * nq * nlb * pk * real_bytes : 0);
+  size_t seg = cluster ? (((size_t)2 * nq * nlb * pk * real_bytes + 15) & ~(size_t)15) : 0;
+  return sums + sig + seg + (cluster ? chunk_cache_bytes(nspecies, pitch, real_bytes, nseg) : 0);
 }
 
 }  // namespace etd

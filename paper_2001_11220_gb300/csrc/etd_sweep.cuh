@@ -621,6 +621,28 @@ __device__ __forceinline__ double4 ld_chunk(const MatTab<double> &M, int j) {
   return make_double4(a.x, a.y, b.x, b.y);
 }
 
+// Chunk-table cache in shared memory (entries of the block's chunks, filled
+// at the start of the sweep; see chunk_sweep)
+__device__ __forceinline__ float4 ld_cc(const float4 *p, int j) { return p[j]; }
+__device__ __forceinline__ double4 ld_cc(const double4 *p, int j) {
+  const double2 *q = reinterpret_cast<const double2 *>(p + j);
+  const double2 a = q[0], b = q[1];
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_cc(float4 *p, int j, float4 v) { p[j] = v; }
+__device__ __forceinline__ void st_cc(double4 *p, int j, double4 v) {
+  double2 *q = reinterpret_cast<double2 *>(p + j);
+  q[0] = make_double2(v.x, v.y);
+  q[1] = make_double2(v.z, v.w);
+}
+
+// chunk entry jb + j of M: from the block's cache cc (entry j) when there is one
+template <typename R>
+__device__ __forceinline__ typename V4T<R>::T chunk_at(const MatTab<R> &M, int jb,
+                                                      const typename V4T<R>::T *cc, int j) {
+  return cc ? ld_cc(cc, j) : ld_chunk(M, jb + j);
+}
+
 // Sequential carry chain of one (line, solve) over m chunks (chunk-table
 // entries jb .. jb+m-1): F[j] (chunk summary) becomes the forward carry
 // G_in[j], Y[j] the backward carry X[j+1], starting from the forward carry G0
@@ -707,6 +729,53 @@ __device__ __forceinline__ void solve_matrix(int q, int &s, int &g) {
   }
 }
 
+
+// chain_line reading the chunk entries from the block's cache cc (entry j = chunk jb + j)
+template <typename R, typename V>
+__device__ __forceinline__ void chain_line_cc(const MatTab<R> &M, V *F, V *Y, int m, int jb, V G0, V X0, V &Gout,
+                                           V &Xout, const typename V4T<R>::T *cc) {
+  constexpr int SB = 8;
+  const int nb = (m + SB - 1) / SB;
+  V G = G0, Gl = G0;
+  for (int b = 0; b < nb; ++b) {
+    const int j0 = b * SB;
+    V f[SB];
+    R a[SB];
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      f[k] = F[j0 + k];
+      a[k] = chunk_at(M, jb, cc, j0 + k).x;
+    }
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      F[j0 + k] = G;
+      G = vfma(Splat<V>::of(a[k]), G, f[k]);
+      Gl = (j0 + k == m - 1) ? G : Gl;
+    }
+  }
+  V X = X0;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int j0 = b * SB;
+    V gi[SB], yv[SB];
+    R cy[SB], cz[SB];
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      const typename V4T<R>::T c = chunk_at(M, jb, cc, j0 + k);
+      gi[k] = F[j0 + k];
+      yv[k] = Y[j0 + k];
+      cy[k] = c.y;
+      cz[k] = c.z;
+    }
+#pragma unroll
+    for (int k = SB - 1; k >= 0; --k) {
+      const V y = vfma(Splat<V>::of(cy[k]), gi[k], yv[k]);
+      Y[j0 + k] = X;
+      X = (j0 + k < m) ? vfma(Splat<V>::of(cz[k]), X, y) : X;
+    }
+  }
+  Gout = Gl;
+  Xout = X;
+}
 
 // Long lines (m > 32 chunks): one warp per (line, solve).  Each lane composes
 // the affine chunk maps of a contiguous block of chunks, a shuffle scan over
@@ -796,6 +865,22 @@ struct SegCtx {
 
 __device__ __forceinline__ SegCtx whole_lines(int m) { return SegCtx{SEG_WHOLE, 0, 0, m, 0, 0}; }
 
+// Chunk-table cache of a cluster-segmented block (see chunk_sweep): matrix
+// (s, g) holds the chunk entries jb .. jb + cpitch - 1 at (3 s + g) * cpitch,
+// followed by every matrix's nseg segment entries at 3 S cpitch + (3 s + g) nseg.
+template <typename R, int S, int KIND>
+__device__ __forceinline__ const typename V4T<R>::T *chunk_cache(const void *cache, int cpitch, int q) {
+  int ms, mg;
+  solve_matrix<R, S, KIND>(q, ms, mg);
+  return reinterpret_cast<const typename V4T<R>::T *>(cache) + (3 * ms + mg) * cpitch;
+}
+template <typename R, int S, int KIND>
+__device__ __forceinline__ const typename V4T<R>::T *segment_cache(const void *cache, int cpitch, int nseg, int q) {
+  int ms, mg;
+  solve_matrix<R, S, KIND>(q, ms, mg);
+  return reinterpret_cast<const typename V4T<R>::T *>(cache) + 3 * S * cpitch + (3 * ms + mg) * nseg;
+}
+
 // ---- thread-block clusters (cluster-segmented sweeps)
 // Split cluster barrier: arrive publishes this thread's shared-memory writes
 // (release), wait returns once every thread of the cluster has arrived
@@ -830,18 +915,33 @@ __device__ __forceinline__ void ld_dsmem_pair(unsigned a, float2 &g, float2 &x) 
 // F/Y: the forward value after the segment, G = sum_j (prod_{i>j} A_i) F_j,
 // and the solution value at its first position with zero carries,
 // X = sum_j (prod_{i<j} B_i) (Y_j + kappa_j G_in[j]) (chunk maps of the
-// segment: forward G -> A G + F, backward X -> B X + Y + kappa G_in).
+// segment: forward G -> A G + F, backward X -> B X + Y + kappa G_in).  The
+// loads of each batch of SB chunks are issued before its dependent FMAs
+// (chunk tables and the exchange rows are padded to a multiple of 8).
 template <typename R, typename V>
 __device__ __forceinline__ void segment_summary(const MatTab<R> &M, const V *F, const V *Y, int m, int jb, V &Gout,
-                                                V &Xout) {
+                                                V &Xout, const typename V4T<R>::T *cc = nullptr) {
+  constexpr int SB = 4;
   V G = Splat<V>::of(R(0)), X = G;
   R pb = R(1);
-  for (int j = 0; j < m; ++j) {
-    const typename V4T<R>::T c = ld_chunk(M, jb + j);
-    const V y = vfma(Splat<V>::of(c.y), G, Y[j]);
-    X = vfma(Splat<V>::of(pb), y, X);
-    pb *= c.z;
-    G = vfma(Splat<V>::of(c.x), G, F[j]);
+  for (int j0 = 0; j0 < m; j0 += SB) {
+    typename V4T<R>::T c[SB];
+    V f[SB], y[SB];
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      c[k] = chunk_at(M, jb, cc, j0 + k);
+      f[k] = F[j0 + k];
+      y[k] = Y[j0 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < SB; ++k) {
+      if (j0 + k < m) {
+        const V yy = vfma(Splat<V>::of(c[k].y), G, y[k]);
+        X = vfma(Splat<V>::of(pb), yy, X);
+        pb *= c[k].z;
+        G = vfma(Splat<V>::of(c[k].x), G, f[k]);
+      }
+    }
   }
   Gout = G;
   Xout = X;
@@ -863,7 +963,8 @@ __device__ __forceinline__ void segment_summary(const MatTab<R> &M, const V *F, 
 // block has finished reading it.
 template <typename R, typename V, int PK, int S, int KIND>
 __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq,
-                                                   const SegCtx &sc) {
+                                                   const SegCtx &sc, const void *cache) {
+  const int cpitch = A.pitch - 1;
   constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
   constexpr int SB = 8;  // segment summaries requested per batch
   const int nlb = A.nlb, pitch = A.pitch;
@@ -881,7 +982,7 @@ __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF,
     solve_matrix<R, S, KIND>(q, ms, mg);
     V G, X;
     segment_summary<R, V>(A.mat[ms][mg], sF + (q * nlb + l) * pitch, sY + (q * nlb + l) * pitch, sc.mv, sc.jb, G,
-                          X);
+                          X, chunk_cache<R, S, KIND>(cache, cpitch, q));
     sSum[2 * (q * nlb + l)] = G;
     sSum[2 * (q * nlb + l) + 1] = X;
   }
@@ -894,6 +995,7 @@ __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF,
     int ms, mg;
     solve_matrix<R, S, KIND>(q, ms, mg);
     const MatTab<R> &M = A.mat[ms][mg];
+    const typename V4T<R>::T *sgc = segment_cache<R, S, KIND>(cache, cpitch, A.nseg, q);
     const unsigned slot = (unsigned)__cvta_generic_to_shared(sSum + 2 * (q * nlb + l));
     V G = zero, G0 = zero, Xf = zero, Xa = zero;
     R pbf = R(1), pba = R(1);
@@ -909,7 +1011,7 @@ __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF,
       for (int k = 0; k < SB; ++k) {
         const int kk = k0 + k;
         if (kk < ns) {
-          const typename V4T<R>::T c = ld_segc(M, kk);
+          const typename V4T<R>::T c = ld_cc(sgc, kk);
           if (kk == sc.seg) G0 = G;
           const V y = vfma(Splat<V>::of(c.y), G, sx[k]);  // segment kk's first value minus B_seg X_after
           Xf = vfma(Splat<V>::of(pbf), y, Xf);
@@ -924,7 +1026,8 @@ __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF,
     }
     put_sigma(sSig + (q * nlb + l) * PK, M, Xf, G);  // cyclic line: y_0 = Xf, y_{p-1} = G
     V Gd, Xd;
-    chain_line<R, V>(M, sF + (q * nlb + l) * pitch, sY + (q * nlb + l) * pitch, sc.mv, sc.jb, G0, Xa, Gd, Xd);
+    chain_line_cc<R, V>(M, sF + (q * nlb + l) * pitch, sY + (q * nlb + l) * pitch, sc.mv, sc.jb, G0, Xa, Gd, Xd,
+                        chunk_cache<R, S, KIND>(cache, cpitch, q));
   }
   cluster_arrive();
 }
@@ -936,10 +1039,10 @@ __device__ __forceinline__ void scan_lines_cluster(const SweepArgs<R> &A, V *sF,
 // lines).
 template <typename R, typename V, int PK, int S, int KIND, bool CL = false>
 __device__ __forceinline__ void scan_lines(const SweepArgs<R> &A, V *sF, V *sY, R *sSig, int q0, int nq,
-                                           const SegCtx &sc) {
+                                           const SegCtx &sc, const void *cache = nullptr) {
   const int nlb = A.nlb, pitch = A.pitch;
   if constexpr (CL) {  // cluster-segmented kernels (compiled separately)
-    scan_lines_cluster<R, V, PK, S, KIND>(A, sF, sY, sSig, q0, nq, sc);
+    scan_lines_cluster<R, V, PK, S, KIND>(A, sF, sY, sSig, q0, nq, sc, cache);
     return;
   }
   if (sc.phase == SEG_WHOLE && A.mx > 32) {
@@ -1130,6 +1233,34 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
   V *sF = reinterpret_cast<V *>(exch);
   V *sY = sF + NQ * nlb * pitch;
   R *sSig = reinterpret_cast<R *>(exch + ((2 * NQ * nlb * pitch * (int)sizeof(V) + 15) & ~15));
+  // Chunk-table cache (cluster-segmented sweeps): the chunk entries of this
+  // block's chunks (jb .. jb + pitch - 2) of the 3 matrices of every species
+  // and every matrix's segment entries, copied once at the start so that the
+  // serial chains of the segment exchange read shared memory instead of
+  // waiting on the global tables (blocks of other segments ran on the SM
+  // before, so those entries are rarely in L1).  It follows the
+  // Sherman-Morrison scalars and the cluster summaries, as sized by
+  // sweep_smem_bytes.  Whole-line sweeps keep reading the global tables (their
+  // chains are short and the copy cost more than it saved).
+  using C4 = typename V4T<R>::T;
+  auto cache_base = [&]() {  // recomputed where needed (keeps no pointer live across the sweep)
+    return reinterpret_cast<C4 *>(reinterpret_cast<unsigned char *>(sSig) +
+                                  ((NQ * nlb * PK * (int)sizeof(double) + 15) & ~15) +
+                                  (CL ? ((2 * NQ * nlb * (int)sizeof(V) + 15) & ~15) : 0));
+  };
+  if constexpr (CL) {
+    C4 *cch = cache_base();
+    const int cpitch = pitch - 1;
+    for (int idx = threadIdx.x; idx < 3 * S * cpitch; idx += blockDim.x) {
+      const int mi = idx / cpitch;
+      st_cc(cch, idx, ld_chunk(A.mat[mi / 3][mi % 3], c.sc.jb + (idx - mi * cpitch)));
+    }
+    C4 *csg = cch + 3 * S * cpitch;
+    for (int idx = threadIdx.x; idx < 3 * S * A.nseg; idx += blockDim.x) {
+      const int mi = idx / A.nseg;
+      st_cc(csg, idx, ld_segc(A.mat[mi / 3][mi % 3], idx - mi * A.nseg));
+    }
+  }
   const int myidx = l * pitch + j;
   const int qstride = nlb * pitch;
   auto put = [&](int q, V F, V Y) {
@@ -1221,7 +1352,8 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, 0, NQ,
                                   scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
                                       : A.segphase == SEG_SUMMARY                           ? SEG_SUMMARY
-                                                                                            : SEG_SOLVE));
+                                                                                            : SEG_SOLVE),
+                                  CL ? (const void *)cache_base() : nullptr);
     if (A.segphase == SEG_SUMMARY) return;  // segment summaries written
     __syncthreads();
     // pass 2: w <- P w (first: FIRST forms w from c_U, c_f before they are
@@ -1294,7 +1426,8 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, 0, S,
                                   scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
                                       : A.segphase == SEG_SUMMARY                           ? SEG_SUMMARY
-                                                                                            : SEG_SOLVE));
+                                                                                            : SEG_SOLVE),
+                                  CL ? (const void *)cache_base() : nullptr);
     if (A.segphase == SEG_SUMMARY) return;  // P summaries written
     __syncthreads();
 #pragma unroll
@@ -1346,7 +1479,8 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
     scan_lines<R, V, PK, S, KIND, CL>(A, sF, sY, sSig, S, 2 * S,
                                   scx(A.segphase == SEG_WHOLE || A.segphase == SEG_CLUSTER ? A.segphase
                                       : A.segphase == SEG_SOLVE                             ? SEG_SUMMARY
-                                                                                            : SEG_SOLVE));
+                                                                                            : SEG_SOLVE),
+                                  CL ? (const void *)cache_base() : nullptr);
     if (A.segphase == SEG_SOLVE) return;  // T and S summaries written
     __syncthreads();
 #pragma unroll
