@@ -954,8 +954,9 @@ __device__ __forceinline__ void segment_summary(const MatTab<R> &M, const V *F, 
 // all segments, chains them with the segment coefficients (A_seg, K_seg,
 // B_seg) into its forward carry G0, the solution value X0 after its segment
 // and the line's first value and last forward value (Sherman-Morrison
-// scalar), then runs its own chunk chain from (G0, X0).  The summary slots
-// follow the Sherman-Morrison scalars; distinct solves use distinct slots,
+// scalar), then runs its own chunk chain from (G0, X0).  Chunk and segment
+// entries come from the block's table cache (see chunk_sweep).  The summary
+// slots follow the Sherman-Morrison scalars; distinct solves use distinct slots,
 // so the two exchanges of a LAST sweep never overwrite a slot still being
 // read.  Barrier protocol per thread: [wait (closes the previous exchange's
 // trailing arrive)] publish, arrive, wait, read + chain, arrive; the block's
