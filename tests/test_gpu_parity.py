@@ -167,6 +167,29 @@ def test_schnakenberg_4096_one_step_fp32():
     assert e32 <= FP32_STEP_TOL
 
 
+@pytest.mark.parametrize("name", ["mms3d_256", "schnakenberg2d_4096"])
+def test_full_size_in_the_benchmark_configuration(name):
+    """The benchmark workloads at full size in the launch configuration the
+    benchmark times: tile shapes autotuned on a scratch state exactly as
+    bench.py does (on 4096^2 this picks the cluster-segmented sweeps), then
+    one FP32 step from the same state against the FP64 oracle."""
+    w = W.mms_3d(256) if name == "mms3d_256" else W.schnakenberg_2d(4096)
+    U0 = W.initial_state(w)
+    ctx = _api().from_workload(w, "fp32")
+    U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+    ctx.autotune(U.clone())
+    inf = ctx.info()
+    ctx.run(U, 0.0, 1)
+    torch.cuda.synchronize()
+    out = U.double().cpu().numpy()
+    ctx.close()
+    err = rel_err(out, oracle_run(w, U0, 1))
+    tiles = ",".join(f"{inf['chunk'][a]}:{inf['lines_per_block'][a]}:{inf['staged'][a]}:{inf['pack'][a]}"
+                     for a in range(w.dim))
+    print(f"{name} autotuned ({tiles}) one FP32 step: err {err:.3e}")
+    assert err <= FP32_STEP_TOL, (err, tiles)
+
+
 def test_run_host_matches_device_run():
     w = W.brusselator_2d(p=40, steps=7)
     U0 = W.initial_state(w)
