@@ -185,9 +185,15 @@ etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps
  * pointers. */
 etd_status etd_batch_autotune(etd_ctx *ctx, void *const *U_work);
 
-/* Re-tune the per-axis chunk lengths by timing every candidate on the
- * context's stream with CUDA events (work buffer: a device state of the
- * context's shape, overwritten).  Synchronises. */
+/* Re-plan every axis by timing each candidate sweep on the context's stream
+ * with CUDA events and keeping the fastest: the kernel family (register,
+ * FP32 line pairs, staged, FP32 tile, segmented or cluster-segmented for
+ * long lines), the chunk length, the lines per block and, for segmented
+ * sweeps, the chunks per segment (etd_get_info reports the choice; every
+ * candidate computes the same step).  U_work: a device state of the
+ * context's shape, used as scratch (overwritten).  Synchronises; captured
+ * graphs are dropped.  ETD_ERR_INVALID_ARG on a batched context or a null
+ * pointer. */
 etd_status etd_autotune(etd_ctx *ctx, void *U_work);
 
 etd_status etd_set_stream(etd_ctx *ctx, void *stream);
