@@ -109,7 +109,9 @@ typedef struct {
                                     2: FP32 tile kernel (lines_per_block then counts line units),
                                     3: segmented register kernel (long lines split over blocks;
                                     summary, carry and solve launches), 4: the same in one launch,
-                                    the blocks of a line group forming a thread-block cluster */
+                                    the blocks of a line group forming a thread-block cluster,
+                                    5: circulant kernel of a periodic axis (constant-coefficient
+                                    factorisation, no line tables) */
   int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
                                     (lines_per_block then counts pairs), 1: one line per thread;
                                     segmented kernels: chunks per segment */
@@ -210,19 +212,25 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info);
 /* One step without any device allocation.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc -- plugins whose host
  * application owns every device allocation through its own pool, and
- * real-time loops that must not touch the allocator after start-up.  Same arguments as etd_create plus the
- * state: U (device, layout above) holds U_n at t_n on entry and U_{n+1} on
- * return.  Scratch (the three carried fields and the line tables) lives in
- * one static __device__ array of ETD_NOALLOC_BYTES (64 MiB) that every GPU
- * loading the library keeps until exit; problems with 3 s N elements (plus
- * tables) beyond it are rejected with ETD_ERR_INVALID_ARG before any device
- * work.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Each call recomputes the line tables on the
- * host, copies them into the array on `stream` and synchronises that stream
- * once before launching the sweeps.  All calls share the one array and keep
- * the last call's contents: calls that overlap on the GPU (other streams,
- * other host threads) race. */
+ * real-time loops that must not touch the allocator after start-up.  Same
+ * arguments as etd_create plus the state: U (device, layout above) holds U_n
+ * at t_n on entry and U_{n+1} on return.  Scratch (the three carried fields
+ * and the line tables) lives in one static __device__ array of
+ * ETD_NOALLOC_BYTES (64 MiB) that every GPU loading the library keeps until
+ * exit.  Limits, checked before any device work:
+ *   - 3 s N elements plus the line tables must fit the array, else
+ *     ETD_ERR_INVALID_ARG;
+ *   - every axis must fit one block of whole lines (at most 512 chunks of
+ *     16 positions: n <= 8192 per axis), else ETD_ERR_UNSUPPORTED (the
+ *     segmented plans of etd_create need device buffers this call does not
+ *     have).
+ * Every call looks up the array's device address (cudaGetSymbolAddress) in
+ * the CUDA context current on the calling thread, so a host that switches
+ * contexts or resets the device gets the address valid for the current one.
+ * Each call recomputes the line tables on the host, copies them into the
+ * array on `stream` and synchronises that stream once before launching the
+ * sweeps.  All calls share the one array and keep the last call's contents:
+ * calls that overlap on the GPU (other streams, other host threads) race. */
 etd_status etd_step_noalloc(const etd_grid *grid, const double *D, const etd_reaction *reaction, double k,
                             int32_t precision, void *U, double t_n, void *stream);
 

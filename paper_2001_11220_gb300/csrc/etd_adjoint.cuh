@@ -146,9 +146,11 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
   }
 }
 
-// block-wide sum of nv per-thread values added atomically to acc[0..nv)
+// block-wide sum of NV per-thread values, written to this block's slot
+// part[blockIdx.x * NV + i] (reduce_partials adds the slots to the
+// accumulators in a fixed order, so repeated runs give identical sums)
 template <int NV>
-__device__ __forceinline__ void block_accumulate(double (&v)[NV], double *acc, double *red) {
+__device__ __forceinline__ void block_accumulate(double (&v)[NV], double *part, double *red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i)
@@ -160,8 +162,20 @@ __device__ __forceinline__ void block_accumulate(double (&v)[NV], double *acc, d
   if (threadIdx.x < NV) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += red[w * NV + threadIdx.x];
-    if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+    part[(size_t)blockIdx.x * NV + threadIdx.x] = s;
   }
+}
+
+// acc[i] += sum_b part[b * nv + i] for i < nv: warp i adds the slots in a
+// fixed order (lane-strided partial sums, then a fixed shuffle tree)
+static __global__ void __launch_bounds__(32 * (MAX_SPECIES + 8)) reduce_partials_kernel(const double *__restrict__ part,
+                                                                                 int nblocks, int nv, double *acc) {
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += part[(size_t)b * nv + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) acc[i] += s;
 }
 
 template <typename R, int S, int L, bool CONTIG, int KIND>
@@ -473,13 +487,14 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
   for (int s = 0; s < MAX_SPECIES; ++s) v[s] = (s < S && line_ok) ? (double)dD[s] * A.invD[s] : 0.0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[MAX_SPECIES + i] = line_ok ? (double)pg[i] : 0.0;
-  block_accumulate<MAX_SPECIES + 8>(v, A.acc, red);
+  block_accumulate<MAX_SPECIES + 8>(v, A.part, red);
 }
 
 // L = 1/2 sum (U - target)^2, Ubar = U - target
+// (per-block partial sums to part[blockIdx.x], added by reduce_partials_kernel)
 template <typename R>
 __global__ void __launch_bounds__(256) misfit_kernel(const R *__restrict__ U, const R *__restrict__ T,
-                                                      R *__restrict__ Ub, long long n, double *loss) {
+                                                      R *__restrict__ Ub, long long n, double *part) {
   __shared__ double red[8];
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -493,7 +508,7 @@ __global__ void __launch_bounds__(256) misfit_kernel(const R *__restrict__ U, co
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    atomicAdd(loss, s);
+    part[blockIdx.x] = s;
   }
 }
 

@@ -10,8 +10,9 @@ cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int k
 #undef CALL
 }
 
-cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, cudaStream_t s) {
-  return launch_misfit<float>(U, target, Ubar, n, loss, s);
+cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, double *part,
+                        cudaStream_t s) {
+  return launch_misfit<float>(U, target, Ubar, n, loss, part, s);
 }
 
 }  // namespace etd

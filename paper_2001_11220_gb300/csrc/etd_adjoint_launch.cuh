@@ -13,6 +13,9 @@ cudaError_t launch_adj_one(const SweepArgs<R> &a, int nthreads, size_t smem, cud
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
   fn<<<a.nblocks, nthreads, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_partials_kernel<<<1, 32 * (MAX_SPECIES + 8), 0, s>>>(a.part, a.nblocks, MAX_SPECIES + 8, a.acc);
   return cudaGetLastError();
 }
 
@@ -33,13 +36,19 @@ cudaError_t launch_adj_one(const SweepArgs<R> &a, int nthreads, size_t smem, cud
     default: return cudaErrorInvalidValue;      \
   }
 
-template <typename R>
-cudaError_t launch_misfit(const R *U, const R *T, R *Ub, long long n, double *loss, cudaStream_t s) {
-  const int threads = 256;
-  long long blocks = (n + threads - 1) / threads;
+inline int misfit_blocks(long long n) {
+  long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
-  misfit_kernel<R><<<(int)blocks, threads, 0, s>>>(U, T, Ub, n, loss);
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+template <typename R>
+cudaError_t launch_misfit(const R *U, const R *T, R *Ub, long long n, double *loss, double *part, cudaStream_t s) {
+  const int blocks = misfit_blocks(n);
+  misfit_kernel<R><<<blocks, 256, 0, s>>>(U, T, Ub, n, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_partials_kernel<<<1, 32, 0, s>>>(part, blocks, 1, loss);
   return cudaGetLastError();
 }
 

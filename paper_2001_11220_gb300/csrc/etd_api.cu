@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/etdrdpif.h"
+#include "etd_circ.h"
 #include "etd_context.h"
 #include "etd_internal.h"
 #include "etd_tables.h"
@@ -148,6 +149,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
   P.mx = P.m;
   P.nseg = 1;
   P.cluster = false;
+  P.circ = false;
   if (pack == 2) {
     // register kernel on line pairs (lo, lo + 1) of a strided FP32 axis with an even stride
     if (I.real_bytes != 4 || a == 0 || st % 2 != 0 || L != 8) return false;
@@ -243,6 +245,7 @@ bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk) {
   P.mx = m;
   P.nseg = 1;
   P.cluster = false;
+  P.circ = false;
   const int S = I.S, nq = (P.kind == SWEEP_LAST) ? 3 * S : 5 * S;
   StagePlan sp{};
   sp.staged = 2;
@@ -304,6 +307,7 @@ bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster) {
   P.nlines = I.N / n;
   P.pk = 1;
   P.sp = StagePlan{};
+  P.circ = false;
   P.mx = mx;
   P.nseg = (m + mx - 1) / mx;
   P.pitch = exchange_pitch(mx);
@@ -321,6 +325,41 @@ bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster) {
   P.nthreads = nlb * mx;
   P.cluster = cluster;
   P.smem = sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes, 1, cluster, P.nseg);
+  return P.smem <= 200 * 1024;
+}
+
+// Circulant kernels (etd_circ.cuh) for a periodic axis: p = m L with m a
+// power of two.  First axis: lanes along the line, one block of
+// max(m, 256) threads holding 256 / m lines (m <= 512).  Problems with a
+// manufactured source are left to the table kernels.
+bool plan_axis_circ(Instance &I, int a, int L) {
+  AxisPlan &P = I.plan[a];
+  const long long n = I.n[a];
+  if (I.bc[a] != BC_PERIODIC || a != 0) return false;
+  if (I.rkind == ETD_REACTION_ENZYME && I.rp[0] != 0.0) return false;
+  if (I.real_bytes == 4 ? (L != 8 && L != 16) : (L != 4 && L != 8)) return false;
+  if (n % L != 0) return false;
+  const long long m = n / L;
+  if (m < 1 || m > 512 || (m & (m - 1)) != 0) return false;
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  P.L = L;
+  P.m = (int)m;
+  P.kind = SWEEP_FIRST;
+  P.st = st;
+  P.nlines = I.N / n;
+  P.pitch = 1;
+  P.pk = 1;
+  P.sp = StagePlan{};
+  P.mx = P.m;
+  P.nseg = 1;
+  P.cluster = false;
+  P.circ = true;
+  P.nthreads = (int)std::max<long long>(m, 256);
+  P.nlb = P.nthreads / P.m;
+  P.nlo_blocks = 1;
+  P.nblocks = (int)((P.nlines + P.nlb - 1) / P.nlb);
+  P.smem = circ_first_smem(I.S, L, P.nthreads, P.m, P.nlb, I.real_bytes);
   return P.smem <= 200 * 1024;
 }
 
@@ -348,11 +387,19 @@ bool cluster_plan_fits(const Instance &I, int a) {
   return nclusters > 0;
 }
 
-// tile kernels move U with 16-byte copies
-bool needs_aligned_state(const Instance &I) {
-  for (int a = 0; a < I.dim; ++a)
-    if (I.plan[a].sp.staged == 2) return true;
-  return false;
+// alignment in bytes the kernels need of the state pointer: tile kernels
+// move U with 16-byte copies, circulant sweeps with 16-byte copies and
+// 32-byte stores
+size_t state_alignment(const Instance &I) {
+  size_t al = 1;
+  for (int a = 0; a < I.dim; ++a) {
+    if (I.plan[a].sp.staged == 2) al = std::max<size_t>(al, 16);
+    if (I.plan[a].circ) al = std::max<size_t>(al, 32);
+  }
+  return al;
+}
+bool misaligned_state(const Instance &I, const void *U) {
+  return (reinterpret_cast<uintptr_t>(U) & (state_alignment(I) - 1)) != 0;
 }
 
 int default_chunk(const Instance &I, int a) {
@@ -454,6 +501,65 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
     if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading line tables");
   }
   AxisPlan &P = I.plan[a];
+  if (I.circ_tables[a]) {
+    cudaFree(I.circ_tables[a]);
+    I.circ_tables[a] = nullptr;
+  }
+  if (P.circ) {
+    // circulant coefficients of every (species, gamma) and their power tables Lambda^i
+    const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+    CircHost H[MAX_SPECIES][3];
+    size_t per = 0;
+    for (int s = 0; s < I.S; ++s)
+      for (int g = 0; g < 3; ++g) {
+        circ_coeffs((I.k / gammas[g]) * I.D[s] / (h * h), (int)I.n[a], P.L, H[s][g]);
+        per = std::max(per, H[s][g].lpow.size());
+      }
+    const size_t rb = I.real_bytes;
+    std::vector<unsigned char> img((size_t)I.S * 3 * per * rb, 0);
+    for (int s = 0; s < I.S; ++s)
+      for (int g = 0; g < 3; ++g)
+        for (size_t i = 0; i < H[s][g].lpow.size(); ++i) {
+          unsigned char *d = img.data() + ((size_t)(s * 3 + g) * per + i) * rb;
+          if (rb == 8) memcpy(d, &H[s][g].lpow[i], 8);
+          else {
+            const float v = (float)H[s][g].lpow[i];
+            memcpy(d, &v, 4);
+          }
+        }
+    err = cudaMalloc(&I.circ_tables[a], img.size());
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "circulant power tables");
+    err = cudaMemcpy(I.circ_tables[a], img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "uploading circulant power tables");
+    auto fill = [&](auto &C, auto zero) {
+      using R = decltype(zero);
+      memset(&C, 0, sizeof(C));
+      C.N = I.N;
+      C.st = P.st;
+      C.nlines = P.nlines;
+      C.nlo = P.st;
+      C.p = (int)I.n[a];
+      C.m = P.m;
+      C.lpb = P.nlb;
+      C.ncol = P.nlb;
+      C.nlo_blocks = P.nlo_blocks;
+      C.rkind = I.rkind;
+      C.kR = (R)I.k;
+      C.half_kR = (R)(0.5 * I.k);
+      for (int j = 0; j < 8; ++j) C.rpR[j] = (R)I.rp[j];
+      for (int s = 0; s < I.S; ++s) {
+        C.cP[s] = (R)(1.0 / H[s][0].alpha);
+        C.cT[s] = (R)(9.0 / H[s][1].alpha);
+        C.cS[s] = (R)(8.0 / H[s][2].alpha);
+        for (int g = 0; g < 3; ++g) {
+          circ_to_args<R>(H[s][g], C.mat[s][g]);
+          C.lpow[s][g] = (const R *)((unsigned char *)I.circ_tables[a] + (size_t)(s * 3 + g) * per * rb);
+        }
+      }
+    };
+    if (rb == 8) fill(I.circ64[a], 0.0);
+    else fill(I.circ32[a], 0.0f);
+  }
   if (P.nseg > 1 && !P.cluster) {
     // segment summaries and carries (2 values per solve, line and segment) and scalars
     const int nq = (P.kind == SWEEP_LAST) ? 3 * I.S : 5 * I.S;
@@ -559,6 +665,16 @@ void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A) {
 template <typename R>
 cudaError_t run_sweep(const Instance &I, int a, SweepArgs<R> &A, cudaStream_t s) {
   const AxisPlan &P = I.plan[a];
+  if (P.circ) {
+    CircArgs<R> C;
+    if constexpr (sizeof(R) == 8) C = I.circ64[a];
+    else C = I.circ32[a];
+    for (int f = 0; f < 3; ++f) {
+      C.in[f] = A.in[f];
+      C.out[f] = A.out[f];
+    }
+    return launch_circ(C, I.S, P.L, P.kind, P.nthreads, P.smem, P.nblocks, s);
+  }
   if (P.nseg <= 1) return launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
   if (P.cluster) {
     A.segphase = SEG_CLUSTER;
@@ -614,7 +730,7 @@ cudaError_t prof_end(etd_ctx *ctx, cudaStream_t s, int kind, cudaEvent_t ev0) {
 
 template <typename R>
 static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t s, etd_ctx *prof) {
-  if (needs_aligned_state(I) && (reinterpret_cast<uintptr_t>(U) & 15)) return cudaErrorMisalignedAddress;
+  if (misaligned_state(I, U)) return cudaErrorMisalignedAddress;
   R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
   for (int a = 0; a < I.dim; ++a) {
     const AxisPlan &P = I.plan[a];
@@ -672,7 +788,7 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   // ETD_TILES="L:nlb:kernel[:pack],..." (one entry per axis; kernel 0
   // register, 1 staged, 2 tile with nlb lines per block, 3 segmented register
   // kernel with the fourth field = chunks per segment, 4 the same as one
-  // cluster launch) forces tile shapes, e.g. to reproduce an autotuned
+  // cluster launch, 5 circulant kernel of a periodic axis) forces tile shapes, e.g. to reproduce an autotuned
   // configuration in a profiler run
   const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
@@ -685,7 +801,8 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
         if (p) ++p;
       }
       if (p && sscanf(p, "%d:%d:%d:%d", &fl, &fn, &fs, &fp) >= 3 && (fl == 4 || fl == 8 || fl == 16)) {
-        const bool ok = fs == 4   ? plan_axis_seg(I, a, fl, fn, fp, true) && cluster_plan_fits(I, a)
+        const bool ok = fs == 5   ? plan_axis_circ(I, a, fl)
+                        : fs == 4 ? plan_axis_seg(I, a, fl, fn, fp, true) && cluster_plan_fits(I, a)
                         : fs == 3 ? plan_axis_seg(I, a, fl, fn, fp, false)
                         : fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)
                                   : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1);
@@ -740,7 +857,7 @@ etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction 
 etd_status etd_set_stream(etd_ctx *ctx, void *stream) {
   if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
   ctx->stream = (cudaStream_t)stream;
-  ctx->graphs.clear();
+  drop_graphs(ctx);
   return ETD_OK;
 }
 
@@ -748,8 +865,9 @@ etd_status etd_step(etd_ctx *ctx, void *U, double t_n) {
   if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_step on a batched context");
   if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
-  if (needs_aligned_state(ctx->inst[0]) && (reinterpret_cast<uintptr_t>(U) & 15))
-    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be 16-byte aligned (FP32 tile kernels copy 16 bytes at a time)");
+  if (misaligned_state(ctx->inst[0], U))
+    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be %zu-byte aligned for the planned kernels (tile kernels copy "
+                "16 bytes, circulant sweeps store 32 bytes at a time)", state_alignment(ctx->inst[0]));
   if (!std::isfinite(t_n)) return fail(ctx, ETD_ERR_INVALID_ARG, "t_n not finite");
   cudaError_t e = forward_step(ctx->inst[0], U, t_n, ctx->stream, ctx);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etd_step launch");
@@ -762,8 +880,9 @@ etd_status etd_run(etd_ctx *ctx, void *U, double t0, int64_t nsteps) {
   if (!U) return fail(ctx, ETD_ERR_INVALID_ARG, "U is NULL");
   if (nsteps < 0) return fail(ctx, ETD_ERR_INVALID_ARG, "nsteps < 0");
   if (!std::isfinite(t0)) return fail(ctx, ETD_ERR_INVALID_ARG, "t0 not finite");
-  if (needs_aligned_state(ctx->inst[0]) && (reinterpret_cast<uintptr_t>(U) & 15))
-    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be 16-byte aligned (FP32 tile kernels copy 16 bytes at a time)");
+  if (misaligned_state(ctx->inst[0], U))
+    return fail(ctx, ETD_ERR_INVALID_ARG, "U must be %zu-byte aligned for the planned kernels (tile kernels copy "
+                "16 bytes, circulant sweeps store 32 bytes at a time)", state_alignment(ctx->inst[0]));
   const Instance &I = ctx->inst[0];
   return run_steps(ctx, [&](cudaStream_t s, int64_t n) -> cudaError_t {
     return forward_step(I, U, t0 + (double)n * I.k, s, ctx);
@@ -847,7 +966,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   for (int a = 0; a < I.dim; ++a) {
     info->chunk[a] = I.plan[a].L;
     info->lines_per_block[a] = I.plan[a].nlb;
-    info->staged[a] = I.plan[a].nseg > 1 ? (I.plan[a].cluster ? 4 : 3) : I.plan[a].sp.staged;
+    info->staged[a] = I.plan[a].circ ? 5 : I.plan[a].nseg > 1 ? (I.plan[a].cluster ? 4 : 3) : I.plan[a].sp.staged;
     info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
   }
   return ETD_OK;
@@ -855,13 +974,16 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
 
 void etd_destroy(etd_ctx *ctx) {
   if (!ctx) return;
-  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-  ctx->graphs.clear();
+  drop_graphs(ctx);
   for (Instance &I : ctx->inst) {
     for (void *p : I.owned) cudaFree(p);
     I.owned.clear();
     I.arena.release();
     for (void *&p : I.axis_tables) {
+      if (p) cudaFree(p);
+      p = nullptr;
+    }
+    for (void *&p : I.circ_tables) {
       if (p) cudaFree(p);
       p = nullptr;
     }
@@ -876,6 +998,7 @@ void etd_destroy(etd_ctx *ctx) {
   for (void *p : ctx->adj_ubar)
     if (p) cudaFree(p);
   if (ctx->adj_acc) cudaFree(ctx->adj_acc);
+  if (ctx->adj_part) cudaFree(ctx->adj_part);
   if (ctx->ckpt) cudaFree(ctx->ckpt);
   if (ctx->seg) cudaFree(ctx->seg);
   for (auto &rec : ctx->prof_events) {

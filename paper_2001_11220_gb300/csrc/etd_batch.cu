@@ -131,8 +131,7 @@ etd_status plan_batch(etd_ctx *ctx, const int *Lax) {
       return fail(ctx, ETD_ERR_CUDA, "ensemble launch tables upload");
   }
   // arguments and captured graphs refer to the old plan: rebuild on the next run
-  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-  ctx->graphs.clear();
+  drop_graphs(ctx);
   ctx->batch_states.clear();
   return ETD_OK;
 }
@@ -214,8 +213,7 @@ etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps
     etd_status st = ctx->precision == ETD_FP64 ? upload_batch_args<double>(ctx, U) : upload_batch_args<float>(ctx, U);
     if (st != ETD_OK) return st;
     ctx->batch_states = now;
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    drop_graphs(ctx);
   }
   const Instance &I0 = ctx->inst[0];
   const double k = I0.k;

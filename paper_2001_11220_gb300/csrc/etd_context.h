@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/etdrdpif.h"
+#include "etd_circ.h"
 #include "etd_internal.h"
 
 #define ETD_MAX_BLOCK_THREADS 512
@@ -66,6 +67,7 @@ struct AxisPlan {
   void *seg_buf = nullptr;  // segmented sweeps: summaries, carries, scalars (owned)
   size_t seg_bytes = 0;
   StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel
+  bool circ = false;   // periodic axis solved by the circulant kernels (etd_circ.cuh); nlb = lines per block
 };
 
 // one problem: grid, coefficients, tables, plans and scratch
@@ -94,6 +96,11 @@ struct Instance {
   MatTab<double> atab64[2][3][MAX_SPECIES][3];
   DeviceArena arena;                               // source tables, adjoint tables
   void *axis_tables[3] = {nullptr, nullptr, nullptr};  // forward line tables of each axis (one block)
+  // circulant plans: kernel arguments with every coefficient filled in (only
+  // the field pointers change per launch) and their device power tables
+  CircArgs<float> circ32[3];
+  CircArgs<double> circ64[3];
+  void *circ_tables[3] = {nullptr, nullptr, nullptr};
   std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
 };
 
@@ -139,6 +146,7 @@ struct etd_ctx {
   void *adj_ws = nullptr;         // 9 carried fields: forward axis-0 outputs, axis-1 outputs, adjoint fields
   void *adj_ubar[2] = {nullptr, nullptr};
   double *adj_acc = nullptr;      // dL/dD[2], dL/dparams[8], loss
+  double *adj_part = nullptr;     // per-block partial sums of the adjoint sweeps and the misfit
   void *ckpt = nullptr;           // checkpoint states
   size_t ckpt_states = 0;
   void *seg = nullptr;            // states of one recomputed segment
@@ -153,6 +161,13 @@ cudaError_t forward_step(const Instance &I, void *U, double t, cudaStream_t s, e
 cudaError_t prof_begin(etd_ctx *ctx, cudaStream_t s, cudaEvent_t &ev);
 cudaError_t prof_end(etd_ctx *ctx, cudaStream_t s, int kind, cudaEvent_t ev0);
 template <typename R> void fill_args(const Instance &I, int a, int transpose, SweepArgs<R> &A);
+
+// Destroys every cached executable graph of the context (they hold the old
+// plans, streams or state pointers) and empties the cache.
+inline void drop_graphs(etd_ctx *ctx) {
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
 
 // Enqueue nsteps steps with enqueue(stream, step_index).  Runs of two or more
 // steps on a non-legacy stream are captured once into a CUDA graph (cached

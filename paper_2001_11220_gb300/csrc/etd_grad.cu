@@ -135,6 +135,10 @@ etd_status prepare_adjoint(etd_ctx *ctx, Instance &I) {
     if (cudaMalloc(&ctx->adj_ubar[1], field) != cudaSuccess) return fail(ctx, ETD_ERR_OOM, "adjoint workspace");
     if (cudaMalloc((void **)&ctx->adj_acc, 16 * sizeof(double)) != cudaSuccess)
       return fail(ctx, ETD_ERR_OOM, "adjoint accumulators");
+    size_t np = (size_t)loss_blocks((long long)I.S * I.N);
+    for (int a = 0; a < I.dim; ++a) np = std::max(np, (size_t)I.aplan[a].nblocks * (MAX_SPECIES + 8));
+    if (cudaMalloc((void **)&ctx->adj_part, np * sizeof(double)) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "adjoint partial sums");
   }
   return ETD_OK;
 }
@@ -222,6 +226,7 @@ cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double 
       A.invD[sp] = 1.0 / I.D[sp];
     }
     A.acc = ctx->adj_acc;
+    A.part = ctx->adj_part;
     if (P.kind == ADJ_LAST) {
       A.in[0] = ubar_next;
       A.fin[0] = z;
@@ -358,10 +363,10 @@ etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target
   if (target) {
     if (I.real_bytes == 8)
       e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
-                      ctx->adj_acc + 10, s);
+                      ctx->adj_acc + 10, ctx->adj_part, s);
     else
       e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N,
-                      ctx->adj_acc + 10, s);
+                      ctx->adj_acc + 10, ctx->adj_part, s);
   } else {
     e = cudaMemcpyAsync(ub, ubarN, bytes, cudaMemcpyDeviceToDevice, s);
   }

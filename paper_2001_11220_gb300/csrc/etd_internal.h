@@ -120,6 +120,8 @@ template <typename R> struct SweepArgs {
   MatTab<R> matT[MAX_SPECIES][3];  // tables of the transposed line matrices
   const R *fin[3];                 // forward quantities recomputed for this sweep
   double *acc;                     // device accumulators: dL/dD[MAX_SPECIES], dL/dparams[8]
+  double *part;                    // per-block partial sums [nblocks][MAX_SPECIES + 8], added to acc
+                                   // in a fixed order by a second launch (reproducible sums)
   double invD[MAX_SPECIES];        // 1 / D_s
 };
 
@@ -181,8 +183,11 @@ cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int k
                            cudaStream_t s);
 cudaError_t launch_adjoint(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);
-cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, cudaStream_t s);
-cudaError_t launch_loss(const double *U, const double *target, double *Ubar, long long n, double *loss,
+// part: at least loss_blocks(n) doubles of per-block partial sums
+int loss_blocks(long long n);
+cudaError_t launch_loss(const float *U, const float *target, float *Ubar, long long n, double *loss, double *part,
+                        cudaStream_t s);
+cudaError_t launch_loss(const double *U, const double *target, double *Ubar, long long n, double *loss, double *part,
                         cudaStream_t s);
 
 // shared-memory bytes of one adjoint sweep block

@@ -13,7 +13,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "../../include/etdrdpif.h"
@@ -35,25 +34,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[ETD_NOALLOC_BYT
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_dev_ptr[kMaxDevices] = {nullptr};  // device address of g_noalloc_scratch per device
-
-// set-up, once per device with that device current: the array's device
-// address (its host-side name is only a stand-in for the symbol)
+// The array's device address, looked up on every call with the caller's
+// device and context current.  The host-side name g_noalloc_scratch is only
+// a stand-in for the symbol: handing it to a kernel would fault (or, where
+// the GPU can reach host memory, silently use the wrong memory).  The address
+// is not cached: it belongs to the CUDA context that is current, and a host
+// application may make another context current between calls, or
+// cudaDeviceReset may recreate the primary context; the lookup is a cheap
+// host-side query.
 etd_status scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, ETD_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> g(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_dev_ptr[dev] = p;
-  }
-  *out = g_dev_ptr[dev];
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = p;
   return ETD_OK;
 }
 

@@ -16,6 +16,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
 bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk);
 bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster);
 bool cluster_plan_fits(const Instance &I, int a);
+bool plan_axis_circ(Instance &I, int a, int L);
 etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
 }  // namespace etd
 
@@ -30,9 +31,11 @@ struct Cand {
   bool tile = false;  // FP32 tile kernel with nlb lines per block
   int seg = 0;        // > 0: segmented register kernel with seg chunks per segment
   bool cluster = false;  // segmented as one cluster launch
+  bool circ = false;     // circulant kernel of a periodic axis
 };
 
 bool plan_cand(Instance &I, int a, const Cand &c) {
+  if (c.circ) return plan_axis_circ(I, a, c.L);
   if (c.seg) return plan_axis_seg(I, a, c.L, c.nlb, c.seg, c.cluster) && cluster_plan_fits(I, a);
   if (c.tile) return plan_axis_tile(I, a, c.L, c.nlb, c.pack);
   return plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg, c.pack);
@@ -74,7 +77,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_autotune on a batched context");
   if (!U_work) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work is NULL");
   Instance &I = ctx->inst[0];
-  ctx->graphs.clear();
+  drop_graphs(ctx);
   const int Ls32[] = {4, 8, 16}, Ls64[] = {4, 8};
   const int nlbs[] = {4, 8, 16, 32, 64};
   for (int a = 0; a < I.dim; ++a) {
@@ -90,6 +93,11 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       if (I.real_bytes == 4 && L >= 8)
         for (int nlb : {16, 32})
           for (int pk : {1, 2}) cands.push_back({L, nlb, false, pk, true});  // tile kernels
+      if (I.bc[a] == 2) {  // periodic axis: circulant kernels (planner checks the shape)
+        Cand c{L, 0, true, 1};
+        c.circ = true;
+        cands.push_back(c);
+      }
       if ((I.n[a] + L - 1) / L > 32)  // long lines: segmented blocks (planner checks the shape)
         for (int mx : {16, 32})
           for (int nlb : {8, 16, 32})
@@ -98,7 +106,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
     const AxisPlan keep = I.plan[a];
     double best = 1e30;
     Cand pick{keep.L, keep.sp.staged || keep.pk == 2 ? keep.nlb : 0, !keep.sp.staged, keep.pk,
-              keep.sp.staged == 2, keep.nseg > 1 ? keep.mx : 0, keep.cluster};
+              keep.sp.staged == 2, keep.nseg > 1 ? keep.mx : 0, keep.cluster, keep.circ};
     if (pick.tile) pick.nlb = keep.nlb * keep.pk;
     if (pick.seg) pick.nlb = keep.nlb;
     for (const Cand &c : cands) {
@@ -111,7 +119,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       if (st != ETD_OK) return st;
       if (std::getenv("ETD_TUNE_VERBOSE"))
         fprintf(stderr, "etd_autotune axis %d: L=%d nlb=%d mx=%d %s%s -> %.4f ms\n", a, c.L, I.plan[a].nlb, I.plan[a].mx,
-                I.plan[a].nseg > 1 ? (I.plan[a].cluster ? "cluster-segmented" : "segmented")
+                I.plan[a].circ ? "circulant" : I.plan[a].nseg > 1 ? (I.plan[a].cluster ? "cluster-segmented" : "segmented")
                 : I.plan[a].sp.staged == 2 ? "tile"
                                                  : (I.plan[a].sp.staged ? "staged" : "register"),
                 I.plan[a].pk == 2 ? " pairs" : "", ms);

@@ -1,10 +1,13 @@
 """GPU reverse mode against the FP64 oracle's discrete adjoint (itself pinned
 to finite differences in test_oracle_pins.py).
 
-Tolerances (FP64): state adjoint <= 1e-11 relative; dL/dD and dL/dparams
-<= 1e-9 relative (they are sums over the whole grid of products whose terms
-cancel; the GPU forms <lambda, B x> as <lambda, b - x> / D).  FP32: the error
-of the FP32 gradient against the FP64 oracle gradient is measured and stated.
+Tolerances (FP64): state adjoint and dL/dU0 <= 1e-12 relative (the forward
+bar); over a 40-step run 1e-11.  dL/dD and dL/dparams: fp64_param_grad_bound
+(tests/tolerances.py), the FP64 solve error amplified by the cancellation of
+b - x in <lambda, B x> = <lambda, b - x> / r (measured on the starting state),
+times the number of reversed steps.  The block sums are reduced in a fixed order, so repeated runs are
+bit-identical.  FP32: the error of the FP32 gradient against
+the FP64 oracle gradient is measured and stated.
 """
 import numpy as np
 import pytest
@@ -14,6 +17,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_2001_11220_gb300 import workloads as W  # noqa: E402
 from tests.dense_reference import oracle_problem  # noqa: E402
+from tests.tolerances import fp64_param_grad_bound as pbound  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -61,11 +65,12 @@ def test_step_adjoint_fp64_matches_oracle(w):
     torch.cuda.synchronize()
     ref, rdD, rdp = oracle.step_adjoint(oracle_problem(w), U0, 0.2, ub)
     ctx.close()
-    assert rel(got.cpu().numpy(), ref) <= 1e-11
-    assert rel(dD, rdD) <= 1e-9, (dD, rdD)
+    print(f"{w.name} step adjoint: state {rel(got.cpu().numpy(), ref):.2e}, dD {rel(dD, rdD):.2e}")
+    assert rel(got.cpu().numpy(), ref) <= 1e-12
+    assert rel(dD, rdD) <= pbound(w, U0), (dD, rdD, pbound(w, U0))
     npar = len(w.params)
     if npar and np.max(np.abs(rdp[:npar])) > 0:
-        assert rel(dp[:npar], rdp[:npar]) <= 1e-9, (dp, rdp)
+        assert rel(dp[:npar], rdp[:npar]) <= pbound(w, U0), (dp, rdp, pbound(w, U0))
 
 
 @pytest.mark.parametrize("w,nsteps,ckpt", [
@@ -81,15 +86,19 @@ def test_grad_fp64_matches_oracle(w, nsteps, ckpt):
                                  nsteps, ckpt)
     rloss, rdU0, rdD, rdp = oracle.grad(oracle_problem(w), U0, 0.0, target, nsteps)
     ctx.close()
+    print(f"grad {w.name}: dU0 {rel(dU0.cpu().numpy(), rdU0):.2e}, dD {rel(dD, rdD):.2e}")
     assert abs(loss - rloss) <= 1e-12 * abs(rloss)
-    assert rel(dU0.cpu().numpy(), rdU0) <= 1e-10
-    assert rel(dD, rdD) <= 1e-9, (dD, rdD)
+    assert rel(dU0.cpu().numpy(), rdU0) <= 1e-12
+    assert rel(dD, rdD) <= pbound(w, U0, nsteps), (dD, rdD, pbound(w, U0, nsteps))
     npar = len(w.params)
     if np.max(np.abs(rdp[:npar])) > 0:
-        assert rel(dp[:npar], rdp[:npar]) <= 1e-9, (dp, rdp)
+        assert rel(dp[:npar], rdp[:npar]) <= pbound(w, U0, nsteps), (dp, rdp, pbound(w, U0, nsteps))
 
 
 def test_grad_checkpoint_interval_does_not_change_result():
+    """Recomputation from checkpoints repeats the forward arithmetic exactly and
+    the block sums are reduced in a fixed order: every spacing, and a repeated
+    call, give bit-identical loss and gradients."""
     w = case("bru2d_ck", (16, 12), W.NEUMANN, (0.02, 0.03), "brusselator", (1.0, 3.4), 0.05, ((1.0, 3.4), 0.1))
     U0 = torch.tensor(W.initial_state(w), device="cuda")
     tg = torch.tensor(W.initial_state(w, seed=3), device="cuda")
@@ -97,8 +106,9 @@ def test_grad_checkpoint_interval_does_not_change_result():
     a = ctx.grad(U0, 0.0, tg, 9, 1)
     b = ctx.grad(U0, 0.0, tg, 9, 4)
     c = ctx.grad(U0, 0.0, tg, 9, 9)
+    d = ctx.grad(U0, 0.0, tg, 9, 1)
     ctx.close()
-    for x in (b, c):
+    for x in (b, c, d):
         assert x[0] == a[0]
         assert torch.equal(x[1], a[1])
         assert np.array_equal(x[2], a[2]) and np.array_equal(x[3], a[3])
@@ -153,8 +163,8 @@ def test_grayscott_32_gradient_fp32_and_fp64_vs_oracle():
     print(f"grayscott3d_32 {nsteps} steps: FP32 gradient error vs FP64 oracle: dU0 {e_g32:.3e}, "
           f"dD {e_d32:.3e}, dparams {e_p32:.3e}; FP64: dU0 {rel(g64.cpu().numpy(), rdU0):.3e}")
     assert abs(l64 - rloss) <= 1e-12 * abs(rloss)
-    assert rel(g64.cpu().numpy(), rdU0) <= 1e-10
-    assert rel(d64, rdD) <= 1e-9 and rel(p64[:2], rdp[:2]) <= 1e-9
+    assert rel(g64.cpu().numpy(), rdU0) <= 1e-11
+    assert rel(d64, rdD) <= pbound(w, U0, nsteps) and rel(p64[:2], rdp[:2]) <= pbound(w, U0, nsteps)
     assert e_g32 <= 1e-3 and e_d32 <= 1e-2 and e_p32 <= 1e-2
 
 
@@ -195,9 +205,9 @@ def test_autograd_simulate_matches_oracle_adjoint():
         ub, d1, p1 = oracle.step_adjoint(P, states[i], i * w.k, ub)
         dD += d1
         dp += p1
-    assert rel(U0t.grad.cpu().numpy(), ub) <= 1e-10
-    assert rel(Dt.grad.numpy(), dD) <= 1e-9
-    assert rel(pt.grad.numpy(), dp[:2]) <= 1e-9
+    assert rel(U0t.grad.cpu().numpy(), ub) <= 1e-12
+    assert rel(Dt.grad.numpy(), dD) <= pbound(w, U0, nsteps)
+    assert rel(pt.grad.numpy(), dp[:2]) <= pbound(w, U0, nsteps)
 
 
 @pytest.mark.parametrize("kernel", [3, 4], ids=["segmented", "cluster"])
@@ -216,5 +226,19 @@ def test_grad_with_segmented_forward_sweeps(kernel, monkeypatch):
     rloss, rdU0, rdD, rdp = oracle.grad(oracle_problem(w), U0, 0.0, target, 3)
     ctx.close()
     assert abs(loss - rloss) <= 1e-12 * abs(rloss)
-    assert rel(dU0.cpu().numpy(), rdU0) <= 1e-10
-    assert rel(dD, rdD) <= 1e-9, (dD, rdD)
+    assert rel(dU0.cpu().numpy(), rdU0) <= 1e-12
+    assert rel(dD, rdD) <= pbound(w, U0, 3), (dD, rdD)
+
+
+def test_grad_fp32_repeatable():
+    """FP32 gradient of the 3D Gray-Scott problem: two identical calls give
+    bit-identical loss, dL/dU0, dL/dD and dL/dparams (fixed-order block sums)."""
+    w = W.gray_scott_3d(16, steps=4).with_(k=0.5, D=(0.01, 0.005))
+    U0 = torch.tensor(W.initial_state(w), device="cuda", dtype=torch.float32)
+    tg = torch.tensor(W.initial_state(w, seed=5), device="cuda", dtype=torch.float32)
+    ctx = _ctx(w, "fp32")
+    a = ctx.grad(U0, 0.0, tg, 4, 2)
+    b = ctx.grad(U0, 0.0, tg, 4, 2)
+    ctx.close()
+    assert a[0] == b[0] and torch.equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])

@@ -270,6 +270,38 @@ def test_reaction_steady_states():
         assert np.max(np.abs(oracle.reaction(P, U, 0.0))) < 1e-12
 
 
+def test_gray_scott_interior_equilibrium():
+    """Gray-Scott with F = 0.04, kappa = 0.06 has the non-trivial homogeneous
+    equilibrium (u, v) = (0.5, 0.2): u v = F + kappa and F (1 - u) = (F + kappa) v
+    give 0.1 v^2 - 0.04 v + 0.004 = 0, a double root at v = 0.2.  Every term of
+    the reaction is non-zero there (u v^2 = 0.02 = F (1 - u) = (F + kappa) v), so
+    a swapped u^2 v or a wrong sign of any term moves F away from zero.  Nearby
+    points must not be equilibria."""
+    P = oracle.Problem(n=(3, 3), bc=(2, 2), D=(0.1, 0.1), reaction=oracle.GRAY_SCOTT, params=(0.04, 0.06), k=0.1)
+    U = np.stack([np.full((3, 3), 0.5), np.full((3, 3), 0.2)])
+    assert np.max(np.abs(oracle.reaction(P, U, 0.0))) < 1e-15
+    for du, dv in ((0.01, 0.0), (0.0, 0.01), (-0.01, 0.01)):
+        V = np.stack([np.full((3, 3), 0.5 + du), np.full((3, 3), 0.2 + dv)])
+        assert np.min(np.abs(oracle.reaction(P, V, 0.0)).max(axis=0)) > 1e-4, (du, dv)
+
+
+@pytest.mark.parametrize("kind,params,uv,f", [
+    # hand-evaluated at (u, v) = (0.3, 0.7): -u v^2 + F (1 - u) = -0.147 + 0.028; u v^2 - (F + kappa) v = 0.147 - 0.07
+    (oracle.GRAY_SCOTT, (0.04, 0.06), (0.3, 0.7), (-0.119, 0.077)),
+    # a + u^2 v - (b + 1) u = 1 + 0.5 - 2.2; b u - u^2 v = 1.7 - 0.5 at (0.5, 2)
+    (oracle.BRUSSELATOR, (1.0, 3.4), (0.5, 2.0), (-0.7, 1.2)),
+    # gamma (a - u + u^2 v) = 2 (0.1 - 0.5 + 0.5); gamma (b - u^2 v) = 2 (0.9 - 0.5) at (0.5, 2)
+    (oracle.SCHNAKENBERG, (0.1, 0.9, 2.0), (0.5, 2.0), (0.2, 0.8)),
+])
+def test_reaction_hand_values(kind, params, uv, f):
+    """Two-species reactions at a point where u^2 v and u v^2 differ (Section 8's
+    model equations evaluated by hand)."""
+    P = oracle.Problem(n=(3, 3), bc=(1, 1), D=(0.1, 0.1), reaction=kind, params=params, k=0.1)
+    U = np.stack([np.full((3, 3), uv[0]), np.full((3, 3), uv[1])])
+    out = oracle.reaction(P, U, 0.0)
+    assert np.max(np.abs(out[0] - f[0])) < 1e-14 and np.max(np.abs(out[1] - f[1])) < 1e-14
+
+
 def test_manufactured_source_consistency():
     """u = e^{-t} prod sin(pi x_a) solves u_t = d Lap u - u/(1+u) + src with the continuous
     Laplacian: check the residual pointwise with analytic derivatives."""

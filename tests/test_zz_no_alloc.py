@@ -15,11 +15,11 @@ torch = pytest.importorskip("torch")
 
 from paper_2001_11220_gb300 import _binding as B  # noqa: E402
 from paper_2001_11220_gb300 import workloads as W  # noqa: E402
+from tests.tolerances import fp32_step_bound  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-FP32_STEP_TOL = 2.0 ** -24 * 17 * 64
 
 
 def _noalloc_step(w, U, t, precision, stream):
@@ -48,7 +48,7 @@ def _rel(a, b):
 def test_noalloc_matches_regular_step_twice(w, prec):
     from paper_2001_11220_gb300.api import EtdRdpIf
     precision = B.ETD_FP64 if prec == "fp64" else B.ETD_FP32
-    tol = FP64_TOL if prec == "fp64" else FP32_STEP_TOL
+    tol = FP64_TOL if prec == "fp64" else fp32_step_bound(w)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = EtdRdpIf.from_workload(w, prec, stream=s)
@@ -64,6 +64,38 @@ def test_noalloc_matches_regular_step_twice(w, prec):
         assert err <= tol, (n, err)
         assert bool(torch.isfinite(Bst).all())
     ctx.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The entry point's promise: after a first call (which may load kernel
+    modules), a further call leaves the device's free memory unchanged."""
+    w = W.brusselator_2d(p=48, steps=2)
+    s = torch.cuda.Stream()
+    U = torch.tensor(W.initial_state(w), device="cuda", dtype=torch.float64)
+    _noalloc_step(w, U, 0.0, B.ETD_FP64, s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    _noalloc_step(w, U, w.k, B.ETD_FP64, s)
+    s.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert bool(torch.isfinite(U).all())
+
+
+def test_noalloc_rejects_too_long_axis():
+    """Axes longer than one block of whole lines (n > 8192) need the segmented
+    plans, whose device buffers this entry point does not have."""
+    from paper_2001_11220_gb300.api import make_grid, make_reaction
+    lib = B.load()
+    g = make_grid((8200, 3), (0, 0))
+    r = make_reaction("zero", 1)
+    D = (ctypes.c_double * 1)(1.0)
+    U = torch.zeros(8200 * 3, device="cuda", dtype=torch.float32)
+    st = lib.etd_step_noalloc(ctypes.byref(g), D, ctypes.byref(r), 0.01, B.ETD_FP32,
+                              ctypes.c_void_p(U.data_ptr()), 0.0, None)
+    assert st == B.ETD_ERR_UNSUPPORTED
+    assert b"does not fit one block" in lib.etd_last_error(None)
 
 
 def test_noalloc_rejects_oversize_problem():
