@@ -328,14 +328,18 @@ bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster) {
   return P.smem <= 200 * 1024;
 }
 
-// Circulant kernels (etd_circ.cuh) for a periodic axis: p = m L with m a
-// power of two.  First axis: lanes along the line, one block of
-// max(m, 256) threads holding 256 / m lines (m <= 512).  Problems with a
+// Circulant kernels (etd_circ.cuh) for a periodic axis.  First axis: p = m L
+// with m a power of two, lanes along the line, one block of max(m, 256)
+// threads holding 256 / m lines (m <= 512).  Strided axes: 32 lines (lanes)
+// times wb chunks (warps) per block, p = cs wb L with cs <= 16 blocks per
+// line forming a cluster; the stride a multiple of 32.  Problems with a
 // manufactured source are left to the table kernels.
-bool plan_axis_circ(Instance &I, int a, int L) {
+bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc);
+bool plan_axis_circ(Instance &I, int a, int L, int wb, int nc) {
+  if (a > 0) return plan_axis_circ_strided(I, a, L, wb, nc);
   AxisPlan &P = I.plan[a];
   const long long n = I.n[a];
-  if (I.bc[a] != BC_PERIODIC || a != 0) return false;
+  if (I.bc[a] != BC_PERIODIC) return false;
   if (I.rkind == ETD_REACTION_ENZYME && I.rp[0] != 0.0) return false;
   if (I.real_bytes == 4 ? (L != 8 && L != 16) : (L != 4 && L != 8)) return false;
   if (n % L != 0) return false;
@@ -361,6 +365,73 @@ bool plan_axis_circ(Instance &I, int a, int L) {
   P.nblocks = (int)((P.nlines + P.nlb - 1) / P.nlb);
   P.smem = circ_first_smem(I.S, L, P.nthreads, P.m, P.nlb, I.real_bytes);
   return P.smem <= 200 * 1024;
+}
+
+bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc) {
+  AxisPlan &P = I.plan[a];
+  const long long n = I.n[a];
+  if (I.bc[a] != BC_PERIODIC || a == 0) return false;
+  if (I.rkind == ETD_REACTION_ENZYME && I.rp[0] != 0.0) return false;
+  // (chunks, lines) per block with compiled kernels
+  const bool ok32 = L == 16 && ((wb == 16 && (nc == 16 || nc == 32)) || (wb == 8 && nc == 32) || (wb == 32 && nc == 16));
+  const bool ok64 = L == 8 && ((wb == 8 && nc == 32) || (wb == 16 && nc == 16));
+  if (I.real_bytes == 4 ? !ok32 : !ok64) return false;
+  long long st = 1;
+  for (int b = 0; b < a; ++b) st *= I.n[b];
+  if (st % nc != 0 || n % ((long long)wb * L) != 0) return false;
+  const long long cs = n / ((long long)wb * L);
+  if (cs < 1 || cs > ETD_MAX_CLUSTER) return false;
+  P.L = L;
+  P.m = (int)(n / L);
+  P.kind = (a == I.dim - 1) ? SWEEP_LAST : SWEEP_MIDDLE;
+  P.st = st;
+  P.nlines = I.N / n;
+  P.pitch = 1;
+  P.pk = 1;
+  P.sp = StagePlan{};
+  P.mx = wb;
+  P.nseg = (int)cs;
+  P.cluster = cs > 1;
+  P.circ = true;
+  P.nlb = nc;
+  P.nthreads = wb * nc;
+  P.nlo_blocks = (int)(st / nc);
+  const long long ngroups = (long long)P.nlo_blocks * (I.N / (st * n));
+  if (ngroups > INT_MAX / 2) return false;
+  P.smem = circ_strided_smem(I.S, L, wb, nc, I.real_bytes);
+  if (P.smem > 227 * 1024) return false;
+  // persistent launch: as many clusters (cs > 1) or blocks as the device holds
+  // at once, each walking the line groups
+  int ncl = 0;
+  cudaError_t e;
+  if (I.real_bytes == 8) {
+    CircArgs<double> C{};
+    C.cs = (int)cs;
+    C.wb = wb;
+    C.ncol = nc;
+    e = circ_cluster_capacity(C, I.S, L, P.kind, P.nthreads, P.smem, ncl);
+  } else {
+    CircArgs<float> C{};
+    C.cs = (int)cs;
+    C.wb = wb;
+    C.ncol = nc;
+    e = circ_cluster_capacity(C, I.S, L, P.kind, P.nthreads, P.smem, ncl);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cs == 1) {  // the capacity query gave blocks per SM
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ncl *= nsm;
+  }
+  if (ncl < 1) return false;
+  P.nblocks = (int)(std::min<long long>(ncl, ngroups) * cs);
+  return true;
 }
 
 // a cluster-segmented plan of axis a can launch on the current device
@@ -513,17 +584,19 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
     for (int s = 0; s < I.S; ++s)
       for (int g = 0; g < 3; ++g) {
         circ_coeffs((I.k / gammas[g]) * I.D[s] / (h * h), (int)I.n[a], P.L, H[s][g]);
-        per = std::max(per, H[s][g].lpow.size());
+        per = std::max(per, H[s][g].lpow.size() + H[s][g].kch.size());
       }
     const size_t rb = I.real_bytes;
     std::vector<unsigned char> img((size_t)I.S * 3 * per * rb, 0);
     for (int s = 0; s < I.S; ++s)
       for (int g = 0; g < 3; ++g)
-        for (size_t i = 0; i < H[s][g].lpow.size(); ++i) {
+        for (size_t i = 0; i < H[s][g].lpow.size() + H[s][g].kch.size(); ++i) {
+          const size_t nl = H[s][g].lpow.size();
+          const double x = i < nl ? H[s][g].lpow[i] : H[s][g].kch[i - nl];
           unsigned char *d = img.data() + ((size_t)(s * 3 + g) * per + i) * rb;
-          if (rb == 8) memcpy(d, &H[s][g].lpow[i], 8);
+          if (rb == 8) memcpy(d, &x, 8);
           else {
-            const float v = (float)H[s][g].lpow[i];
+            const float v = (float)x;
             memcpy(d, &v, 4);
           }
         }
@@ -543,6 +616,10 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
       C.lpb = P.nlb;
       C.ncol = P.nlb;
       C.nlo_blocks = P.nlo_blocks;
+      C.cs = P.circ && a > 0 ? P.nseg : 1;
+      C.wb = P.mx;
+      C.ngroups = (int)((long long)P.nlo_blocks * (I.N / (P.st * I.n[a])));
+      C.lst = P.st * I.n[a];
       C.rkind = I.rkind;
       C.kR = (R)I.k;
       C.half_kR = (R)(0.5 * I.k);
@@ -551,9 +628,12 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
         C.cP[s] = (R)(1.0 / H[s][0].alpha);
         C.cT[s] = (R)(9.0 / H[s][1].alpha);
         C.cS[s] = (R)(8.0 / H[s][2].alpha);
+        C.iaT[s] = (R)(1.0 / H[s][1].alpha);
+        C.iaS[s] = (R)(1.0 / H[s][2].alpha);
         for (int g = 0; g < 3; ++g) {
           circ_to_args<R>(H[s][g], C.mat[s][g]);
           C.lpow[s][g] = (const R *)((unsigned char *)I.circ_tables[a] + (size_t)(s * 3 + g) * per * rb);
+          C.kch[s][g] = C.lpow[s][g] + H[s][g].lpow.size();
         }
       }
     };
@@ -788,7 +868,8 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
   // ETD_TILES="L:nlb:kernel[:pack],..." (one entry per axis; kernel 0
   // register, 1 staged, 2 tile with nlb lines per block, 3 segmented register
   // kernel with the fourth field = chunks per segment, 4 the same as one
-  // cluster launch, 5 circulant kernel of a periodic axis) forces tile shapes, e.g. to reproduce an autotuned
+  // cluster launch, 5 circulant kernel of a periodic axis with nlb = chunks
+  // and the fourth field = lines per block on strided axes) forces tile shapes, e.g. to reproduce an autotuned
   // configuration in a profiler run
   const char *forced = std::getenv("ETD_TILES");
   for (int a = 0; a < I.dim; ++a) {
@@ -801,7 +882,7 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
         if (p) ++p;
       }
       if (p && sscanf(p, "%d:%d:%d:%d", &fl, &fn, &fs, &fp) >= 3 && (fl == 4 || fl == 8 || fl == 16)) {
-        const bool ok = fs == 5   ? plan_axis_circ(I, a, fl)
+        const bool ok = fs == 5   ? plan_axis_circ(I, a, fl, fn > 0 ? fn : 16, fp > 1 ? fp : 32)
                         : fs == 4 ? plan_axis_seg(I, a, fl, fn, fp, true) && cluster_plan_fits(I, a)
                         : fs == 3 ? plan_axis_seg(I, a, fl, fn, fp, false)
                         : fs == 2 ? plan_axis_tile(I, a, fl, fn, fp)

@@ -22,10 +22,83 @@ cudaError_t launch_first(const CircArgs<R> &a, int nthreads, size_t smem, int nb
   return cudaGetLastError();
 }
 
+template <typename R, int S, int L, int KIND, int WB, int NC>
+cudaError_t launch_strided(const CircArgs<R> &a, size_t smem, int nblocks, cudaStream_t s, int *capacity) {
+  auto fn = circ_strided_kernel<R, S, L, KIND, WB, NC>;
+  cudaError_t e = ensure_dyn_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nblocks, 1, 1);
+  cfg.blockDim = dim3(WB * NC, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  int na = 0;
+  if (a.cs > 1) {
+    if (a.cs > 8) {
+      e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    na = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  if (capacity) {
+    *capacity = 0;
+    cfg.gridDim = dim3((unsigned)(a.cs > 1 ? a.cs : 1), 1, 1);
+    if (a.cs <= 1) {
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, WB * NC, smem);
+      *capacity = per_sm;
+      return e;
+    }
+    return cudaOccupancyMaxActiveClusters(capacity, fn, &cfg);
+  }
+  e = cudaLaunchKernelEx(&cfg, fn, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// strided sweeps, (chunks, lines) per block: FP32 (L = 16) 16 x 16, 16 x 32,
+// 8 x 32, 32 x 16; FP64 (L = 8) 8 x 32, 16 x 16
+template <typename R>
+cudaError_t strided_any(const CircArgs<R> &a, int nspecies, int L, int kind, size_t smem, int nblocks,
+                        cudaStream_t s, int *capacity) {
+  constexpr int LL = sizeof(R) == 4 ? 16 : 8;
+  if (L != LL) return cudaErrorInvalidValue;
+  const int key = (a.wb * 100 + a.ncol) * 100 + nspecies * 10 + kind;
+#define ETD_CIRC_STRIDED(WB_, NC_)                                                                         \
+  case (WB_ * 100 + NC_) * 100 + 11: return launch_strided<R, 1, LL, SWEEP_MIDDLE, WB_, NC_>(a, smem, nblocks, s, capacity); \
+  case (WB_ * 100 + NC_) * 100 + 12: return launch_strided<R, 1, LL, SWEEP_LAST, WB_, NC_>(a, smem, nblocks, s, capacity);   \
+  case (WB_ * 100 + NC_) * 100 + 21: return launch_strided<R, 2, LL, SWEEP_MIDDLE, WB_, NC_>(a, smem, nblocks, s, capacity); \
+  case (WB_ * 100 + NC_) * 100 + 22: return launch_strided<R, 2, LL, SWEEP_LAST, WB_, NC_>(a, smem, nblocks, s, capacity);
+  if constexpr (sizeof(R) == 4) {
+    switch (key) {
+      ETD_CIRC_STRIDED(16, 16)
+      ETD_CIRC_STRIDED(16, 32)
+      ETD_CIRC_STRIDED(8, 32)
+      ETD_CIRC_STRIDED(32, 16)
+      default: break;
+    }
+  } else {
+    switch (key) {
+      ETD_CIRC_STRIDED(8, 32)
+      ETD_CIRC_STRIDED(16, 16)
+      default: break;
+    }
+  }
+#undef ETD_CIRC_STRIDED
+  return cudaErrorInvalidValue;
+}
+
 template <typename R>
 cudaError_t launch_any(const CircArgs<R> &a, int nspecies, int L, int kind, int nthreads, size_t smem, int nblocks,
                        cudaStream_t s) {
-  if (kind != SWEEP_FIRST) return cudaErrorNotSupported;
+  if (kind != SWEEP_FIRST) return strided_any<R>(a, nspecies, L, kind, smem, nblocks, s, nullptr);
   const int key = nspecies * 100 + L;
   if constexpr (sizeof(R) == 4) {
     switch (key) {
@@ -55,6 +128,17 @@ cudaError_t launch_circ(const CircArgs<float> &a, int nspecies, int L, int kind,
 cudaError_t launch_circ(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                         int nblocks, cudaStream_t s) {
   return launch_any<double>(a, nspecies, L, kind, nthreads, smem, nblocks, s);
+}
+
+cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                  int &nclusters) {
+  (void)nthreads;
+  return strided_any<float>(a, nspecies, L, kind, smem, 1, nullptr, &nclusters);
+}
+cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                  int &nclusters) {
+  (void)nthreads;
+  return strided_any<double>(a, nspecies, L, kind, smem, 1, nullptr, &nclusters);
 }
 
 }  // namespace etd

@@ -19,6 +19,7 @@
 // U_n + k F(U_n)) share the two rounds; results leave as 32-byte stores.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -347,6 +348,410 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
 #pragma unroll
     for (int t = 0; t < L; t += 32 / (int)sizeof(R)) st32(o + t, zt + t);
   }
+}
+
+// ===================================================== strided axes
+//
+// Lines along a strided axis (MIDDLE: axis 1 of a 3D grid, LAST: the last
+// axis).  A block covers 32 neighbouring lines (lanes: coalesced 128-byte row
+// segments) times WB chunks of L positions (warps); a line longer than WB L
+// is split over cs blocks that form one thread-block cluster.  The block's
+// input fields are staged in shared memory with cp.async ([row][32 lines],
+// conflict-free), so the passes keep only running values in registers.
+// Every group of solves (one right-hand side field each) is exchanged once:
+//   chunks of the block: each thread composes the zero-carry summaries of
+//     the chunks before it (forward prefix) and after it (backward composite
+//     W, with the forward coupling K) from shared memory;
+//   blocks of the line: the block composites are published in shared memory,
+//     one cluster barrier, one warp per solve reads the cs composites through
+//     distributed shared memory, closes the line cyclically and hands the
+//     block's carries to its threads.
+// MIDDLE: R_2 on c_U, R_2 on c_f, P_2 on w (three groups, in place).
+// LAST: U* = P_d w; F(U*); f1 = 9 c_U + 2k c_f + k F*, f2 = 8 c_U + 3k/2 c_f
+//       + k/2 F* (written over the staged c_U, c_f); U_{n+1} = T_d f1 - S_d f2.
+
+namespace circ {
+
+// Exchange of NG solves of this thread's chunk j of column c (block rank,
+// cs blocks; warp w, half h of a warp that holds 32 / NC chunks):
+// F[q], W[q] -> carries Yc[q] (y before the chunk), Zc[q] (z after it).
+// xF, xW: [NG][max(WB, cs)][NC] (after the chunk compositions they take the
+// gathered block composites); blk: [2][NG][NC] published composites;
+// car: [2][NG][NC].  Loops over chunks and blocks run unrolled over the
+// solves only, so each step keeps NG values in flight.
+template <typename R, int WB, int NC, int NG, typename MatIdx>
+__device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi, const R (&F)[NG], const R (&W)[NG],
+                                                 R (&Yc)[NG], R (&Zc)[NG], R *xF, R *xW, R *blk, R *car, int j,
+                                                 int c, int w, int h, int rank) {
+  constexpr int HP = 32 / NC, NW = WB / HP;
+  namespace cg = cooperative_groups;
+  const int cs = A.cs;
+  const int XS = WB > cs ? WB : cs;  // row count of xF / xW
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    xF[(q * XS + j) * NC + c] = F[q];
+    xW[(q * XS + j) * NC + c] = W[q];
+  }
+  __syncthreads();
+  R PF[NG], Ws[NG], LM[NG];
+  const R *Kq[NG];
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    LM[q] = A.mat[mi(q) / 3][mi(q) % 3].lamL;
+    Kq[q] = A.kch[mi(q) / 3][mi(q) % 3];
+    PF[q] = Ws[q] = R(0);
+  }
+  // chunks of the block: forward prefix before j, backward composite after j
+#pragma unroll 1
+  for (int i = 0; i < j; ++i)
+#pragma unroll
+    for (int q = 0; q < NG; ++q) PF[q] = fma(LM[q], PF[q], xF[(q * XS + i) * NC + c]);
+#pragma unroll 1
+  for (int i = WB - 1; i > j; --i)
+#pragma unroll
+    for (int q = 0; q < NG; ++q)
+      Ws[q] = fma(LM[q], fma(Kq[q][WB - 1 - i], xF[(q * XS + i) * NC + c], Ws[q]), xW[(q * XS + i) * NC + c]);
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    if (j == 0) blk[(NG + q) * NC + c] = fma(LM[q], fma(Kq[q][WB - 1], F[q], Ws[q]), W[q]);
+    if (j == WB - 1) blk[q * NC + c] = fma(LM[q], PF[q], F[q]);
+  }
+  if (cs > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();  // composites published (and xF / xW free: every thread has read them)
+    for (int b = w * HP + h; b < cs; b += NW * HP) {  // spread over the warps: block b's composites
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        xF[(q * XS + b) * NC + c] = *cl.map_shared_rank(blk + q * NC + c, b);
+        xW[(q * XS + b) * NC + c] = *cl.map_shared_rank(blk + (NG + q) * NC + c, b);
+      }
+    }
+  } else {
+    __syncthreads();
+    if (j == 0) {  // (w = 0, h = 0)
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        xF[(q * XS) * NC + c] = blk[q * NC + c];
+        xW[(q * XS) * NC + c] = blk[(NG + q) * NC + c];
+      }
+    }
+  }
+  __syncthreads();
+  if (w < NG) {
+    // warp q: the line's cyclic closure and this block's carries for solve q
+    // (with NC = 16 both halves of the warp compute; half 0 writes)
+    const int q = w;
+    const int sg = mi(q);
+    const CircMat<R> &M = A.mat[sg / 3][sg % 3];
+    const R *K = A.kch[sg / 3][sg % 3], *lp = A.lpow[sg / 3][sg % 3];
+    const R LB = lp[WB];  // Lambda^WB
+    const R *gF = xF + (size_t)q * XS * NC + c, *gW = xW + (size_t)q * XS * NC + c;
+    R ftot = R(0), pfb = R(0), fr = R(0);
+#pragma unroll 1
+    for (int b = 0; b < cs; ++b) {
+      const R f = gF[b * NC];
+      if (b == rank) {
+        pfb = ftot;
+        fr = f;
+      }
+      ftot = fma(LB, ftot, f);
+    }
+    R wl = R(0), wsr = R(0);
+#pragma unroll 1
+    for (int b = cs - 1; b >= 0; --b) {
+      if (b == rank) wsr = wl;  // composite of the blocks after this one
+      wl = fma(LB, fma(K[(cs - 1 - b) * WB], gF[b * NC], wl), gW[b * NC]);
+    }
+    const R y0 = ftot * M.inv1m;
+    const R z0 = fma(K[A.m], y0, wl) * M.inv1m;
+    const R ycb = fma(lp[rank * WB], y0, pfb);
+    const R ycn = fma(LB, ycb, fr);
+    const R zcb = fma(lp[(cs - 1 - rank) * WB], z0, fma(K[(cs - 1 - rank) * WB], ycn, wsr));
+    if (h == 0) {
+      car[q * NC + c] = ycb;
+      car[(NG + q) * NC + c] = zcb;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    const int sg = mi(q);
+    const R *K = Kq[q], *lp = A.lpow[sg / 3][sg % 3];
+    const R ycb = car[q * NC + c], zcb = car[(NG + q) * NC + c];
+    Yc[q] = fma(lp[j], ycb, PF[q]);
+    const R yn = fma(LM[q], Yc[q], F[q]);
+    Zc[q] = fma(lp[WB - 1 - j], zcb, fma(K[WB - 1 - j], yn, Ws[q]));
+  }
+}
+
+}  // namespace circ
+
+template <typename R, int S, int L, int KIND, int WB, int NC>
+__global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_constant__ CircArgs<R> A) {
+  using namespace circ;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char circ_smem[];
+  constexpr int ROWS = WB * L;           // rows of the line in this block
+  constexpr int VW = 16 / sizeof(R);
+  constexpr int HP = 32 / NC;            // chunks per warp (lanes: NC columns x HP chunks)
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int c = lane % NC, h = lane / NC, j = w * HP + h;  // column, half, chunk
+  const int cs = A.cs;
+  const int rank = (int)(blockIdx.x % (unsigned)cs);
+  // persistent: cluster (or block) cid walks the line groups cid, cid + ncl, ...
+  const int ncl = (int)(gridDim.x / (unsigned)cs), cid = (int)(blockIdx.x / (unsigned)cs);
+  const long long st = A.st;
+  const int ngroups = A.ngroups;
+  const unsigned nlob = (unsigned)A.nlo_blocks;
+  auto group_base = [&](int g) -> long long {  // row 0, lane 0 of this block's tile of group g
+    const unsigned hi = (unsigned)g / nlob, lo = (unsigned)g - hi * nlob;
+    return (long long)lo * NC + ((long long)rank * ROWS) * st + (long long)hi * A.lst;
+  };
+  // tile [3 fields][S][ROWS * NC]: row t of chunk j at ((j / HP) L + t) 32 + (j % HP) NC,
+  // so a warp's HP chunks read one 32-wide row (conflict-free)
+  R *tile = reinterpret_cast<R *>(circ_smem);
+  constexpr int XS = WB > 16 ? WB : 16;         // exchange rows (chunks of a block, or gathered blocks)
+  R *xF = tile + (size_t)3 * S * ROWS * NC;    // [2S][XS][NC] (an exchange of NG solves uses [NG][max(WB, cs)])
+  R *xW = xF + (size_t)2 * S * XS * NC;
+  R *blk = xW + (size_t)2 * S * XS * NC;       // [3 exchanges][2][2S][NC]
+  R *car = blk + (size_t)3 * 2 * 2 * S * NC;   // [2][2S][NC]
+  auto Tf = [&](int f, int s) -> R * { return tile + (size_t)(f * S + s) * ROWS * NC; };
+  // this thread's column of its chunk in field f, species s (row t at + t * 32)
+  auto Tc = [&](int f, int s) -> R * { return Tf(f, s) + (w * L) * 32 + h * NC + c; };
+  // stage field fld of group g into its buffer (cp.async, 16 bytes); always
+  // one commit group, empty past the last group, so the wait counts hold
+  auto stage = [&](int fld, int g) {
+    if (g < ngroups) {
+      constexpr int PER_ROW = NC / VW;  // 16-byte pieces per row segment
+      const long long gb = group_base(g);
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+#pragma unroll 1
+        for (int k = tid; k < ROWS * PER_ROW; k += WB * NC) {
+          const int row = k / PER_ROW, col = (k % PER_ROW) * VW;
+          const int cj = row / L, ct = row - cj * L;
+          cp_async16(Tf(fld, s) + ((cj / HP) * L + ct) * 32 + (cj % HP) * NC + col,
+                     A.in[fld] + s * A.N + gb + (long long)row * st + col);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  const int r0 = j * L;  // this thread's first row in the tile
+
+  if constexpr (KIND == SWEEP_MIDDLE) {
+    // fields in order c_U, c_f, w; each is exchanged on its own, and its
+    // buffer refilled with the next group's field right after its last read
+    stage(0, cid);
+    stage(1, cid);
+    stage(2, cid);
+#pragma unroll 1
+    for (int g = cid; g < ngroups; g += ncl) {
+      const long long mybase = group_base(g) + (long long)r0 * st + c;
+      // R_2 = 9 T - 8 S on c_U, then on c_f
+#pragma unroll 1
+      for (int fld = 0; fld < 2; ++fld) {
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        __syncthreads();
+        R F[2 * S], W[2 * S], Yc[2 * S], Zc[2 * S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
+          R y0 = R(0), w0 = R(0), y1 = R(0), w1 = R(0);
+          const R *col = Tc(fld, s);
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            const R b = col[t * 32];
+            y0 = fma(MT.lam, y0, b);
+            w0 = fma(MT.pw[t], y0, w0);
+            y1 = fma(MS.lam, y1, b);
+            w1 = fma(MS.pw[t], y1, w1);
+          }
+          F[2 * s] = y0; W[2 * s] = w0;
+          F[2 * s + 1] = y1; W[2 * s + 1] = w1;
+        }
+        auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
+        strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)fld * 2 * 2 * S * NC, car, j,
+                                       c, w, h, rank);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
+          const R *col = Tc(fld, s);
+          R *out = A.out[fld] + s * A.N + mybase;
+          R zt[L], ys[L];
+          R y = Yc[2 * s], y2 = Yc[2 * s + 1];
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            const R b = col[t * 32];
+            y = fma(MT.lam, y, b);
+            zt[t] = y;
+            y2 = fma(MS.lam, y2, b);
+            ys[t] = y2;
+          }
+          R z = Zc[2 * s], z2 = Zc[2 * s + 1];
+#pragma unroll
+          for (int t = L - 1; t >= 0; --t) {
+            z = fma(MT.lam, z, zt[t]);
+            z2 = fma(MS.lam, z2, ys[t]);
+            out[(long long)t * st] = fma(A.cT[s], z, -A.cS[s] * z2);  // R = 9T - 8S
+          }
+        }
+        __syncthreads();  // every thread is done with this field's buffer
+        stage(fld, g + ncl);
+      }
+      // P_2 on w
+      {
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        __syncthreads();
+        R F[S], W[S], Yc[S], Zc[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &M = A.mat[s][0];
+          R y = R(0), w = R(0);
+          const R *col = Tc(2, s);
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            y = fma(M.lam, y, col[t * 32]);
+            w = fma(M.pw[t], y, w);
+          }
+          F[s] = y;
+          W[s] = w;
+        }
+        auto mi = [&](int q) { return q * 3; };
+        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * 2 * S * NC, car, j, c, w,
+                                   h, rank);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &M = A.mat[s][0];
+          const R *col = Tc(2, s);
+          R *out = A.out[2] + s * A.N + mybase;
+          R ys[L];
+          R y = Yc[s];
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            y = fma(M.lam, y, col[t * 32]);
+            ys[t] = y;
+          }
+          R z = Zc[s];
+#pragma unroll
+          for (int t = L - 1; t >= 0; --t) {
+            z = fma(M.lam, z, ys[t]);
+            out[(long long)t * st] = A.cP[s] * z;
+          }
+        }
+        __syncthreads();
+        stage(2, g + ncl);
+      }
+    }
+  } else {
+    // buffers: 2 = w (phase A), 0 = c_U, 1 = c_f (phase C, overwritten by f1, f2)
+    stage(2, cid);
+    stage(0, cid);
+    stage(1, cid);
+#pragma unroll 1
+    for (int g = cid; g < ngroups; g += ncl) {
+      const long long mybase = group_base(g) + (long long)r0 * st + c;
+      // ---- phase A: U* = P_d w
+      asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // w of g (c_U, c_f may still be in flight)
+      __syncthreads();
+      R Ustar[S][L];
+      {
+        R F[S], W[S], Yc[S], Zc[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &M = A.mat[s][0];
+          const R *col = Tc(2, s);
+          R y = R(0), w = R(0);
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            y = fma(M.lam, y, col[t * 32]);
+            w = fma(M.pw[t], y, w);
+          }
+          F[s] = y;
+          W[s] = w;
+        }
+        auto mi = [&](int q) { return q * 3 + 0; };
+        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk, car, j, c, w, h, rank);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const CircMat<R> &M = A.mat[s][0];
+          const R *col = Tc(2, s);
+          R y = Yc[s];
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            y = fma(M.lam, y, col[t * 32]);
+            Ustar[s][t] = y;
+          }
+          R z = Zc[s];
+#pragma unroll
+          for (int t = L - 1; t >= 0; --t) {
+            z = fma(M.lam, z, Ustar[s][t]);
+            Ustar[s][t] = A.cP[s] * z;
+          }
+        }
+      }
+      __syncthreads();  // w of g fully read: refill with the next group's
+      stage(2, g + ncl);
+      // ---- F(U*, t_{n+1}); f1, f2 over the staged c_U, c_f; summaries of T f1, S f2
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // c_U, c_f of g
+      __syncthreads();
+      R F[2 * S], W[2 * S], Yc[2 * S], Zc[2 * S];
+#pragma unroll
+      for (int q = 0; q < 2 * S; ++q) F[q] = W[q] = R(0);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        R u[S], fr[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u[s] = Ustar[s][t];
+        reaction<R, S>(A, u, fr);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          R *cu = Tc(0, s) + t * 32, *cf = Tc(1, s) + t * 32;
+          const R a = *cu, b = *cf;
+          const R f1 = fma(A.kR, fr[s], fma(R(2) * A.kR, b, R(9) * a));
+          const R f2 = fma(A.half_kR, fr[s], fma(R(1.5) * A.kR, b, R(8) * a));
+          *cu = f1;
+          *cf = f2;
+          const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
+          F[2 * s] = fma(MT.lam, F[2 * s], f1);
+          W[2 * s] = fma(MT.pw[t], F[2 * s], W[2 * s]);
+          F[2 * s + 1] = fma(MS.lam, F[2 * s + 1], f2);
+          W[2 * s + 1] = fma(MS.pw[t], F[2 * s + 1], W[2 * s + 1]);
+        }
+      }
+      auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
+      strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * S * NC, car, j, c, w,
+                                     h, rank);
+      // ---- U_{n+1} = T_d f1 - S_d f2
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
+        const R *c1 = Tc(0, s), *c2 = Tc(1, s);
+        R zt[L], ys[L];
+        R y = Yc[2 * s], y2 = Yc[2 * s + 1];
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          y = fma(MT.lam, y, c1[t * 32]);
+          zt[t] = y;
+          y2 = fma(MS.lam, y2, c2[t * 32]);
+          ys[t] = y2;
+        }
+        R z = Zc[2 * s], z2 = Zc[2 * s + 1];
+        R *out = A.out[0] + s * A.N + mybase;
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+          z = fma(MT.lam, z, zt[t]);
+          z2 = fma(MS.lam, z2, ys[t]);
+          out[(long long)t * st] = fma(A.iaT[s], z, -A.iaS[s] * z2);
+        }
+      }
+      __syncthreads();  // f1, f2 of g fully read: refill with the next group's c_U, c_f
+      stage(0, g + ncl);
+      stage(1, g + ncl);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  // no block of a cluster leaves while another may still read its shared memory
+  if (cs > 1) cg::this_cluster().sync();
 }
 
 }  // namespace etd

@@ -55,19 +55,25 @@ template <typename R> struct CircArgs {
   int lpb;            // contiguous sweeps: lines per block
   int ncol;           // strided sweeps: lines (columns) per block
   int nlo_blocks;     // strided sweeps: blocks along the contiguous line index
+  int cs;             // strided sweeps: blocks per line (thread-block cluster size; 1: whole lines)
+  int wb;             // strided sweeps: chunks (warps) per block
+  int ngroups;        // strided sweeps: groups of 32 neighbouring lines
+  long long lst;      // strided sweeps: st * p, the stride of the slow line index
   int rkind;          // reaction kind
   R kR;               // k
   R rpR[8];           // reaction parameters
   R half_kR;          // k / 2
   R cT[MAX_SPECIES], cS[MAX_SPECIES], cP[MAX_SPECIES];  // 9/alpha_T, 8/alpha_S, 1/alpha_P
+  R iaT[MAX_SPECIES], iaS[MAX_SPECIES];                  // 1/alpha_T, 1/alpha_S (last sweep: T f1 - S f2)
   CircMat<R> mat[MAX_SPECIES][3];                        // [species][0: P, 1: T, 2: S]
-  const R *lpow[MAX_SPECIES][3];                         // Lambda^i, i = 0 .. m (device)
+  const R *lpow[MAX_SPECIES][3];                         // Lambda^i, i = 0 .. m + 32 (device)
+  const R *kch[MAX_SPECIES][3];                          // K_{nL} = sum_{s<nL} lambda^{2s+1}, n = 0 .. m
 };
 
 // host-side coefficients of one matrix (FP64)
 struct CircHost {
   double lam = 0, alpha = 1, lamL = 0, kap = 0, inv1m = 1;
-  std::vector<double> pw, lpow, sc, sw;
+  std::vector<double> pw, lpow, kch, sc, sw;
 };
 
 inline void circ_coeffs(double c, int p, int L, CircHost &H) {
@@ -90,6 +96,10 @@ inline void circ_coeffs(double c, int p, int L, CircHost &H) {
     H.lpow[i] = r;
     r *= H.lamL;
   }
+  // K_{nL}: effect of the forward carry entering n chunks on the backward
+  // value at their start (K_{(a+b)L} = K_{aL} + Lambda^{2a} K_{bL})
+  H.kch.assign((size_t)m + 1, 0.0);
+  for (int n = 1; n <= m; ++n) H.kch[n] = H.kch[n - 1] + H.kap * std::pow(H.lamL, 2.0 * (n - 1));
   H.sc.assign(5, 0.0);
   H.sw.assign(5, 0.0);
   for (int k = 0; k < 5; ++k) {
@@ -115,6 +125,22 @@ cudaError_t launch_circ(const CircArgs<float> &a, int nspecies, int L, int kind,
                         int nblocks, cudaStream_t s);
 cudaError_t launch_circ(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                         int nblocks, cudaStream_t s);
+
+// strided sweeps: NC lines x WB chunks per block (WB NC threads); the tile
+// holds the 3 input fields of every species for the block's WB L rows, then
+// the exchange buffers of up to 2 s solves, the block summaries published to
+// the cluster (one set per exchange) and the block carries
+inline size_t circ_strided_smem(int nspecies, int L, int WB, int NC, size_t real_bytes) {
+  const size_t tile = (size_t)3 * nspecies * WB * L * NC * real_bytes;
+  const size_t exch = (size_t)2 * 2 * nspecies * (WB > 16 ? WB : 16) * NC * real_bytes;
+  const size_t blk = (size_t)3 * 2 * 2 * nspecies * NC * real_bytes;
+  const size_t car = (size_t)2 * 2 * nspecies * NC * real_bytes;
+  return tile + exch + blk + car;
+}
+cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                  int &nclusters);
+cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                  int &nclusters);
 
 // shared memory of a contiguous circulant sweep block of nthreads threads
 inline size_t circ_first_smem(int nspecies, int L, int nthreads, int m, int lpb, size_t real_bytes) {

@@ -16,7 +16,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
 bool plan_axis_tile(Instance &I, int a, int L, int NLB, int pk);
 bool plan_axis_seg(Instance &I, int a, int L, int nlb, int mx, bool cluster);
 bool cluster_plan_fits(const Instance &I, int a);
-bool plan_axis_circ(Instance &I, int a, int L);
+bool plan_axis_circ(Instance &I, int a, int L, int wb, int nc);
 etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a);
 }  // namespace etd
 
@@ -35,7 +35,7 @@ struct Cand {
 };
 
 bool plan_cand(Instance &I, int a, const Cand &c) {
-  if (c.circ) return plan_axis_circ(I, a, c.L);
+  if (c.circ) return plan_axis_circ(I, a, c.L, c.nlb, c.pack);
   if (c.seg) return plan_axis_seg(I, a, c.L, c.nlb, c.seg, c.cluster) && cluster_plan_fits(I, a);
   if (c.tile) return plan_axis_tile(I, a, c.L, c.nlb, c.pack);
   return plan_axis_ex(I, a, c.L, ETD_MAX_BLOCK_THREADS, c.nlb, c.reg, c.pack);
@@ -93,11 +93,15 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
       if (I.real_bytes == 4 && L >= 8)
         for (int nlb : {16, 32})
           for (int pk : {1, 2}) cands.push_back({L, nlb, false, pk, true});  // tile kernels
-      if (I.bc[a] == 2) {  // periodic axis: circulant kernels (planner checks the shape)
-        Cand c{L, 0, true, 1};
-        c.circ = true;
-        cands.push_back(c);
-      }
+      if (I.bc[a] == 2)  // periodic axis: circulant kernels (planner checks the shape; nlb = chunks per block)
+        for (int wb : {8, 16, 32})
+          for (int nc : {16, 32}) {  // chunks and lines per block (first axis: one shape)
+            if (a == 0 && (wb != 16 || nc != 32)) continue;
+            if (wb * nc > 512) continue;
+            Cand c{L, wb, true, nc};
+            c.circ = true;
+            cands.push_back(c);
+          }
       if ((I.n[a] + L - 1) / L > 32)  // long lines: segmented blocks (planner checks the shape)
         for (int mx : {16, 32})
           for (int nlb : {8, 16, 32})
@@ -109,6 +113,10 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
               keep.sp.staged == 2, keep.nseg > 1 ? keep.mx : 0, keep.cluster, keep.circ};
     if (pick.tile) pick.nlb = keep.nlb * keep.pk;
     if (pick.seg) pick.nlb = keep.nlb;
+    if (pick.circ) {  // circulant plans: chunks and lines per block
+      pick.nlb = keep.mx;
+      pick.pack = keep.nlb;
+    }
     for (const Cand &c : cands) {
       if (!plan_cand(I, a, c)) continue;
       if (c.reg && I.plan[a].sp.staged) continue;
