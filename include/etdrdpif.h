@@ -115,6 +115,8 @@ typedef struct {
   int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
                                     (lines_per_block then counts pairs), 1: one line per thread;
                                     segmented kernels: chunks per segment */
+  int32_t grid_blocks[3];        /* blocks of each axis's sweep launch (persistent circulant
+                                    sweeps: the blocks resident at once) */
 } etd_info;
 
 /* Create a context for one problem.  Validates every argument

@@ -38,7 +38,7 @@ class etd_info(ctypes.Structure):
                 ("npoints", ctypes.c_int64), ("state_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
                 ("algorithmic_bytes", ctypes.c_int64), ("launches_per_step", ctypes.c_int32),
                 ("chunk", ctypes.c_int32 * 3), ("lines_per_block", ctypes.c_int32 * 3),
-                ("staged", ctypes.c_int32 * 3), ("pack", ctypes.c_int32 * 3)]
+                ("staged", ctypes.c_int32 * 3), ("pack", ctypes.c_int32 * 3), ("grid_blocks", ctypes.c_int32 * 3)]
 
 
 class EtdError(RuntimeError):

@@ -143,7 +143,7 @@ class EtdRdpIf:
     def info(self) -> dict:
         inf = B.etd_info()
         B.check(self.lib.etd_get_info(self.ctx, ctypes.byref(inf)), self.ctx)
-        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block", "staged", "pack") else getattr(inf, f))
+        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block", "staged", "pack", "grid_blocks") else getattr(inf, f))
                 for f, _ in inf._fields_}
 
     def close(self):
@@ -208,7 +208,7 @@ class EtdEnsemble:
     def info(self) -> dict:
         inf = B.etd_info()
         B.check(self.lib.etd_get_info(self.ctx, ctypes.byref(inf)), self.ctx)
-        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block", "staged", "pack") else getattr(inf, f))
+        return {f: (list(getattr(inf, f)) if f in ("chunk", "lines_per_block", "staged", "pack", "grid_blocks") else getattr(inf, f))
                 for f, _ in inf._fields_}
 
     def close(self):

@@ -1049,6 +1049,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     info->lines_per_block[a] = I.plan[a].nlb;
     info->staged[a] = I.plan[a].circ ? 5 : I.plan[a].nseg > 1 ? (I.plan[a].cluster ? 4 : 3) : I.plan[a].sp.staged;
     info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
+    info->grid_blocks[a] = I.plan[a].nblocks;
   }
   return ETD_OK;
 }

@@ -381,9 +381,11 @@ namespace circ {
 // solves only, so each step keeps NG values in flight.
 template <typename R, int WB, int NC, int NG, typename MatIdx>
 __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi, const R (&F)[NG], const R (&W)[NG],
-                                                 R (&Yc)[NG], R (&Zc)[NG], R *xF, R *xW, R *blk, R *car, int j,
-                                                 int c, int w, int h, int rank) {
+                                                 R (&Yc)[NG], R (&Zc)[NG], R *xF, R *xW, R *blk, R *car,
+                                                 const R *tab, int j, int c, int w, int h, int rank) {
   constexpr int HP = 32 / NC, NW = WB / HP;
+  constexpr int TS = 2 * (WB + 1) + 35;  // per matrix: K_{nL}, Lambda^n (n <= WB); K, Lambda at block
+                                         // multiples (b <= 16); K_{m L}
   namespace cg = cooperative_groups;
   const int cs = A.cs;
   const int XS = WB > cs ? WB : cs;  // row count of xF / xW
@@ -398,7 +400,7 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
 #pragma unroll
   for (int q = 0; q < NG; ++q) {
     LM[q] = A.mat[mi(q) / 3][mi(q) % 3].lamL;
-    Kq[q] = A.kch[mi(q) / 3][mi(q) % 3];
+    Kq[q] = tab + mi(q) * TS;  // K_{nL} in shared memory
     PF[q] = Ws[q] = R(0);
   }
   // chunks of the block: forward prefix before j, backward composite after j
@@ -443,8 +445,8 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
     const int q = w;
     const int sg = mi(q);
     const CircMat<R> &M = A.mat[sg / 3][sg % 3];
-    const R *K = A.kch[sg / 3][sg % 3], *lp = A.lpow[sg / 3][sg % 3];
-    const R LB = lp[WB];  // Lambda^WB
+    const R *tk = tab + sg * TS, *tl = tk + (WB + 1), *tkb = tl + (WB + 1), *tlb = tkb + 17;
+    const R LB = tl[WB];  // Lambda^WB
     const R *gF = xF + (size_t)q * XS * NC + c, *gW = xW + (size_t)q * XS * NC + c;
     R ftot = R(0), pfb = R(0), fr = R(0);
 #pragma unroll 1
@@ -460,13 +462,13 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
 #pragma unroll 1
     for (int b = cs - 1; b >= 0; --b) {
       if (b == rank) wsr = wl;  // composite of the blocks after this one
-      wl = fma(LB, fma(K[(cs - 1 - b) * WB], gF[b * NC], wl), gW[b * NC]);
+      wl = fma(LB, fma(tkb[cs - 1 - b], gF[b * NC], wl), gW[b * NC]);
     }
     const R y0 = ftot * M.inv1m;
-    const R z0 = fma(K[A.m], y0, wl) * M.inv1m;
-    const R ycb = fma(lp[rank * WB], y0, pfb);
+    const R z0 = fma(tlb[17], y0, wl) * M.inv1m;  // K_{mL}
+    const R ycb = fma(tlb[rank], y0, pfb);
     const R ycn = fma(LB, ycb, fr);
-    const R zcb = fma(lp[(cs - 1 - rank) * WB], z0, fma(K[(cs - 1 - rank) * WB], ycn, wsr));
+    const R zcb = fma(tlb[cs - 1 - rank], z0, fma(tkb[cs - 1 - rank], ycn, wsr));
     if (h == 0) {
       car[q * NC + c] = ycb;
       car[(NG + q) * NC + c] = zcb;
@@ -476,7 +478,7 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
 #pragma unroll
   for (int q = 0; q < NG; ++q) {
     const int sg = mi(q);
-    const R *K = Kq[q], *lp = A.lpow[sg / 3][sg % 3];
+    const R *K = Kq[q], *lp = Kq[q] + (WB + 1);
     const R ycb = car[q * NC + c], zcb = car[(NG + q) * NC + c];
     Yc[q] = fma(lp[j], ycb, PF[q]);
     const R yn = fma(LM[q], Yc[q], F[q]);
@@ -515,6 +517,24 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   R *xW = xF + (size_t)2 * S * XS * NC;
   R *blk = xW + (size_t)2 * S * XS * NC;       // [3 exchanges][2][2S][NC]
   R *car = blk + (size_t)3 * 2 * 2 * S * NC;   // [2][2S][NC]
+  constexpr int TS = 2 * (WB + 1) + 35;
+  R *tab = car + (size_t)2 * 2 * S * NC;       // [S * 3 matrices][TS]: the exchange's coefficient tables
+  for (int e = tid; e < S * 3 * TS; e += WB * NC) {
+    const int mx = e / TS, o = e - mx * TS;
+    const R *kch = A.kch[mx / 3][mx % 3], *lpw = A.lpow[mx / 3][mx % 3];
+    R v;
+    if (o <= WB) v = kch[o];                                                    // K_{oL}
+    else if (o <= 2 * WB + 1) v = lpw[o - (WB + 1)];                            // Lambda^n
+    else if (o < 2 * WB + 2 + 17) {                                             // K at block multiples
+      const int b = o - (2 * WB + 2);
+      v = b * WB <= A.m ? kch[b * WB] : R(0);
+    } else if (o < 2 * WB + 2 + 34) {                                           // Lambda at block multiples
+      const int b = o - (2 * WB + 2 + 17);
+      v = b * WB <= A.m ? lpw[b * WB] : R(0);
+    } else v = kch[A.m];                                                        // K_{mL}
+    tab[e] = v;
+  }
+  __syncthreads();
   auto Tf = [&](int f, int s) -> R * { return tile + (size_t)(f * S + s) * ROWS * NC; };
   // this thread's column of its chunk in field f, species s (row t at + t * 32)
   auto Tc = [&](int f, int s) -> R * { return Tf(f, s) + (w * L) * 32 + h * NC + c; };
@@ -570,8 +590,8 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           F[2 * s + 1] = y1; W[2 * s + 1] = w1;
         }
         auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
-        strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)fld * 2 * 2 * S * NC, car, j,
-                                       c, w, h, rank);
+        strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)fld * 2 * 2 * S * NC, car, tab,
+                                       j, c, w, h, rank);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
@@ -617,8 +637,8 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           W[s] = w;
         }
         auto mi = [&](int q) { return q * 3; };
-        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * 2 * S * NC, car, j, c, w,
-                                   h, rank);
+        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * 2 * S * NC, car, tab, j, c,
+                                   w, h, rank);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &M = A.mat[s][0];
@@ -670,7 +690,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           W[s] = w;
         }
         auto mi = [&](int q) { return q * 3 + 0; };
-        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk, car, j, c, w, h, rank);
+        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk, car, tab, j, c, w, h, rank);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &M = A.mat[s][0];
@@ -719,8 +739,8 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
         }
       }
       auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
-      strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * S * NC, car, j, c, w,
-                                     h, rank);
+      strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * S * NC, car, tab, j, c,
+                                     w, h, rank);
       // ---- U_{n+1} = T_d f1 - S_d f2
 #pragma unroll
       for (int s = 0; s < S; ++s) {

@@ -135,7 +135,8 @@ inline size_t circ_strided_smem(int nspecies, int L, int WB, int NC, size_t real
   const size_t exch = (size_t)2 * 2 * nspecies * (WB > 16 ? WB : 16) * NC * real_bytes;
   const size_t blk = (size_t)3 * 2 * 2 * nspecies * NC * real_bytes;
   const size_t car = (size_t)2 * 2 * nspecies * NC * real_bytes;
-  return tile + exch + blk + car;
+  const size_t tab = (size_t)nspecies * 3 * (2 * (WB + 1) + 35) * real_bytes;
+  return tile + exch + blk + car + tab;
 }
 cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                                   int &nclusters);
