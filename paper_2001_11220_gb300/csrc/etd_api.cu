@@ -362,9 +362,19 @@ bool plan_axis_circ(Instance &I, int a, int L, int wb, int nc) {
   P.nthreads = (int)std::max<long long>(m, 256);
   P.nlb = P.nthreads / P.m;
   P.nlo_blocks = 1;
-  P.nblocks = (int)((P.nlines + P.nlb - 1) / P.nlb);
   P.smem = circ_first_smem(I.S, L, P.nthreads, P.m, P.nlb, I.real_bytes);
-  return P.smem <= 200 * 1024;
+  if (P.smem > 200 * 1024) return false;
+  // persistent: the blocks resident at once, each walking the line groups
+  const long long ngroups = (P.nlines + P.nlb - 1) / P.nlb;
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (circ_first_capacity(I.real_bytes, I.S, L, P.nthreads, P.smem, per_sm) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (per_sm < 1) return false;
+  P.nblocks = (int)std::min<long long>(ngroups, (long long)per_sm * nsm);
+  return true;
 }
 
 bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc) {

@@ -141,4 +141,30 @@ cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L
   return strided_any<double>(a, nspecies, L, kind, smem, 1, nullptr, &nclusters);
 }
 
+cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthreads, size_t smem, int &blocks_per_sm) {
+  blocks_per_sm = 0;
+  const void *fn = nullptr;
+  const int key = nspecies * 100 + L;
+  if (real_bytes == 4) {
+    switch (key) {
+      case 108: fn = (const void *)circ_first_kernel<float, 1, 8>; break;
+      case 116: fn = (const void *)circ_first_kernel<float, 1, 16>; break;
+      case 208: fn = (const void *)circ_first_kernel<float, 2, 8>; break;
+      case 216: fn = (const void *)circ_first_kernel<float, 2, 16>; break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (key) {
+      case 104: fn = (const void *)circ_first_kernel<double, 1, 4>; break;
+      case 108: fn = (const void *)circ_first_kernel<double, 1, 8>; break;
+      case 204: fn = (const void *)circ_first_kernel<double, 2, 4>; break;
+      case 208: fn = (const void *)circ_first_kernel<double, 2, 8>; break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  cudaError_t e = ensure_dyn_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, nthreads, smem);
+}
+
 }  // namespace etd

@@ -103,7 +103,10 @@ __host__ __device__ constexpr int qmat(int q) { return q == 4 ? 0 : (q & 1) ? 2 
 
 }  // namespace circ
 
-// Thread j of a line: chunk j.  Block: lpb lines x m threads (max(m, 256) threads).
+// Thread j of a line: chunk j.  Block: lpb lines x m threads (max(m, 256)
+// threads).  Persistent: block b takes the line groups b, b + gridDim.x, ...
+// and stages the next group's chunks (cp.async into the other half of its
+// double buffer) while it solves the current one.
 template <typename R, int S, int L>
 __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__ CircArgs<R> A) {
   using namespace circ;
@@ -113,26 +116,38 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
   constexpr int NQ = 5;
   const int m = A.m, tid = threadIdx.x, nthr = blockDim.x;
   const int lb = tid / m, j = tid - lb * m;
-  const long long line = (long long)blockIdx.x * A.lpb + lb;
-  const bool ok = line < A.nlines;
   const int lane = tid & 31;
   const int G = m < 32 ? m : 32;       // lanes of one line in a warp
   const int gl = lane & (G - 1);
   const int nw = m > 32 ? m / 32 : 1;  // warps of one line
   const int w = j >> 5;
-  R *stage = reinterpret_cast<R *>(circ_smem);
-  R *tot = stage + (size_t)S * nthr * CSZ;  // [2][lpb][nw][S][NQ]
-
-  // ---- stage U_n: thread-private padded slot per species ([s][tid][CSZ])
+  R *stage0 = reinterpret_cast<R *>(circ_smem);         // [2 buffers][S][nthr][CSZ]
+  R *tot = stage0 + (size_t)2 * S * nthr * CSZ;         // [2][lpb][nw][S][NQ]
+  const long long ngrp = (A.nlines + A.lpb - 1) / A.lpb;
+  // stage U_n of line group gi into buffer bi: thread-private padded slot per species
+  auto stage = [&](long long gi, int bi) {
+    const long long ln = gi * A.lpb + lb;
+    if (gi < ngrp && ln < A.nlines) {
+      const long long b0 = ln * (long long)A.p + (long long)j * L;
+      R *dst = stage0 + (size_t)bi * S * nthr * CSZ;
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int v = 0; v < L; v += VW)
+          cp_async16(dst + ((size_t)s * nthr + tid) * CSZ + v, A.in[0] + s * A.N + b0 + v);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  stage(blockIdx.x, 0);
+  int bi = 0;
+#pragma unroll 1
+  for (long long gi = blockIdx.x; gi < ngrp; gi += gridDim.x, bi ^= 1) {
+  const long long line = gi * A.lpb + lb;
+  const bool ok = line < A.nlines;
+  stage(gi + gridDim.x, bi ^ 1);                        // prefetch the next group
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this thread's chunk of the current group
+  R *stage = stage0 + (size_t)bi * S * nthr * CSZ;
   const long long base = line * (long long)A.p + (long long)j * L;
-  if (ok) {
-#pragma unroll
-    for (int s = 0; s < S; ++s)
-#pragma unroll
-      for (int v = 0; v < L; v += VW)
-        cp_async16(stage + ((size_t)s * nthr + tid) * CSZ + v, A.in[0] + s * A.N + base + v);
-  }
-  cp_async_wait_all();
   auto su = [&](int s, int t) -> R { return stage[((size_t)s * nthr + tid) * CSZ + t]; };
 
   // ---- pass 1: zero-carry summaries of every solve
@@ -194,6 +209,7 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
         R v = lane < nw ? tot[((size_t)(lb * nw + lane) * S + s) * NQ + q] : R(0);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
+          if ((1 << k) >= nw) break;
           const R o = __shfl_up_sync(FULL, v, 1 << k);
           if (lane >= (1 << k)) v = fma(M.sw[k], o, v);
         }
@@ -258,6 +274,7 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
         R v = lane < nw ? tb[((size_t)(lb * nw + lane) * S + s) * NQ + q] : R(0);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
+          if ((1 << k) >= nw) break;
           const R o = __shfl_down_sync(FULL, v, 1 << k);
           if (lane + (1 << k) < nw) v = fma(M.sw[k], o, v);
         }
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
     }
 
   // ---- pass 2: recurrences from the carries, combination, 32-byte stores
-  if (!ok) return;
+  if (ok) {
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const CircMat<R> &MP = A.mat[s][0], &MT = A.mat[s][1], &MS = A.mat[s][2];
@@ -348,6 +365,9 @@ __global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__
 #pragma unroll
     for (int t = 0; t < L; t += 32 / (int)sizeof(R)) st32(o + t, zt + t);
   }
+  }  // ok
+  }  // line groups
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ===================================================== strided axes
