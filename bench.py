@@ -1,11 +1,20 @@
 """Benchmark of one ETD-RDP-IF step on GB300.
 
-Workload: 3D scalar Dirichlet problem u_t = Lap u - u/(1+u) + f(x,t) on the
-unit cube, f manufactured so u = e^{-t} sin(pi x) sin(pi y) sin(pi z) is
-exact, 256^3 interior nodes, k = h = 1/257, FP32 state and arithmetic (the
-FP64 reference mode is timed beside it).  A "step" is one full ETD-RDP-IF
-step: the three fused axis sweeps (F(U_n), predictor, R_1/P_1 on x; R_2/P_2 on
-y; P_3, F(U*), corrector T_3/S_3 on z).  Metric: cell-species-steps/s.
+Headline workload: 2D Schnakenberg reaction-diffusion on the periodic unit
+square, u_t = Lap u + 1000 (0.1 - u + u^2 v), v_t = 10 Lap v + 1000 (0.9 - u^2 v),
+4096^2 nodes, 2 species, k = 1e-4, FP32 state and arithmetic (cyclic lines:
+the circulant kernels, or the table kernels with Sherman-Morrison, whichever
+the autotuner times faster).  A "step" is one full ETD-RDP-IF step: the two
+fused axis sweeps (F(U_n), predictor, R_1/P_1 on x; P_2, F(U*), corrector
+T_2/S_2 on y).  Metric: cell-species-steps/s, timed over K steps replayed from
+one captured CUDA graph (the path etd_run gives users).
+
+Beside it: the per-sweep event-timed run behind the roofline, the end-to-end
+rate through etd_run_host (host buffer copied in and out every step), the 3D
+manufactured 256^3 problem in FP32 and FP64 (speed-up at the accuracy each
+reaches against the exact solution), the 3D Gray-Scott 256^3 forward and
+checkpointed gradient, the 64^2 Brusselator in FP64 (microseconds per step),
+the 512-instance ensemble, and the CPU oracle on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp32|fp64]
 
@@ -30,7 +39,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ETD-RDP-IF cell-species-steps/s"
 UNIT = "cell-species-steps/s"
-P_BENCH = 256
+P_HEAD = 4096      # headline grid: 4096^2 periodic Schnakenberg
+P_3D = 256         # 3D manufactured and Gray-Scott grids
 
 
 def _dist():
@@ -52,7 +62,8 @@ def _peaks():
 # sources that compile into the forward sweep kernels (their DRAM traffic
 # depends on nothing else but the tile shapes, recorded beside each entry)
 SWEEP_SOURCES = ("etd_internal.h", "etd_tables.h", "etd_sweep.cuh", "etd_sweep_smem.cuh", "etd_sweep_launch.cuh",
-                 "etd_sweep_f32.cu", "etd_sweep_f64.cu", "etd_sweep_cluster.cu")
+                 "etd_sweep_f32.cu", "etd_sweep_f64.cu", "etd_sweep_cluster.cu", "etd_circ.h", "etd_circ.cuh",
+                 "etd_circ.cu")
 
 
 def _csrc_hash() -> str:
@@ -160,23 +171,29 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baselines(w):
+def cpu_baselines(w, name):
     """The oracle on all host cores (3 steps of the full grid) and on one
-    core (1 step), about 15 s of CPU time in all on a 16-core host."""
+    core (1 step): a bounded sample of the workload, about 15 s of CPU time."""
     v, dt, used = oracle_baseline(w, 3, host_cores())
     v1, dt1, _ = oracle_baseline(w, 1, 1)
     return {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"3 oracle steps of the full {P_BENCH}^3 grid (FP64, OpenMP over lines and points, "
+            "sample": f"3 oracle steps of the full {name} grid (FP64, OpenMP over lines and points, "
                       f"{used} threads, {dt:.1f} s)",
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
-                              "sample": f"1 oracle step of the full {P_BENCH}^3 grid (FP64, 1 thread, {dt1:.1f} s)"}}
+                              "sample": f"1 oracle step of the full {name} grid (FP64, 1 thread, {dt1:.1f} s)"}}
+
+
+def head_workload(W):
+    return W.schnakenberg_2d(P_HEAD)
 
 
 def workload_desc(w, precision):
-    return {"workload": f"mms3d_{P_BENCH}: 3D Dirichlet u_t = Lap u - u/(1+u) + f, {P_BENCH}^3 interior nodes, "
-                        f"k = h = 1/{P_BENCH + 1}, manufactured u = e^-t sin sin sin",
+    fb = w.npoints * (4 if precision == "fp32" else 8)
+    return {"workload": f"schnakenberg2d_{P_HEAD}: 2D periodic Schnakenberg u_t = Lap u + 1000 (0.1 - u + u^2 v), "
+                        f"v_t = 10 Lap v + 1000 (0.9 - u^2 v), {P_HEAD}^2 nodes, 2 species, k = 1e-4, "
+                        f"IC (1, 0.9) + U(-1e-3, 1e-3)",
             "points": w.npoints, "species": w.nspecies, "precision": precision,
-            "l2": "inputs larger than L2: each sweep streams 4-6 fields of %d MB" % (w.npoints * (4 if precision == "fp32" else 8) // 2**20)}
+            "l2": f"inputs larger than L2: each sweep streams 4 fields of {2 * fb // 2**20} MB (2 species)"}
 
 
 def _timed(fn, stream, reps=1):
@@ -194,70 +211,126 @@ def _timed(fn, stream, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
-    """Throughput of the other benchmark problems (cell-species-steps/s):
-    forward + adjoint (checkpointed gradient) on the main workload and on the
-    256^3 periodic Gray-Scott problem, the 4096^2 periodic Schnakenberg step,
-    and the 512-instance Brusselator ensemble."""
+def tiles_of(info, dim):
+    # tile shapes per axis in the ETD_TILES format (L:lines:kernel:pack), to reproduce in a profiler run
+    return ",".join(f"{info['chunk'][a]}:{info['lines_per_block'][a]}:{info['staged'][a]}:{info['pack'][a]}"
+                    for a in range(dim))
+
+
+SWEEP_FIELDS = {0: 4, 1: 6, 2: 4}   # fields read + written per point: first, middle, last sweep
+
+
+def sweep_roofline(ctx, U, w, nsteps, rb, peak, workload_key, tiles):
+    """Per-sweep device times from a profiled run (CUDA events around every
+    sweep launch on the context's stream) and their HBM rooflines."""
+    import torch
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.run(U, 0.0, nsteps)
+    torch.cuda.synchronize()
+    sweep_ms, sweep_n = ctx.profile_read()
+    ctx.profile(False)
+    names = {0: "sweep_first_x", 1: "sweep_middle_y", 2: "sweep_last_" + ("y" if w.dim == 2 else "z")}
+    tl = tiles.split(",")
+    out = {}
+    for kind in range(3):
+        if sweep_n[kind] == 0:
+            continue
+        t = sweep_ms[kind] / sweep_n[kind] / 1e3
+        alg = SWEEP_FIELDS[kind] * w.nspecies * w.npoints * rb
+        axis = {0: 0, 1: 1, 2: w.dim - 1}[kind]
+        out[names[kind]] = {"ms": t * 1e3, "launches": sweep_n[kind], "algorithmic_bytes_per_launch": alg,
+                            "achieved_gbs": alg / t / 1e9, "frac": alg / t / 1e9 / peak,
+                            "traffic": _traffic(names[kind], workload_key, tl[axis])}
+    return out, int(sum(sweep_n))
+
+
+def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp64=True):
+    """The other benchmark problems (cell-species-steps/s, each a few
+    device-timed steps replayed from a graph)."""
     import torch
     from paper_2001_11220_gb300.api import EtdEnsemble
     out = {}
 
-    def mk(w, prec):
+    def mk(w, prec, tune=True):
         with torch.cuda.stream(stream):
             c = EtdRdpIf.from_workload(w, prec, stream=stream)
             U = torch.tensor(W.initial_state(w), device="cuda", dtype=c.dtype)
-            c.autotune(U.clone())    # tile shapes per axis, timed on a scratch copy of the state
+            if tune:
+                c.autotune(U.clone())    # tile shapes per axis, timed on a scratch copy of the state
         return c, U
 
-    # forward + adjoint: etd_grad over 20 steps, checkpoint every 10 (main workload)
-    w = W.mms_3d(P_BENCH)
+    # 3D manufactured 256^3 (Dirichlet, 1 species): FP32 and FP64 throughput, and
+    # the accuracy each reaches at T = 1 (k = h, 257 steps) against the exact solution
+    w = W.mms_3d(P_3D)
+    res = {}
+    for prec in ("fp32", "fp64") if include_fp64 else ("fp32",):
+        c, U = mk(w, prec)
+        rb = 4 if prec == "fp32" else 8
+        nst = 20 if prec == "fp32" else 5
+        ms = _timed(lambda: c.run(U, 0.0, nst), stream)
+        tiles = tiles_of(c.info(), 3)
+        per, _ = sweep_roofline(c, U, w, 3, rb, peak, f"mms3d_{P_3D}_{prec}", tiles)
+        with torch.cuda.stream(stream):
+            V = torch.tensor(W.initial_state(w), device="cuda", dtype=c.dtype)
+        c.run(V, 0.0, w.steps)               # the whole run to T = 1
+        torch.cuda.synchronize()
+        exact = W.exact_mms(w, w.steps * w.k)
+        err = float(abs(V.double().cpu().numpy() - exact).max() / abs(exact).max())
+        res[prec] = {"value": w.npoints * nst / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / nst, "tiles": tiles,
+                     "per_sweep": per, "err_vs_exact_at_T1": err,
+                     "step_frac": c.info()["algorithmic_bytes"] / (ms / nst / 1e3) / 1e9 / peak}
+        c.close()
+        del U, V
+    if include_fp64:
+        res["speedup_fp32_over_fp64"] = res["fp32"]["value"] / res["fp64"]["value"]
+        res["accuracy_note"] = ("error of the full run (T = 1, 257 steps, k = h = 1/257) against the exact "
+                                "solution: the scheme's own error (second order in h) bounds both precisions")
+    out[f"mms3d_{P_3D}"] = res
+    # forward + adjoint (etd_grad over 20 steps, checkpoint every 10) on the manufactured problem
     c, U = mk(w, "fp32")
     T = U.clone()
     nst = 20
     ms = _timed(lambda: c.grad(U, 0.0, T, nst, 10), stream)
-    out["mms3d_256_fp32_fwd_adjoint"] = {"value": w.npoints * w.nspecies * nst / (ms / 1e3), "unit": UNIT,
-                                         "ms_per_step": ms / nst, "steps": nst, "ckpt_every": 10}
+    out[f"mms3d_{P_3D}_fp32_fwd_adjoint"] = {"value": w.npoints * w.nspecies * nst / (ms / 1e3), "unit": UNIT,
+                                             "ms_per_step": ms / nst, "steps": nst, "ckpt_every": 10}
     c.close()
     del U, T
     # 3D Gray-Scott periodic 256^3, 2 species, k = 1: forward and checkpointed gradient (ckpt 20)
-    w = W.gray_scott_3d(256, steps=20)
+    w = W.gray_scott_3d(P_3D, steps=20)
     c, U = mk(w, "fp32")
     tg = torch.tensor(W.initial_state(w, seed=2002), device="cuda", dtype=torch.float32)
     V = U.clone()
     msf = _timed(lambda: c.run(V, 0.0, 20), stream)
+    tiles = tiles_of(c.info(), 3)
+    per, _ = sweep_roofline(c, V, w, 3, 4, peak, f"grayscott3d_{P_3D}_fp32", tiles)
     msg = _timed(lambda: c.grad(U, 0.0, tg, 20, 20), stream)
     units = w.npoints * w.nspecies * 20
-    out["grayscott3d_256_fp32"] = {"fwd": units / (msf / 1e3), "fwd_adjoint": units / (msg / 1e3), "unit": UNIT,
-                                   "fwd_ms_per_step": msf / 20, "fwd_adjoint_ms_per_step": msg / 20}
+    alg = c.info()["algorithmic_bytes"]
+    # reverse step (per step of the gradient, FP32, 2 species, N points): recompute x and y
+    # sweeps (4 + 6 fields), ADJ_LAST (reads Ubar', c_U, c_f, w; writes 3: 7 fields),
+    # ADJ_MIDDLE (6 adjoint + 3 forward fields read, 3 written: 12), ADJ_FIRST (3 adjoint + U_n
+    # read, Ubar_n written: 5), plus the checkpoint recomputation of the forward step (14)
+    rev_fields = 4 + 6 + 7 + 12 + 5 + 14
+    fb = w.nspecies * w.npoints * 4
+    out[f"grayscott3d_{P_3D}_fp32"] = {
+        "fwd": units / (msf / 1e3), "fwd_adjoint": units / (msg / 1e3), "unit": UNIT,
+        "fwd_ms_per_step": msf / 20, "fwd_adjoint_ms_per_step": msg / 20, "tiles": tiles,
+        "fwd_adjoint_over_fwd": msg / msf,
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "per_sweep": per,
+                     "fwd_step_frac": alg / (msf / 20 / 1e3) / 1e9 / peak,
+                     "fwd_adjoint_algorithmic_bytes_per_step": alg + rev_fields * fb,
+                     "fwd_adjoint_step_frac": (alg + rev_fields * fb) / (msg / 20 / 1e3) / 1e9 / peak}}
     c.close()
     del U, V, tg
-    # 2D Schnakenberg periodic 4096^2 (cyclic lines, FP64 Sherman-Morrison scalar), FP32 state
-    w = W.schnakenberg_2d(4096, steps=20)
-    c, U = mk(w, "fp32")
-    ms = _timed(lambda: c.run(U, 0.0, 20), stream)
-    inf = c.info()
-    tiles = [f"{inf['chunk'][a]}:{inf['lines_per_block'][a]}:{inf['staged'][a]}:{inf['pack'][a]}" for a in range(2)]
-    # per-sweep device times (CUDA events around each sweep, a separate run) against the HBM peak
-    c.profile(True)
-    c.profile_read()
-    c.run(U, 0.0, 20)
-    torch.cuda.synchronize()
-    sweep_ms, sweep_n = c.profile_read()
-    c.profile(False)
-    peak, _ = _peaks()
-    fld = w.nspecies * w.npoints * 4
-    per_sweep = {}
-    for name, kind, a in (("sweep_first_x", 0, 0), ("sweep_last_y", 2, 1)):
-        t = sweep_ms[kind] / max(1, sweep_n[kind]) / 1e3
-        per_sweep[name] = {"ms": t * 1e3, "achieved_gbs": 4 * fld / t / 1e9, "frac": 4 * fld / t / 1e9 / peak,
-                           "traffic": _traffic(name, "schnakenberg2d_4096_fp32", tiles[a])}
-    out["schnakenberg2d_4096_fp32"] = {"value": w.npoints * w.nspecies * 20 / (ms / 1e3), "unit": UNIT,
-                                       "ms_per_step": ms / 20, "tiles": ",".join(tiles),
-                                       "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak,
-                                                    "step_frac": inf["algorithmic_bytes"] / (ms / 20 / 1e3) / 1e9 / peak,
-                                                    "algorithmic_bytes_per_step": inf["algorithmic_bytes"],
-                                                    "per_sweep": per_sweep}}
+    # 2D Brusselator 64^2 Neumann, FP64, 100 steps (T = 1): L2-resident, microseconds per step
+    w = W.brusselator_2d()
+    c, U = mk(w, "fp64", tune=False)
+    ms = _timed(lambda: c.run(U, 0.0, w.steps), stream, reps=3)
+    out["brusselator2d_64_fp64"] = {"value": w.npoints * w.nspecies * w.steps / (ms / 1e3), "unit": UNIT,
+                                    "us_per_step": ms * 1e3 / w.steps, "steps": w.steps,
+                                    "note": "whole 100-step run replayed from one graph; the state (64 KB) "
+                                            "stays in L2, so the step is launch- and latency-bound"}
     c.close()
     del U
     # batched ensemble: 512 Brusselator instances 64^2 .. 512^2, FP32, one launch per sweep
@@ -272,8 +345,10 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
     ms = _timed(lambda: ens.run(states, 0.0, 20), stream)
     units = sum(x.npoints * x.nspecies for x in ws) * 20
     ms_max, units_all, thr = aggregate(ms, units)
+    cells = int(units_all) // 20
     out["ensemble512_brusselator_fp32"] = {"value": thr, "unit": UNIT, "ms_per_step": ms_max / 20,
-                                           "instances": len(ws_all), "cell_species": int(units_all) // 20,
+                                           "instances": len(ws_all), "cell_species": cells,
+                                           "step_frac": 8 * cells * 4 / (ms_max / 20 / 1e3) / 1e9 / peak,
                                            "scaling": "strong (instances sharded across ranks)"}
     ens.close()
     return out
@@ -281,14 +356,14 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier):
 
 def run_reference(args):
     """--impl reference: the CPU oracle, timed on the host cores on a bounded
-    sample of the same workload (each 'step' = one oracle step of 256^3)."""
+    sample of the same workload (each 'step' = one oracle step of 4096^2)."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     from paper_2001_11220_gb300 import workloads as W
-    w = W.mms_3d(P_BENCH)
+    w = head_workload(W)
     # every timed "step" is one oracle step of the full grid on all host cores
-    # (~10 s of CPU time); the run stops after K steps or a 60 s budget
+    # (a few seconds); the run stops after K steps or a 60 s budget
     times = []
     cores = host_cores()
     while len(times) < max(1, args.steps) and sum(times) < 60.0:
@@ -301,7 +376,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_desc(w, "fp64"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                             "sample": f"{len(times)} oracle step(s) of the full {P_BENCH}^3 grid, FP64, "
+                             "sample": f"{len(times)} oracle step(s) of the full {P_HEAD}^2 grid, FP64, "
                                        f"OpenMP over lines and points, {used} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -311,7 +386,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -338,110 +413,61 @@ def main():
     W_ = max(3, args.warmup)
     K = max(1, args.steps)
 
-    w = W.mms_3d(P_BENCH)
+    w = head_workload(W)
     U0 = W.initial_state(w)
     stream = torch.cuda.Stream()
     units_per_step = w.npoints * w.nspecies
-
-    def make(prec):
-        with torch.cuda.stream(stream):
-            ctx = EtdRdpIf.from_workload(w, prec, stream=stream)
-            U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
-        return ctx, U
+    rb = 4 if args.precision == "fp32" else 8
+    peak, peak_src = _peaks()
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def timed(ctx, U, K, profile, tag="etd_timed_steps"):
-        # warm-up (untimed), then K steps between a barrier + synchronize on both sides
-        ctx.run(U, 0.0, W_)
-        torch.cuda.synchronize()
-        if profile:
-            ctx.profile(True)
-            ctx.profile_read()
-        barrier()
-        torch.cuda.synchronize()
-        if not profile:
-            ctx.run(U, W_ * w.k, K)       # builds and caches the CUDA graph of this K-step run
-            torch.cuda.synchronize()
-            barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push(tag)   # profilers can keep just these launches
-        e0.record(stream)
-        ctx.run(U, W_ * w.k, K)
-        e1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        barrier()
-        ms = e0.elapsed_time(e1)
-        per = None
-        if profile:
-            per = ctx.profile_read()
-            ctx.profile(False)
-        return ms, per
-
-    # ---- main measurement: FP32 (or --precision) with per-sweep events
-    ctx, U = make(args.precision)
+    with torch.cuda.stream(stream):
+        ctx = EtdRdpIf.from_workload(w, args.precision, stream=stream)
+        U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
     if not args.no_autotune:
         with torch.cuda.stream(stream):
             Wk = U.clone()
         ctx.autotune(Wk)                      # tile shapes timed per axis on a scratch state
         del Wk
     info = ctx.info()
-    # tile shapes per axis in the ETD_TILES format (L:lines:staged:pack), to reproduce in a profiler run
-    tiles = ",".join(f"{info['chunk'][a]}:{info['lines_per_block'][a]}:{info['staged'][a]}:{info['pack'][a]}"
-                     for a in range(w.dim))
+    tiles = tiles_of(info, w.dim)
+
+    # ---- headline: K steps replayed from one captured CUDA graph (etd_run)
+    ctx.run(U, 0.0, W_)                      # warm-up (untimed)
+    ctx.run(U, W_ * w.k, K)                  # builds and caches the graph of this K-step run
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        ms, per = timed(ctx, U, K, profile=True)
-    clocks = clk.summary()
-    from paper_2001_11220_gb300.parallel import aggregate, shard
-    ms_max, _, value = aggregate(ms, units_per_step * K)   # max time over ranks, summed work
-
-    # per-sweep roofline: dominant kernel = largest total device time
-    kinds = ["sweep_first_x", "sweep_middle_y", "sweep_last_z"]
-    sweep_ms, sweep_launches = per
-    dom = max(range(3), key=lambda i: sweep_ms[i])
-    rb = 4 if args.precision == "fp32" else 8
-    fields = {0: 4, 1: 6, 2: 4}[dom]                       # fields read + written per point
-    alg_bytes = fields * w.nspecies * w.npoints * rb       # per launch
-    avg_s = sweep_ms[dom] / sweep_launches[dom] / 1e3
-    achieved = alg_bytes / avg_s / 1e9
-    peak, peak_src = _peaks()
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(kinds[dom], f"mms3d_{P_BENCH}_{args.precision}", tiles.split(",")[dom]),
-            "kernel": kinds[dom], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "per_sweep_ms": {kinds[i]: sweep_ms[i] / max(1, sweep_launches[i]) for i in range(3)},
-            "step_frac": (info["algorithmic_bytes"] / (ms_max / K / 1e3) / 1e9) / peak}
-    launches = int(sum(sweep_launches))
-
-    # ---- FP64 reference mode (same workload), for the speedup at stated accuracy
-    extra = {}
-    if args.precision == "fp32":
-        ctx64, U64 = make("fp64")
-        if not args.no_autotune:
-            with torch.cuda.stream(stream):
-                Wk = U64.clone()
-            ctx64.autotune(Wk)
-            del Wk
-        K64 = max(3, K // 5)
-        ms64, _ = timed(ctx64, U64, K64, profile=False, tag="etd_timed_steps_fp64")
-        v64 = units_per_step * K64 / (ms64 / 1e3)
-        # accuracy of FP32 against the FP64 path (which matches the FP64 oracle) after 5 steps
-        with torch.cuda.stream(stream):
-            A = torch.tensor(U0, device="cuda", dtype=torch.float32)
-            B64 = torch.tensor(U0, device="cuda", dtype=torch.float64)
-        ctx.run(A, 0.0, 5)
-        ctx64.run(B64, 0.0, 5)
+        torch.cuda.nvtx.range_push("etd_timed_steps")   # profilers can keep just these launches
+        e0.record(stream)
+        ctx.run(U, W_ * w.k, K)
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        err = float((A.double() - B64).abs().max() / B64.abs().max())
-        extra = {"fp64": {"value": v64, "ms_per_step": ms64 / K64},
-                 "speedup_fp32_over_fp64": value / world / v64,
-                 "fp32_rel_err_vs_fp64_after_5_steps": err}
-        ctx64.close()
-        del U64, B64
+    barrier()
+    clocks = clk.summary()
+    ms = e0.elapsed_time(e1)
+    from paper_2001_11220_gb300.parallel import aggregate
+    ms_max, _, value = aggregate(ms, units_per_step * K)   # max time over ranks, summed work
+    launches = K * info["launches_per_step"]
+    finite = bool(torch.isfinite(U).all())
+
+    # ---- per-sweep roofline from a separate profiled run (direct launches, events per sweep)
+    per, _ = sweep_roofline(ctx, U, w, min(K, 200), rb, peak, f"schnakenberg2d_{P_HEAD}_{args.precision}", tiles)
+    dom = max(per, key=lambda k: per[k]["ms"])            # dominant kernel: longest sweep
+    roof = {"bound": "hbm", "achieved": per[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": per[dom]["frac"], "traffic": per[dom]["traffic"], "kernel": dom,
+            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": per[dom]["algorithmic_bytes_per_launch"],
+            "per_sweep": per,
+            "step_frac": (info["algorithmic_bytes"] / (ms_max / K / 1e3) / 1e9) / peak,
+            "algorithmic_bytes_per_step": info["algorithmic_bytes"]}
 
     # ---- end to end through the C ABI with a pinned host buffer, every step
     Hst = torch.tensor(U0, dtype=ctx.dtype).pin_memory()
@@ -456,29 +482,31 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_v = world * units_per_step * args.e2e_steps / float(e2e_t.item())
     state_bytes = info["state_bytes"]
+    ctx.close()
+    del U, Hst
 
     # ---- further workloads on this GPU (each a few device-timed steps)
-    others = {} if args.no_extra else extra_workloads(EtdRdpIf, W, stream, world, rank, barrier)
+    others = {} if args.no_extra else extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baselines(w)
+        cpu = cpu_baselines(w, f"{P_HEAD}^2")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W_,
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": dict(workload_desc(w, args.precision), parallelism="replicas" if world > 1 else "single",
-                               chunk=info["chunk"][:3], lines_per_block=info["lines_per_block"][:3],
-                               staged=info["staged"][:3], tiles=tiles, autotuned=not args.no_autotune),
+                               timed_path="etd_run: K steps replayed from one captured CUDA graph",
+                               chunk=info["chunk"][:2], lines_per_block=info["lines_per_block"][:2],
+                               staged=info["staged"][:2], grid_blocks=info["grid_blocks"][:2], tiles=tiles,
+                               autotuned=not args.no_autotune, state_finite=finite),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes},
                 "gpu_launches": launches, "clocks": clocks}
-        line.update(extra)
         line["workloads"] = others
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -859,6 +859,13 @@ cudaError_t forward_step(const Instance &I, void *U, double t, cudaStream_t s, e
 
 // ------------------------------------------------------------ instances
 
+// ETD_CIRCULANT=0 keeps periodic axes on the table kernels unless ETD_TILES
+// asks otherwise (to compare the two families)
+static bool forced_only_tables() {
+  const char *v = std::getenv("ETD_CIRCULANT");
+  return v && v[0] == '0';
+}
+
 etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const double *D, const etd_reaction *rx,
                          double k, int32_t precision, bool with_scratch) {
   I.dim = grid->dim;
@@ -899,6 +906,18 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
                                   : plan_axis_ex(I, a, fl, ETD_MAX_BLOCK_THREADS, fn, !fs, fp == 2 && !fs ? 2 : 1);
         if (ok) continue;
       }
+    }
+    // periodic axes: the circulant kernels where a shape fits (fastest measured);
+    // otherwise, and for other boundaries, the table kernels
+    if (with_scratch && I.bc[a] == BC_PERIODIC && !forced_only_tables()) {  // (ensembles plan their own)
+      const int Lc = I.real_bytes == 4 ? 16 : 8;
+      bool ok = false;
+      if (a == 0) ok = plan_axis_circ(I, a, Lc, 16, 32);
+      else if (I.real_bytes == 4)
+        ok = plan_axis_circ(I, a, Lc, 16, 32) || plan_axis_circ(I, a, Lc, 8, 32) || plan_axis_circ(I, a, Lc, 16, 16);
+      else
+        ok = plan_axis_circ(I, a, Lc, 8, 32) || plan_axis_circ(I, a, Lc, 16, 16);
+      if (ok) continue;
     }
     while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
     if (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))

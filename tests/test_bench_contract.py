@@ -26,4 +26,4 @@ def test_reference_arm_json_line():
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert "workload" in line["config"] and "256" in line["config"]["workload"]
+    assert "workload" in line["config"] and "4096" in line["config"]["workload"]
