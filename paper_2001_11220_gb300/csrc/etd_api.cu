@@ -763,6 +763,8 @@ cudaError_t run_sweep(const Instance &I, int a, SweepArgs<R> &A, cudaStream_t s)
       C.in[f] = A.in[f];
       C.out[f] = A.out[f];
     }
+    // strided sweeps with 32 lines per block stage their tiles by TMA
+    if (a > 0 && P.nlb == 32 && !circ_encode_maps(C, I.S, P.mx * P.L)) return cudaErrorNotSupported;
     return launch_circ(C, I.S, P.L, P.kind, P.nthreads, P.smem, P.nblocks, s);
   }
   if (P.nseg <= 1) return launch_sweep(A, I.S, P.L, P.kind, P.nthreads, P.smem, s);
@@ -1019,6 +1021,8 @@ etd_status etd_run_host(etd_ctx *ctx, void *U_host, double t0, int64_t nsteps) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  if (circ_take_status())
+    return fail(ctx, ETD_ERR_TIMEOUT, "a sweep kernel's bounded wait for its tile copies gave up");
   return ETD_OK;
 }
 
@@ -1032,6 +1036,8 @@ etd_status etd_profile_read(etd_ctx *ctx, double *ms, int64_t *launches) {
   if (!ctx || !ms || !launches) return fail(ctx, ETD_ERR_INVALID_ARG, "null argument");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  if (circ_take_status())
+    return fail(ctx, ETD_ERR_TIMEOUT, "a sweep kernel's bounded wait for its tile copies gave up");
   for (auto &rec : ctx->prof_events) {
     float t = 0.f;
     e = cudaEventElapsedTime(&t, rec.second.first, rec.second.second);

@@ -167,4 +167,63 @@ cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthread
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, nthreads, smem);
 }
 
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename R>
+bool encode_maps(CircArgs<R> &a, int nspecies, int rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)a.st, (cuuint64_t)(a.N / a.st), (cuuint64_t)nspecies};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.st * sizeof(R), (cuuint64_t)a.N * sizeof(R)};
+  const cuuint32_t box[3] = {32u, (cuuint32_t)rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  for (int f = 0; f < 3; ++f) {
+    if (!a.in[f]) return false;
+    if (enc(&a.tmap[f], dt, 3, (void *)a.in[f], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+bool circ_encode_maps(CircArgs<float> &a, int nspecies, int rows) { return encode_maps<float>(a, nspecies, rows); }
+bool circ_encode_maps(CircArgs<double> &a, int nspecies, int rows) { return encode_maps<double>(a, nspecies, rows); }
+
+int circ_take_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_circ_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_circ_status, &zero, sizeof(int));
+  }
+  return v;
+}
+
 }  // namespace etd

@@ -27,6 +27,9 @@
 
 namespace etd {
 
+// non-zero after a kernel's bounded wait for a TMA copy gave up
+__device__ int g_circ_status;
+
 namespace circ {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -96,6 +99,40 @@ __device__ __forceinline__ void st32(float *p, const float *v) {
 __device__ __forceinline__ void st32(double *p, const double *v) {
   asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
                : "memory");
+}
+
+// ---- TMA (cp.async.bulk.tensor) and mbarrier helpers
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase `parity` of an mbarrier: gives up after 2^24 polls
+// (each poll may suspend the thread for a while), returning false; the
+// caller records the failure and carries on so that every block of a
+// cluster still reaches the same barriers.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (int it = 0; it < (1 << 24); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 // solve q of species s: 0 T on U, 1 S on U, 2 T on F, 3 S on F, 4 P on U + k F
@@ -512,7 +549,7 @@ template <typename R, int S, int L, int KIND, int WB, int NC>
 __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_constant__ CircArgs<R> A) {
   using namespace circ;
   namespace cg = cooperative_groups;
-  extern __shared__ __align__(16) unsigned char circ_smem[];
+  extern __shared__ __align__(128) unsigned char circ_smem[];
   constexpr int ROWS = WB * L;           // rows of the line in this block
   constexpr int VW = 16 / sizeof(R);
   constexpr int HP = 32 / NC;            // chunks per warp (lanes: NC columns x HP chunks)
@@ -558,9 +595,31 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   auto Tf = [&](int f, int s) -> R * { return tile + (size_t)(f * S + s) * ROWS * NC; };
   // this thread's column of its chunk in field f, species s (row t at + t * 32)
   auto Tc = [&](int f, int s) -> R * { return Tf(f, s) + (w * L) * 32 + h * NC + c; };
-  // stage field fld of group g into its buffer (cp.async, 16 bytes); always
-  // one commit group, empty past the last group, so the wait counts hold
+  // NC = 32: every field buffer is one TMA box per species, completed on the
+  // field's mbarrier (phase = this block's group count & 1)
+  constexpr bool TMA = (NC == 32);
+  __shared__ __align__(8) unsigned long long fbar[3];
+  if constexpr (TMA) {
+    if (tid == 0) {
+      for (int f = 0; f < 3; ++f) mbar_init(&fbar[f], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // stage field fld of group g into its buffer (TMA, or cp.async with 16-byte
+  // pieces: always one commit group, empty past the last group, so the wait
+  // counts hold)
   auto stage = [&](int fld, int g) {
+    if constexpr (TMA) {
+      if (tid == 0 && g < ngroups) {
+        const unsigned hi = (unsigned)g / nlob, lo = (unsigned)g - hi * nlob;
+        mbar_expect_tx(&fbar[fld], (unsigned)(S * ROWS * NC * sizeof(R)));
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          tma_load_3d(Tf(fld, s), &A.tmap[fld], (int)(lo * NC), (int)(hi * A.p + rank * ROWS), s, &fbar[fld]);
+      }
+      return;
+    }
     if (g < ngroups) {
       constexpr int PER_ROW = NC / VW;  // 16-byte pieces per row segment
       const long long gb = group_base(g);
@@ -577,6 +636,19 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
   const int r0 = j * L;  // this thread's first row in the tile
+  int it = 0;            // groups this block has processed (mbarrier phase)
+  // wait until field fld of the current group is in shared memory; with
+  // cp.async, `pending` is how many later commit groups may stay in flight
+  auto wait_field = [&](int fld, int pending) {
+    if constexpr (TMA) {
+      if (!mbar_wait(&fbar[fld], (unsigned)(it & 1))) atomicOr(&g_circ_status, 1);
+    } else {
+      if (pending >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+      else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+  };
 
   if constexpr (KIND == SWEEP_MIDDLE) {
     // fields in order c_U, c_f, w; each is exchanged on its own, and its
@@ -590,8 +662,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
       // R_2 = 9 T - 8 S on c_U, then on c_f
 #pragma unroll 1
       for (int fld = 0; fld < 2; ++fld) {
-        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-        __syncthreads();
+        wait_field(fld, 2);
         R F[2 * S], W[2 * S], Yc[2 * S], Zc[2 * S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -640,8 +711,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
       }
       // P_2 on w
       {
-        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-        __syncthreads();
+        wait_field(2, 2);
         R F[S], W[S], Yc[S], Zc[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -681,6 +751,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
         __syncthreads();
         stage(2, g + ncl);
       }
+      ++it;
     }
   } else {
     // buffers: 2 = w (phase A), 0 = c_U, 1 = c_f (phase C, overwritten by f1, f2)
@@ -691,8 +762,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
     for (int g = cid; g < ngroups; g += ncl) {
       const long long mybase = group_base(g) + (long long)r0 * st + c;
       // ---- phase A: U* = P_d w
-      asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // w of g (c_U, c_f may still be in flight)
-      __syncthreads();
+      wait_field(2, 2);  // w of g (c_U, c_f may still be in flight)
       R Ustar[S][L];
       {
         R F[S], W[S], Yc[S], Zc[S];
@@ -732,8 +802,8 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
       __syncthreads();  // w of g fully read: refill with the next group's
       stage(2, g + ncl);
       // ---- F(U*, t_{n+1}); f1, f2 over the staged c_U, c_f; summaries of T f1, S f2
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // c_U, c_f of g
-      __syncthreads();
+      wait_field(0, 1);  // c_U, c_f of g
+      wait_field(1, 1);
       R F[2 * S], W[2 * S], Yc[2 * S], Zc[2 * S];
 #pragma unroll
       for (int q = 0; q < 2 * S; ++q) F[q] = W[q] = R(0);
@@ -787,9 +857,10 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
       __syncthreads();  // f1, f2 of g fully read: refill with the next group's c_U, c_f
       stage(0, g + ncl);
       stage(1, g + ncl);
+      ++it;
     }
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if constexpr (!TMA) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   // no block of a cluster leaves while another may still read its shared memory
   if (cs > 1) cg::this_cluster().sync();
 }

@@ -21,6 +21,8 @@
 // the kernels read no per-position tables.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime)
+
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -44,6 +46,10 @@ template <typename R> struct CircMat {
 
 // Arguments of one circulant sweep launch.
 template <typename R> struct CircArgs {
+  // strided sweeps with 32 lines per block: tensor maps of the three input
+  // fields as 3D tensors {st, N / st, species} (box: 32 lines x the block's
+  // rows x 1 species), loaded by TMA (cp.async.bulk.tensor)
+  CUtensorMap tmap[3];
   const R *in[3];     // FIRST: U_n.  MIDDLE / LAST: c_U, c_f, w
   R *out[3];          // FIRST / MIDDLE: c_U, c_f, w.  LAST: U_{n+1}
   long long N;        // points per species
@@ -119,6 +125,14 @@ template <typename R> inline void circ_to_args(const CircHost &H, CircMat<R> &M)
     M.sw[k] = (R)H.sw[k];
   }
 }
+
+// Tensor maps of the strided sweep's three input fields (32 lines x rows per
+// box); false if the driver's encoder is unavailable or refuses the layout
+bool circ_encode_maps(CircArgs<float> &a, int nspecies, int rows);
+bool circ_encode_maps(CircArgs<double> &a, int nspecies, int rows);
+// set to non-zero by a kernel whose wait for a TMA copy gave up (bounded
+// wait); read and cleared by circ_take_status
+int circ_take_status();
 
 // launchers (one per element type); kind: SweepKind
 cudaError_t launch_circ(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
