@@ -15,7 +15,7 @@ cudaError_t ensure_dyn_smem(K fn, size_t smem) {
 
 template <typename R, int S, int L>
 cudaError_t launch_first(const CircArgs<R> &a, int nthreads, size_t smem, int nblocks, cudaStream_t s) {
-  auto fn = circ_first_kernel<R, S, L>;
+  auto fn = nthreads == 512 ? circ_first_kernel<R, S, L, 512> : circ_first_kernel<R, S, L, 256>;
   cudaError_t e = ensure_dyn_smem(fn, smem);
   if (e != cudaSuccess) return e;
   fn<<<nblocks, nthreads, smem, s>>>(a);
@@ -145,23 +145,27 @@ cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthread
   blocks_per_sm = 0;
   const void *fn = nullptr;
   const int key = nspecies * 100 + L;
+  const bool big = nthreads == 512;
+#define ETD_FIRST_FN(R_, S_, L_) \
+  (big ? (const void *)circ_first_kernel<R_, S_, L_, 512> : (const void *)circ_first_kernel<R_, S_, L_, 256>)
   if (real_bytes == 4) {
     switch (key) {
-      case 108: fn = (const void *)circ_first_kernel<float, 1, 8>; break;
-      case 116: fn = (const void *)circ_first_kernel<float, 1, 16>; break;
-      case 208: fn = (const void *)circ_first_kernel<float, 2, 8>; break;
-      case 216: fn = (const void *)circ_first_kernel<float, 2, 16>; break;
+      case 108: fn = ETD_FIRST_FN(float, 1, 8); break;
+      case 116: fn = ETD_FIRST_FN(float, 1, 16); break;
+      case 208: fn = ETD_FIRST_FN(float, 2, 8); break;
+      case 216: fn = ETD_FIRST_FN(float, 2, 16); break;
       default: return cudaErrorInvalidValue;
     }
   } else {
     switch (key) {
-      case 104: fn = (const void *)circ_first_kernel<double, 1, 4>; break;
-      case 108: fn = (const void *)circ_first_kernel<double, 1, 8>; break;
-      case 204: fn = (const void *)circ_first_kernel<double, 2, 4>; break;
-      case 208: fn = (const void *)circ_first_kernel<double, 2, 8>; break;
+      case 104: fn = ETD_FIRST_FN(double, 1, 4); break;
+      case 108: fn = ETD_FIRST_FN(double, 1, 8); break;
+      case 204: fn = ETD_FIRST_FN(double, 2, 4); break;
+      case 208: fn = ETD_FIRST_FN(double, 2, 8); break;
       default: return cudaErrorInvalidValue;
     }
   }
+#undef ETD_FIRST_FN
   cudaError_t e = ensure_dyn_smem(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, nthreads, smem);

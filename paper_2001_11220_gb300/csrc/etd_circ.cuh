@@ -3,8 +3,7 @@
 //
 // A block holds `lpb` whole lines of m chunks (p = m L); thread j of a line
 // owns chunk j.  The chunk is staged in shared memory with cp.async (the
-// thread's private slot, padded so that 16-byte reads of consecutive threads
-// fall on distinct bank groups), so the passes keep only running values in
+// thread's private slot), so the passes keep only running values in
 // registers.  Every solve runs as (see etd_circ.h for the algebra):
 //   pass 1: zero-carry chunk summaries F_j, W_j (two FMAs per position, the
 //           weights lambda^t are kernel-parameter constants);
@@ -144,12 +143,12 @@ __host__ __device__ constexpr int qmat(int q) { return q == 4 ? 0 : (q & 1) ? 2 
 // threads).  Persistent: block b takes the line groups b, b + gridDim.x, ...
 // and stages the next group's chunks (cp.async into the other half of its
 // double buffer) while it solves the current one.
-template <typename R, int S, int L>
-__global__ void __launch_bounds__(512) circ_first_kernel(const __grid_constant__ CircArgs<R> A) {
+template <typename R, int S, int L, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const __grid_constant__ CircArgs<R> A) {
   using namespace circ;
   extern __shared__ __align__(16) unsigned char circ_smem[];
   constexpr int VW = 16 / sizeof(R);   // elements per 16 bytes
-  constexpr int CSZ = L + VW;          // padded chunk slot
+  constexpr int CSZ = L;               // chunk slot (unpadded: three blocks fit an SM)
   constexpr int NQ = 5;
   const int m = A.m, tid = threadIdx.x, nthr = blockDim.x;
   const int lb = tid / m, j = tid - lb * m;

@@ -161,8 +161,7 @@ cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthread
 
 // shared memory of a contiguous circulant sweep block of nthreads threads
 inline size_t circ_first_smem(int nspecies, int L, int nthreads, int m, int lpb, size_t real_bytes) {
-  const int pad = (int)(16 / real_bytes);
-  const size_t stage = (size_t)2 * nspecies * nthreads * (L + pad) * real_bytes;  // double buffer
+  const size_t stage = (size_t)2 * nspecies * nthreads * L * real_bytes;  // double buffer
   const int nw = m > 32 ? m / 32 : 1;
   const size_t tot = (size_t)2 * lpb * nw * 5 * nspecies * real_bytes;
   return stage + ((tot + 15) & ~(size_t)15);
