@@ -460,11 +460,11 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
     PF[q] = Ws[q] = R(0);
   }
   // chunks of the block: forward prefix before j, backward composite after j
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < j; ++i)
 #pragma unroll
     for (int q = 0; q < NG; ++q) PF[q] = fma(LM[q], PF[q], xF[(q * XS + i) * NC + c]);
-#pragma unroll 1
+#pragma unroll 4
   for (int i = WB - 1; i > j; --i)
 #pragma unroll
     for (int q = 0; q < NG; ++q)
@@ -504,21 +504,20 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
     const R *tk = tab + sg * TS, *tl = tk + (WB + 1), *tkb = tl + (WB + 1), *tlb = tkb + 17;
     const R LB = tl[WB];  // Lambda^WB
     const R *gF = xF + (size_t)q * XS * NC + c, *gW = xW + (size_t)q * XS * NC + c;
-    R ftot = R(0), pfb = R(0), fr = R(0);
-#pragma unroll 1
-    for (int b = 0; b < cs; ++b) {
-      const R f = gF[b * NC];
-      if (b == rank) {
+    // the forward chain over blocks 0 .. cs-1 and the backward chain over
+    // cs-1 .. 0 are independent: one loop runs both
+    R ftot = R(0), pfb = R(0), fr = R(0), wl = R(0), wsr = R(0);
+#pragma unroll 4
+    for (int i = 0; i < cs; ++i) {
+      const R f = gF[i * NC];
+      if (i == rank) {
         pfb = ftot;
         fr = f;
       }
       ftot = fma(LB, ftot, f);
-    }
-    R wl = R(0), wsr = R(0);
-#pragma unroll 1
-    for (int b = cs - 1; b >= 0; --b) {
+      const int b = cs - 1 - i;
       if (b == rank) wsr = wl;  // composite of the blocks after this one
-      wl = fma(LB, fma(tkb[cs - 1 - b], gF[b * NC], wl), gW[b * NC]);
+      wl = fma(LB, fma(tkb[i], gF[b * NC], wl), gW[b * NC]);
     }
     const R y0 = ftot * M.inv1m;
     const R z0 = fma(tlb[17], y0, wl) * M.inv1m;  // K_{mL}
