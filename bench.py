@@ -85,7 +85,10 @@ def _traffic(kernel: str, workload: str, tile: str):
             tab = json.load(f)
     except Exception:
         return None
-    ent = tab.get(workload, {}).get(kernel)
+    wl = tab.get(workload, {})
+    ent = wl.get(kernel)
+    if not ent or ent.get("tile") != tile:   # captures of other tile shapes of the same kernel
+        ent = wl.get(kernel + "_by_tile", {}).get(tile)
     if not ent or ent.get("csrc_hash") != _csrc_hash() or ent.get("tile") != tile:
         return None
     return float(ent["dram_bytes_per_launch"])
