@@ -145,6 +145,32 @@ def test_mms3d_full_run(p):
     assert e32 <= 1e-5
 
 
+def test_mms3d_convergence_full_runs_fp64_and_fp32():
+    """Second order in k = h on the manufactured 3D Dirichlet problem (Section 8.1's
+    check, here on the GPU): full runs to T = 1 at p = 32, 64, 128, 256 in FP64 and
+    FP32, error against the exact solution e^{-t} sin sin sin.  FP64 matches the
+    oracle at p <= 64; the observed order of the FP64 errors approaches 2 (the
+    oracle's own pin: 1.92, 1.96 from p = 15 to 63), and FP32 reaches the same
+    accuracy as FP64 at every size (its rounding stays below the scheme's error)."""
+    errs = {"fp64": [], "fp32": []}
+    for p in (32, 64, 128, 256):
+        w = W.mms_3d(p)
+        U0 = W.initial_state(w)
+        exact = W.exact_mms(w, w.steps * w.k)
+        for prec in ("fp64", "fp32"):
+            got = gpu_run(w, U0, w.steps, prec)
+            errs[prec].append(float(np.max(np.abs(got - exact)) / np.max(np.abs(exact))))
+            if prec == "fp64" and p <= 64:
+                assert rel_err(got, oracle_run(w, U0, w.steps)) <= FP64_TOL
+    eoc = {k: [math.log(v[i] / v[i + 1]) / math.log((2 * 32 * 2 ** i + 1) / (32 * 2 ** i + 1)) for i in range(3)]
+           for k, v in errs.items()}
+    print(f"mms3d T = 1 errors vs exact: FP64 {errs['fp64']}, FP32 {errs['fp32']}; EOC FP64 {eoc['fp64']}, "
+          f"FP32 {eoc['fp32']}")
+    assert all(1.85 < e < 2.15 for e in eoc["fp64"]), eoc
+    for a, b in zip(errs["fp32"], errs["fp64"]):
+        assert abs(a - b) <= 0.3 * b, (a, b)
+
+
 def test_mms3d_256_one_step_full_size():
     """3D Dirichlet manufactured problem at the benchmark size 256^3, one step, FP64 and FP32."""
     w = W.mms_3d(256)
