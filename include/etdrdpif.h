@@ -172,13 +172,36 @@ etd_status etd_run_vjp(etd_ctx *ctx, const void *U0, double t0, int64_t nsteps, 
 
 /* Batched ensemble: ninst independent problems (grids[i], D[i*nspecies ..],
  * reactions[i]; all instances share nspecies, dim and precision; k is
- * common) advanced together, one launch per sweep kind covering every
- * instance.  etd_batch_run takes an array of ninst device state pointers
- * (host array).  Other entry points reject batched contexts. */
+ * common; ninst < 2^24) advanced together.  Each time step is ONE persistent
+ * kernel launch (Section 7's step on every instance): resident blocks take
+ * (axis, instance, line block) work items from a device queue ordered so
+ * that every item's dependencies -- all blocks of the previous sweep of the
+ * same instance -- come earlier, and wait for them on per-instance
+ * completion counters with a bounded wait.  Multi-step runs are captured
+ * into a CUDA graph and replayed.  (ETD_ENSEMBLE_PERSISTENT=0 in the
+ * environment at create time selects one launch per sweep kind instead.)
+ * etd_batch_run takes an array of ninst device state pointers (host array),
+ * synchronises the context's stream and returns ETD_ERR_TIMEOUT if a
+ * dependency wait gave up (the states are then incomplete; the counters are
+ * reset and the context stays usable).  Other entry points reject batched
+ * contexts. */
 etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *D,
                             const etd_reaction *reactions, double k, int32_t precision,
                             void *stream, etd_ctx **out);
 etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps);
+
+/* Limit of each dependency wait of the persistent ensemble step, in seconds
+ * (default 1; (0, 60]).  ETD_ERR_INVALID_ARG on a single-problem context or
+ * a limit outside the range. */
+etd_status etd_batch_set_wait_limit(etd_ctx *ctx, double seconds);
+
+/* Test hook of the bounded waits.  Seeds the completion counter of sweep
+ * `axis` (0 .. dim-2) of instance `instance` with a value the next step's
+ * blocks cannot raise to its target, so the first wait on it runs out and
+ * the next etd_batch_run returns ETD_ERR_TIMEOUT (naming instance and
+ * axis + 1).  Synchronises.  ETD_ERR_INVALID_ARG on indices out of range or
+ * a context without the persistent step. */
+etd_status etd_batch_debug_hold(etd_ctx *ctx, int32_t instance, int32_t axis);
 
 /* Choose the ensemble's line-block shapes (the chunk length of every axis,
  * shared by all instances; each instance then fills the common block size

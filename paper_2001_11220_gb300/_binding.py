@@ -19,7 +19,8 @@ ETD_FP64, ETD_FP32 = 0, 1
 
 # every symbol include/etdrdpif.h declares
 EXPORTS = ["etd_create", "etd_step", "etd_run", "etd_run_host", "etd_step_adjoint", "etd_grad", "etd_run_vjp",
-           "etd_batch_create", "etd_batch_run", "etd_batch_autotune", "etd_autotune", "etd_set_stream", "etd_profile",
+           "etd_batch_create", "etd_batch_run", "etd_batch_autotune", "etd_batch_set_wait_limit",
+           "etd_batch_debug_hold", "etd_autotune", "etd_set_stream", "etd_profile",
            "etd_profile_read", "etd_get_info", "etd_step_noalloc",
            "etd_last_error", "etd_destroy"]
 
@@ -72,6 +73,8 @@ def load() -> ctypes.CDLL:
         "etd_batch_create": ([i32, ctypes.POINTER(etd_grid), dptr, ctypes.POINTER(etd_reaction), dbl, i32, vp, pp], i32),
         "etd_batch_run": ([vp, pp, dbl, i64], i32),
         "etd_batch_autotune": ([vp, pp], i32),
+        "etd_batch_set_wait_limit": ([vp, dbl], i32),
+        "etd_batch_debug_hold": ([vp, i32, i32], i32),
         "etd_autotune": ([vp, vp], i32),
         "etd_set_stream": ([vp, vp], i32),
         "etd_profile": ([vp, i32], i32),

@@ -161,7 +161,9 @@ class EtdRdpIf:
 class EtdEnsemble:
     """Many independent problems (same dimension, species count, precision and
     time step; any grid size, boundaries, coefficients and reaction parameters)
-    advanced together: one kernel launch per sweep kind covers every instance."""
+    advanced together: one persistent kernel launch per time step covers every
+    sweep of every instance (work queue, per-instance completion counters,
+    bounded waits; a wait that runs out raises EtdError ETD_ERR_TIMEOUT)."""
 
     def __init__(self, workloads, precision="fp32", stream=None):
         self.lib = B.load()
@@ -197,6 +199,15 @@ class EtdEnsemble:
         ptrs = (ctypes.c_void_p * self.n)(*[U.data_ptr() for U in states])
         B.check(self.lib.etd_batch_run(self.ctx, ptrs, float(t0), int(nsteps)), self.ctx)
         return states
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of each dependency wait inside the step kernel (default 1 s)."""
+        B.check(self.lib.etd_batch_set_wait_limit(self.ctx, float(seconds)), self.ctx)
+
+    def debug_hold(self, instance: int, axis: int = 0):
+        """Test hook: the next run's wait on sweep `axis` of `instance` never
+        releases, so that run raises ETD_ERR_TIMEOUT."""
+        B.check(self.lib.etd_batch_debug_hold(self.ctx, int(instance), int(axis)), self.ctx)
 
     def autotune(self, work_states):
         """Pick the line-block shapes by timing candidates; work_states are scratch

@@ -199,6 +199,8 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
     int nlb = pow2_floor(std::min(32, std::max(1, max_threads / P.m)));
     if (reg_force && nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
     while (nlb > 1 && nlb / 2 >= P.nlines) nlb /= 2;
+    // short lines: many lines per block, but their exchange buffers must fit
+    while (nlb > 1 && sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes) > 200 * 1024) nlb /= 2;
     P.nlb = nlb;
     P.nlo_blocks = 1;
     P.nblocks = (int)((P.nlines + nlb - 1) / nlb);
@@ -208,6 +210,7 @@ bool plan_axis_ex(Instance &I, int a, int L, int max_threads, int nlb_force, boo
     nlb = (int)std::min<long long>(nlb, ((st + 31) / 32) * 32);
     nlb = std::max(1, nlb);
     if (reg_force && nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
+    while (nlb > 1 && sweep_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes) > 200 * 1024) nlb /= 2;
     P.nlb = nlb;
     P.nlo_blocks = (int)((st + nlb - 1) / nlb);
     const long long nhi = I.N / (st * n);
@@ -1070,6 +1073,7 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
   launches = 0;
   for (int a = 0; a < I.dim; ++a)
     launches += ctx->batched || I.plan[a].nseg <= 1 || I.plan[a].cluster ? 1 : (I.plan[a].kind == SWEEP_LAST ? 5 : 3);
+  if (ctx->batched && ctx->ens_on) launches = 1;  // one persistent launch covers every sweep
   for (const Instance &J : ctx->inst)
     for (int a = 0; a < J.dim; ++a)
       if (J.plan[a].nseg > 1 && J.plan[a].seg_buf) scratch += (long long)J.plan[a].seg_bytes;
@@ -1084,7 +1088,8 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     info->lines_per_block[a] = I.plan[a].nlb;
     info->staged[a] = I.plan[a].circ ? 5 : I.plan[a].nseg > 1 ? (I.plan[a].cluster ? 4 : 3) : I.plan[a].sp.staged;
     info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
-    info->grid_blocks[a] = I.plan[a].nblocks;
+    info->grid_blocks[a] = ctx->batched ? (ctx->ens_on ? ctx->ens_grid : ctx->batch_total_blocks[a])
+                                        : I.plan[a].nblocks;
   }
   return ETD_OK;
 }
@@ -1111,6 +1116,10 @@ void etd_destroy(etd_ctx *ctx) {
     if (ctx->batch_args[a]) cudaFree(ctx->batch_args[a]);
     if (ctx->batch_block_start[a]) cudaFree(ctx->batch_block_start[a]);
   }
+  if (ctx->ens_items) cudaFree(ctx->ens_items);
+  if (ctx->ens_queue) cudaFree(ctx->ens_queue);
+  if (ctx->ens_done) cudaFree(ctx->ens_done);
+  if (ctx->ens_status) cudaFree(ctx->ens_status);
   if (ctx->adj_ws) cudaFree(ctx->adj_ws);
   for (void *p : ctx->adj_ubar)
     if (p) cudaFree(p);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/etdrdpif.h"
@@ -61,6 +62,88 @@ etd_status upload_batch_args(etd_ctx *ctx, void *const *U) {
   return ETD_OK;
 }
 
+template <typename R>
+cudaError_t ensemble_launch(etd_ctx *ctx, const EnsArgs<R> &E, cudaStream_t s, int *resident) {
+  const Instance &I0 = ctx->inst[0];
+  const int LS = I0.dim > 1 ? ctx->batch_L[1] : ctx->batch_L[0];
+  if (I0.dim == 2)
+    return launch_ensemble_2d(E, I0.S, ctx->batch_L[0], LS, ctx->ens_threads, ctx->ens_smem, ctx->ens_grid, s,
+                              resident);
+  return launch_ensemble_3d(E, I0.S, ctx->batch_L[0], LS, ctx->ens_threads, ctx->ens_smem, ctx->ens_grid, s,
+                            resident);
+}
+
+// Work list of the persistent step.  Instances are taken in groups whose
+// scratch (3 fields) adds up to about ens_window_mb; group g's sweep a is
+// queued in round g + a, after the first sweep of group g + a, so every item
+// comes after the items it depends on (sweep a - 1 of its instance, one round
+// earlier) and the scratch a group writes is read back while it may still be
+// in L2.  ens_window_mb = 0: one group (every instance's sweep 0, then 1, ...).
+etd_status plan_ensemble_step(etd_ctx *ctx) {
+  const int ninst = (int)ctx->inst.size();
+  const int dim = ctx->inst[0].dim;
+  std::vector<int> gstart(1, 0);
+  if (ctx->ens_window_mb > 0) {
+    const double win = ctx->ens_window_mb * 1048576.0;
+    double acc = 0;
+    for (int i = 0; i < ninst; ++i) {
+      const Instance &I = ctx->inst[i];
+      const double b = 3.0 * I.S * (double)I.N * I.real_bytes;
+      if (acc > 0 && acc + b > win) {
+        gstart.push_back(i);
+        acc = 0;
+      }
+      acc += b;
+    }
+  }
+  gstart.push_back(ninst);
+  const int G = (int)gstart.size() - 1;
+  std::vector<int2> items;
+  for (int r = 0; r < G + dim - 1; ++r)
+    for (int a = 0; a < dim; ++a) {
+      const int g = r - a;
+      if (g < 0 || g >= G) continue;
+      for (int i = gstart[g]; i < gstart[g + 1]; ++i)
+        for (int b = 0; b < ctx->inst[i].plan[a].nblocks; ++b) items.push_back(make_int2((a << 24) | i, b));
+    }
+  if (ninst >= (1 << 24)) return fail(ctx, ETD_ERR_UNSUPPORTED, "more than 2^24 instances");
+  if (ctx->ens_items && (int)items.size() != ctx->ens_nitems) {
+    cudaFree(ctx->ens_items);
+    ctx->ens_items = nullptr;
+  }
+  if (!ctx->ens_items && cudaMalloc((void **)&ctx->ens_items, sizeof(int2) * items.size()) != cudaSuccess)
+    return fail(ctx, ETD_ERR_OOM, "ensemble work list");
+  ctx->ens_nitems = (int)items.size();
+  if (cudaMemcpy(ctx->ens_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(ctx, ETD_ERR_CUDA, "ensemble work list upload");
+  if (!ctx->ens_queue) {
+    if (cudaMalloc((void **)&ctx->ens_queue, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->ens_done, sizeof(int) * (size_t)std::max(1, dim - 1) * ninst) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->ens_status, sizeof(int) * ENS_STATUS_WORDS) != cudaSuccess)
+      return fail(ctx, ETD_ERR_OOM, "ensemble counters");
+    if (cudaMemset(ctx->ens_queue, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ctx->ens_done, 0, sizeof(int) * (size_t)std::max(1, dim - 1) * ninst) != cudaSuccess ||
+        cudaMemset(ctx->ens_status, 0, sizeof(int) * ENS_STATUS_WORDS) != cudaSuccess)
+      return fail(ctx, ETD_ERR_CUDA, "ensemble counters");
+  }
+  int thr = 0;
+  size_t smem = 0;
+  for (int a = 0; a < dim; ++a) {
+    thr = std::max(thr, ctx->batch_threads[a]);
+    smem = std::max(smem, ctx->batch_smem[a]);
+  }
+  ctx->ens_threads = (thr + 31) / 32 * 32;
+  ctx->ens_smem = smem;
+  int resident = 0;
+  cudaError_t e;
+  if (ctx->precision == ETD_FP64) e = ensemble_launch<double>(ctx, EnsArgs<double>{}, nullptr, &resident);
+  else e = ensemble_launch<float>(ctx, EnsArgs<float>{}, nullptr, &resident);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ensemble step kernel occupancy");
+  if (resident < 1) return fail(ctx, ETD_ERR_UNSUPPORTED, "ensemble step kernel does not fit an SM");
+  ctx->ens_grid = std::min(resident, ctx->ens_nitems);
+  return ETD_OK;
+}
+
 // Plan every instance's sweeps with chunk length Lax[a] on axis a, rebuild
 // their line tables, let instances fill the common block size with more
 // lines, and (re)build the block prefix sums of the launches.
@@ -68,10 +151,12 @@ etd_status plan_batch(etd_ctx *ctx, const int *Lax) {
   const int ninst = (int)ctx->inst.size();
   const int dim = ctx->inst[0].dim;
   const int rb = ctx->inst[0].real_bytes;
+  if (ctx->ens_on && dim == 3 && Lax[1] != Lax[2])
+    return fail(ctx, ETD_ERR_UNSUPPORTED, "persistent ensemble step: axes 1 and 2 share one chunk length");
   for (int i = 0; i < ninst; ++i) {
     Instance &I = ctx->inst[i];
     for (int a = 0; a < dim; ++a) {
-      if (!plan_axis_ex(I, a, Lax[a], ETD_MAX_BLOCK_THREADS, 0, true, 1))
+      if (!plan_axis_ex(I, a, Lax[a], ctx->ens_on ? ctx->ens_max_threads : ETD_MAX_BLOCK_THREADS, 0, true, 1))
         return fail(ctx, ETD_ERR_UNSUPPORTED, "instance %d axis %d does not fit one block", i, a);
     }
   }
@@ -79,9 +164,14 @@ etd_status plan_batch(etd_ctx *ctx, const int *Lax) {
   // many lines per block as fit that size (small instances would otherwise
   // leave most of each block idle)
   const char *nofill = std::getenv("ETD_BATCH_NOFILL");
+  // (persistent step: one block size for every axis)
+  int Tall = 0;
+  for (int a = 0; a < dim; ++a)
+    for (int i = 0; i < ninst; ++i) Tall = std::max(Tall, ctx->inst[i].plan[a].nthreads);
   for (int a = 0; a < dim && !(nofill && nofill[0] == '1'); ++a) {
     int T = 0;
     for (int i = 0; i < ninst; ++i) T = std::max(T, ctx->inst[i].plan[a].nthreads);
+    if (ctx->ens_on) T = Tall;
     for (int i = 0; i < ninst; ++i) {
       Instance &I = ctx->inst[i];
       AxisPlan &P = I.plan[a];
@@ -130,6 +220,10 @@ etd_status plan_batch(etd_ctx *ctx, const int *Lax) {
         cudaSuccess)
       return fail(ctx, ETD_ERR_CUDA, "ensemble launch tables upload");
   }
+  if (ctx->ens_on) {
+    etd_status st = plan_ensemble_step(ctx);
+    if (st != ETD_OK) return st;
+  }
   // arguments and captured graphs refer to the old plan: rebuild on the next run
   drop_graphs(ctx);
   ctx->batch_states.clear();
@@ -157,6 +251,14 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
   ctx->stream = (cudaStream_t)stream;
   ctx->precision = precision;
   ctx->batched = true;
+  // one persistent launch per step unless ETD_ENSEMBLE_PERSISTENT=0 (one launch per sweep kind)
+  const char *pe = std::getenv("ETD_ENSEMBLE_PERSISTENT");
+  ctx->ens_on = !(pe && pe[0] == '0');
+  if (const char *w = std::getenv("ETD_ENSEMBLE_WINDOW_MB")) ctx->ens_window_mb = std::max(0.0, atof(w));
+  if (const char *t = std::getenv("ETD_ENSEMBLE_THREADS")) {
+    const int v = atoi(t);
+    if (v == 128 || v == 256 || v == 512) ctx->ens_max_threads = v;
+  }
   ctx->inst.resize(ninst);
   const int dim = grids[0].dim;
   const int rb = precision == ETD_FP64 ? 8 : 4;
@@ -217,6 +319,50 @@ etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps
   }
   const Instance &I0 = ctx->inst[0];
   const double k = I0.k;
+  if (ctx->ens_on) {
+    auto enqueue_ens = [&](cudaStream_t s, int64_t n) -> cudaError_t {
+      const double t = t0 + (double)n * k;
+      auto fill = [&](auto &E) {
+        using R = std::remove_reference_t<decltype(E.exp_mt[0])>;
+        for (int a = 0; a < 3; ++a) {
+          E.args[a] = a < I0.dim ? (const SweepArgs<R> *)ctx->batch_args[a] : nullptr;
+          E.t_eval[a] = a == I0.dim - 1 ? t + k : t;
+          E.exp_mt[a] = (R)std::exp(-E.t_eval[a]);
+        }
+        E.items = ctx->ens_items;
+        E.nitems = ctx->ens_nitems;
+        E.ninst = ninst;
+        E.queue = ctx->ens_queue;
+        E.done = ctx->ens_done;
+        E.status = ctx->ens_status;
+        E.wait_ns = (long long)(ctx->ens_wait_s * 1e9);
+      };
+      if (ctx->precision == ETD_FP64) {
+        EnsArgs<double> E{};
+        fill(E);
+        return ensemble_launch<double>(ctx, E, s, nullptr);
+      }
+      EnsArgs<float> E{};
+      fill(E);
+      return ensemble_launch<float>(ctx, E, s, nullptr);
+    };
+    etd_status st = run_steps(ctx, enqueue_ens, GraphKey{ctx->batch_states.data(), nullptr, t0, nsteps}, nsteps);
+    if (st != ETD_OK) return st;
+    // the waits' status: ETD_ERR_TIMEOUT if one gave up (the steps after it are skipped)
+    int status[ENS_STATUS_WORDS] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(status, ctx->ens_status, sizeof(status), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ensemble step status");
+    if (status[0]) {
+      cudaMemsetAsync(ctx->ens_status, 0, sizeof(int) * ENS_STATUS_WORDS, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      return fail(ctx, ETD_ERR_TIMEOUT,
+                  "ensemble step: the wait of instance %d axis %d for sweep %d gave up after %g s; the run is "
+                  "incomplete",
+                  status[1], status[2], status[2] - 1, ctx->ens_wait_s);
+    }
+    return ETD_OK;
+  }
   auto enqueue = [&](cudaStream_t s, int64_t n) -> cudaError_t {
     const double t = t0 + (double)n * k;
     for (int a = 0; a < I0.dim; ++a) {
@@ -258,6 +404,7 @@ etd_status etd_batch_autotune(etd_ctx *ctx, void *const *U_work) {
   for (int c = 0; c < (1 << dim) && st == ETD_OK; ++c) {
     int Lax[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) Lax[a] = choices[(c >> a) & 1];
+    if (ctx->ens_on && dim == 3 && Lax[1] != Lax[2]) continue;  // one chunk length on axes 1 and 2
     if (plan_batch(ctx, Lax) != ETD_OK) continue;  // this shape does not fit every instance
     st = etd_batch_run(ctx, U_work, 0.0, 2);       // warm-up (arguments, graph)
     if (st != ETD_OK) break;
@@ -278,6 +425,33 @@ etd_status etd_batch_autotune(etd_ctx *ctx, void *const *U_work) {
   cudaEventDestroy(e1);
   if (st != ETD_OK) return st;
   return plan_batch(ctx, best_ms < 1e30 ? best : keep);
+}
+
+etd_status etd_batch_set_wait_limit(etd_ctx *ctx, double seconds) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_batch_set_wait_limit on a single-problem context");
+  if (!(seconds > 0.0) || !(seconds <= 60.0))
+    return fail(ctx, ETD_ERR_INVALID_ARG, "wait limit %g s outside (0, 60]", seconds);
+  ctx->ens_wait_s = seconds;
+  drop_graphs(ctx);  // the limit is a launch argument of the captured steps
+  return ETD_OK;
+}
+
+etd_status etd_batch_debug_hold(etd_ctx *ctx, int32_t instance, int32_t axis) {
+  if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->batched || !ctx->ens_on)
+    return fail(ctx, ETD_ERR_INVALID_ARG, "etd_batch_debug_hold needs a batched context with the persistent step");
+  const int ninst = (int)ctx->inst.size();
+  const int dim = ctx->inst[0].dim;
+  if (instance < 0 || instance >= ninst || axis < 0 || axis > dim - 2)
+    return fail(ctx, ETD_ERR_INVALID_ARG, "instance %d axis %d out of range", instance, axis);
+  // a counter this far below zero cannot reach its target (the blocks of one sweep) in a launch
+  const int seed = -(1 << 30);
+  cudaError_t e = cudaMemcpyAsync(ctx->ens_done + (size_t)axis * ninst + instance, &seed, sizeof(int),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // host value must outlive the copy
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ensemble counter seed");
+  return ETD_OK;
 }
 
 }  // extern "C"

@@ -138,6 +138,19 @@ struct etd_ctx {
   int batch_L[3] = {0, 0, 0};
   std::vector<void *> batch_states;  // state pointers the device args were built for
   void *batch_scratch = nullptr;     // scratch of every instance, one allocation
+  // persistent ensemble step (one launch per step): work list, counters, status
+  bool ens_on = false;               // else one launch per sweep kind
+  int2 *ens_items = nullptr;         // (axis << 24 | instance, block), dependencies first
+  int ens_nitems = 0;
+  unsigned *ens_queue = nullptr;     // [2], reset by each launch's last block
+  int *ens_done = nullptr;           // [dim - 1][ninst] finished blocks, reset likewise
+  int *ens_status = nullptr;         // ENS_STATUS_WORDS
+  int ens_threads = 0;
+  size_t ens_smem = 0;
+  int ens_grid = 0;
+  int ens_max_threads = 256;         // largest block of the persistent step (2 resident per SM)
+  double ens_wait_s = 1.0;           // limit of one dependency wait
+  double ens_window_mb = 0.0;        // scratch MB per instance group of the interleaved order (0: by axis)
   // per-sweep profiling (etd_profile)
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;

@@ -153,6 +153,36 @@ cudaError_t launch_sweep_batched(const SweepArgs<double> *args_dev, const int *b
                                  int total_blocks, int nspecies, int L, int kind, int nthreads,
                                  size_t smem, cudaStream_t s, double t_eval);
 
+// Persistent ensemble step (etd_ensemble.cuh): one launch advances every
+// instance of a batched context by one step.
+// status words: [0] non-zero once a dependency wait gave up, [1] instance,
+// [2] axis of the first wait that gave up
+constexpr int ENS_STATUS_WORDS = 4;
+
+template <typename R> struct EnsArgs {
+  const SweepArgs<R> *args[3];  // per axis: SweepArgs of every instance (device)
+  const int2 *items;            // work list: x = axis << 24 | instance, y = block of that sweep
+  int nitems;
+  int ninst;
+  unsigned *queue;              // [0] next item, [1] blocks that have left the loop
+  int *done;                    // [axis][instance]: finished blocks (axes 0 .. dim - 2)
+  int *status;                  // ENS_STATUS_WORDS words
+  long long wait_ns;            // limit of one dependency wait (%globaltimer)
+  double t_eval[3];             // time at which each sweep evaluates F
+  R exp_mt[3];                  // e^{-t_eval} in R
+};
+
+// L0: chunk length of axis 0, LS: of axes 1 and 2.  resident != nullptr:
+// only report the blocks resident at once (blocks per SM x SMs)
+cudaError_t launch_ensemble_2d(const EnsArgs<float> &E, int nspecies, int L0, int LS, int nthreads, size_t smem,
+                               int grid, cudaStream_t s, int *resident);
+cudaError_t launch_ensemble_3d(const EnsArgs<float> &E, int nspecies, int L0, int LS, int nthreads, size_t smem,
+                               int grid, cudaStream_t s, int *resident);
+cudaError_t launch_ensemble_2d(const EnsArgs<double> &E, int nspecies, int L0, int LS, int nthreads, size_t smem,
+                               int grid, cudaStream_t s, int *resident);
+cudaError_t launch_ensemble_3d(const EnsArgs<double> &E, int nspecies, int L0, int LS, int nthreads, size_t smem,
+                               int grid, cudaStream_t s, int *resident);
+
 // cluster-segmented register sweeps (a.segphase = SEG_CLUSTER; FP32 L = 8 or
 // 16, FP64 L = 4 or 8): the launch, and the clusters that fit on the device
 // at once (0: the configuration cannot launch)

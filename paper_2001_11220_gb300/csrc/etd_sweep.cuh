@@ -36,6 +36,12 @@ namespace etd {
 
 template <typename R>
 __device__ __forceinline__ R ld_nc(const R *p) { return __ldg(p); }
+// COH: the data may have been written earlier in the same launch (persistent
+// ensemble step): load at the L2 (.cg), never through the read-only path
+template <bool COH, typename R>
+__device__ __forceinline__ R ld_in(const R *p) {
+  if constexpr (COH) return __ldcg(p); else return __ldg(p);
+}
 
 // ------------------------------------------------------------ lane values
 // V = R (one line per thread) or float2 (a pair of neighbouring lines).  For
@@ -191,6 +197,18 @@ __device__ __forceinline__ void ld32B(const double *p, double *v) {
                : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
                : "l"(p));
 }
+__device__ __forceinline__ void ld32B_cg(const float *p, float *v) {
+  asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void ld32B_cg(const double *p, double *v) {
+  asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];\n"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p)
+               : "memory");
+}
 __device__ __forceinline__ void st32B(float *p, const float *v) {
   asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(v[0]), "f"(v[1]),
                "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
@@ -201,13 +219,15 @@ __device__ __forceinline__ void st32B(double *p, const double *v) {
                : "memory");
 }
 
-template <typename R, int L, bool CONTIG>
+template <typename R, int L, bool CONTIG, bool COH = false>
 __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, long long off, long long st,
                                            int cnt) {
   if constexpr (CONTIG && L % (32 / sizeof(R)) == 0) {
     if (cnt == L && ((reinterpret_cast<uintptr_t>(p + off) & 31) == 0)) {
 #pragma unroll
-      for (int t = 0; t < L; t += 32 / sizeof(R)) ld32B(p + off + t, v + t);
+      for (int t = 0; t < L; t += 32 / sizeof(R)) {
+        if constexpr (COH) ld32B_cg(p + off + t, v + t); else ld32B(p + off + t, v + t);
+      }
       return;
     }
   }
@@ -219,13 +239,13 @@ __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, l
       if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int t = 0; t < L; t += 4) {
-          float4 q = __ldg(reinterpret_cast<const float4 *>(p + off + t));
+          float4 q = ld_in<COH>(reinterpret_cast<const float4 *>(p + off + t));
           v[t] = q.x; v[t + 1] = q.y; v[t + 2] = q.z; v[t + 3] = q.w;
         }
       } else {
 #pragma unroll
         for (int t = 0; t < L; t += 2) {
-          double2 q = __ldg(reinterpret_cast<const double2 *>(p + off + t));
+          double2 q = ld_in<COH>(reinterpret_cast<const double2 *>(p + off + t));
           v[t] = q.x; v[t + 1] = q.y;
         }
       }
@@ -237,15 +257,15 @@ __device__ __forceinline__ void load_chunk(R (&v)[L], const R *__restrict__ p, l
     const int s32 = (int)st;
     if (cnt == L) {
 #pragma unroll
-      for (int t = 0; t < L; ++t) v[t] = ld_nc(q + t * s32);
+      for (int t = 0; t < L; ++t) v[t] = ld_in<COH>(q + t * s32);
     } else {
 #pragma unroll
-      for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_nc(q + t * s32) : R(0);
+      for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_in<COH>(q + t * s32) : R(0);
     }
     return;
   }
 #pragma unroll
-  for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_nc(q + (long long)t * st) : R(0);
+  for (int t = 0; t < L; ++t) v[t] = (t < cnt) ? ld_in<COH>(q + (long long)t * st) : R(0);
 }
 
 template <typename R, int L, bool CONTIG>
@@ -1536,7 +1556,8 @@ __device__ __forceinline__ void store_pairs(const float2 (&v)[L], float2 *__rest
 // PK = 2) and, for segmented sweeps, per segment of mx chunks of those lines;
 // inputs loaded straight from global memory (vector loads on x, coalesced row
 // segments on strided axes).
-template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false>
+// COH: inputs may have been written earlier in the same launch (coherent loads)
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false, bool COH = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
                                             R exp_mt) {
   (void)t_eval;
@@ -1560,6 +1581,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
   if constexpr (PK == 2) {
     // strided axis, even stride: pair l covers lines lo, lo + 1 of one row
     static_assert(!CONTIG && sizeof(R) == 4, "line pairs: FP32 strided sweeps");
+    static_assert(!COH, "line pairs: read-only inputs");
     const long long lo0 = (long long)(lb % A.nlo_blocks) * nlb * 2;
     const long long lo = lo0 + 2 * l;
     const long long hi = lb / A.nlo_blocks;
@@ -1619,7 +1641,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     c.sc = sc;
     const long long off0 = base + (long long)c.i0 * st;
     const int cnt = c.cnt;
-    auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG>(v, A.in[f] + s * N, off0, st, cnt); };
+    auto load = [&](int f, int s, R (&v)[L]) { load_chunk<R, L, CONTIG, COH>(v, A.in[f] + s * N, off0, st, cnt); };
     auto store = [&](int f, int s, const R (&v)[L]) {
       store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt);
     };
