@@ -412,7 +412,7 @@ bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc) {
   const long long ngroups = (long long)P.nlo_blocks * (I.N / (st * n));
   if (ngroups > INT_MAX / 2) return false;
   P.smem = circ_strided_smem(I.S, L, wb, nc, I.real_bytes);
-  if (P.smem > 227 * 1024) return false;
+  if (P.smem + CIRC_STRIDED_STATIC_SMEM > 227 * 1024) return false;
   // persistent launch: as many clusters (cs > 1) or blocks as the device holds
   // at once, each walking the line groups
   int ncl = 0;

@@ -116,22 +116,88 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
-// Bounded wait for phase `parity` of an mbarrier: gives up after 2^24 polls
-// (each poll may suspend the thread for a while), returning false; the
-// caller records the failure and carries on so that every block of a
-// cluster still reaches the same barriers.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// distributed shared memory: this CTA's shared address `a` in cluster block `rank`
+__device__ __forceinline__ unsigned mapa_u32(unsigned a, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// asynchronous stores into another block's shared memory, each completing its
+// byte count on that block's mbarrier (no ordering with this block's other
+// memory operations: nothing waits for its global stores)
+__device__ __forceinline__ void st_async(unsigned ra, float v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];\n" ::"r"(ra), "f"(v),
+               "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned ra, double v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];\n" ::"r"(ra), "d"(v),
+               "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async2(unsigned ra, float a, float b, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(ra),
+               "f"(a), "f"(b), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async2(unsigned ra, double a, double b, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];\n" ::"r"(ra),
+               "d"(a), "d"(b), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async4(unsigned ra, float a, float b, float c, float d, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];\n" ::"r"(
+                   ra),
+               "f"(a), "f"(b), "f"(c), "f"(d), "r"(rbar)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier: gives up after 0.25 s of
+// %globaltimer (or 2^22 polls), or at once once an earlier wait of this block
+// gave up (*fail, shared, set here), returning false; the caller records the
+// failure in g_circ_status and carries on so that every block of a cluster
+// still reaches the same barriers and the launch ends.
+__device__ __forceinline__ unsigned long long circ_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_wait_t(unsigned long long *bar, unsigned parity, int *fail) {
   const unsigned a = smem_u32(bar);
-  for (int it = 0; it < (1 << 24); ++it) {
+  unsigned long long t0 = 0;
+  for (int it = 0; it < (1 << 22); ++it) {
     unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if constexpr (CLUSTER)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, "
+          "1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
     if (ok) return true;
+    if ((it & 63) == 0) {
+      if (*(volatile int *)fail != 0) return false;
+      const unsigned long long t = circ_globaltimer();
+      if (it == 0) t0 = t;
+      else if (t - t0 > 250000000ull) break;
+    }
   }
+  *(volatile int *)fail = 1;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *fail) {
+  return mbar_wait_t<false>(bar, parity, fail);
+}
+// acquiring at cluster scope (phases completed by other blocks' st.async)
+__device__ __forceinline__ bool mbar_wait_cluster(unsigned long long *bar, unsigned parity, int *fail) {
+  return mbar_wait_t<true>(bar, parity, fail);
 }
 
 // solve q of species s: 0 T on U, 1 S on U, 2 T on F, 3 S on F, 4 P on U + k F
@@ -541,6 +607,127 @@ __device__ __forceinline__ void strided_exchange(const CircArgs<R> &A, MatIdx mi
   }
 }
 
+// Exchange number x of a line split over a cluster (cs > 1), push form.
+// The block's two exchange buffers alternate: exchange x receives the cluster's
+// block composites in buf[x & 1] ([F, W][cs][NC][NG]) and composes its own
+// chunks in buf[(x + 1) & 1] ([F, W][NG][WB][NC]).  The block's composites
+// go to every other block's receive buffer by st.async, which completes their
+// bytes on that block's mbarrier xbar[x & 1]; the wait is on this block's own
+// barrier and on nothing of the sender's other memory traffic (a cluster
+// barrier's release would first drain the sender's outstanding global stores).
+// Reuse needs no further barrier: a block pushes exchange x + 1 only after it
+// received this block's exchange-x push, which this block sends after its
+// last read of buf[(x + 1) & 1] for exchange x - 1 and before its composition
+// in it; likewise for x + 2 into buf[x & 1].  xbar[x & 1] is re-armed for
+// exchange x + 2 (ng_next2 solves) once exchange x has been read.
+template <typename R, int WB, int NC, int NG, typename MatIdx>
+__device__ __forceinline__ void strided_exchange_push(const CircArgs<R> &A, MatIdx mi, const R (&F)[NG],
+                                                      const R (&W)[NG], R (&Yc)[NG], R (&Zc)[NG], R *buf0, R *buf1,
+                                                      unsigned long long *xbar, int x, int ng_next2, R *car,
+                                                      const R *tab, int j, int c, int w, int h, int rank, int tid,
+                                                      int *fail) {
+  static_assert(WB > 1, "the first and last chunk of a block are different threads");
+  constexpr int TS = 2 * (WB + 1) + 35;
+  const int cs = A.cs;
+  R *rb = (x & 1) ? buf1 : buf0;
+  R *xF = (x & 1) ? buf0 : buf1;
+  R *xW = xF + NG * WB * NC;
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    xF[(q * WB + j) * NC + c] = F[q];
+    xW[(q * WB + j) * NC + c] = W[q];
+  }
+  __syncthreads();
+  R PF[NG], Ws[NG], LM[NG];
+  const R *Kq[NG];
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    LM[q] = A.mat[mi(q) / 3][mi(q) % 3].lamL;
+    Kq[q] = tab + mi(q) * TS;
+    PF[q] = Ws[q] = R(0);
+  }
+#pragma unroll 4
+  for (int i = 0; i < j; ++i)
+#pragma unroll
+    for (int q = 0; q < NG; ++q) PF[q] = fma(LM[q], PF[q], xF[(q * WB + i) * NC + c]);
+#pragma unroll 4
+  for (int i = WB - 1; i > j; --i)
+#pragma unroll
+    for (int q = 0; q < NG; ++q)
+      Ws[q] = fma(LM[q], fma(Kq[q][WB - 1 - i], xF[(q * WB + i) * NC + c], Ws[q]), xW[(q * WB + i) * NC + c]);
+  // the block's composites (last chunk: forward, first chunk: backward) to
+  // slot `rank` of every block's receive buffer
+  const unsigned long long *bar = xbar + (x & 1);
+  if (j == WB - 1 || j == 0) {
+    const int fw = (j == 0) ? 1 : 0;
+    R v[NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q)
+      v[q] = fw ? fma(LM[q], fma(Kq[q][WB - 1], F[q], Ws[q]), W[q]) : fma(LM[q], PF[q], F[q]);
+    R *slot = rb + ((fw * cs + rank) * NC + c) * NG;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) slot[q] = v[q];
+    const unsigned la = smem_u32(slot), lbar = smem_u32(bar);
+    for (int d = 1; d < cs; ++d) {
+      int dst = rank + d;
+      if (dst >= cs) dst -= cs;
+      const unsigned ra = mapa_u32(la, (unsigned)dst), rbar = mapa_u32(lbar, (unsigned)dst);
+      if constexpr (sizeof(R) == 4 && NG % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < NG; k += 4) st_async4(ra + k * 4, v[k], v[k + 1], v[k + 2], v[k + 3], rbar);
+      } else if constexpr (NG % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < NG; k += 2) st_async2(ra + k * (unsigned)sizeof(R), v[k], v[k + 1], rbar);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NG; ++k) st_async(ra + k * (unsigned)sizeof(R), v[k], rbar);
+      }
+    }
+  }
+  __syncthreads();  // own slots written; the composition buffer is read
+  if (w < NG) {
+    if (!mbar_wait_cluster(xbar + (x & 1), (unsigned)((x >> 1) & 1), fail)) atomicOr(&g_circ_status, 2);
+    const int q = w;
+    const int sg = mi(q);
+    const CircMat<R> &M = A.mat[sg / 3][sg % 3];
+    const R *tk = tab + sg * TS, *tl = tk + (WB + 1), *tkb = tl + (WB + 1), *tlb = tkb + 17;
+    const R LB = tl[WB];
+    const R *gF = rb + (size_t)c * NG + q, *gW = rb + ((size_t)cs * NC + c) * NG + q;
+    R ftot = R(0), pfb = R(0), fr = R(0), wl = R(0), wsr = R(0);
+#pragma unroll 4
+    for (int i = 0; i < cs; ++i) {
+      const R f = gF[i * NC * NG];
+      if (i == rank) {
+        pfb = ftot;
+        fr = f;
+      }
+      ftot = fma(LB, ftot, f);
+      const int b = cs - 1 - i;
+      if (b == rank) wsr = wl;
+      wl = fma(LB, fma(tkb[i], gF[b * NC * NG], wl), gW[b * NC * NG]);
+    }
+    const R y0 = ftot * M.inv1m;
+    const R z0 = fma(tlb[17], y0, wl) * M.inv1m;
+    const R ycb = fma(tlb[rank], y0, pfb);
+    const R ycn = fma(LB, ycb, fr);
+    const R zcb = fma(tlb[cs - 1 - rank], z0, fma(tkb[cs - 1 - rank], ycn, wsr));
+    if (h == 0) {
+      car[q * NC + c] = ycb;
+      car[(NG + q) * NC + c] = zcb;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) mbar_expect_tx(xbar + (x & 1), (unsigned)((cs - 1) * 2 * ng_next2 * NC * (int)sizeof(R)));
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    const R *K = Kq[q], *lp = Kq[q] + (WB + 1);
+    const R ycb = car[q * NC + c], zcb = car[(NG + q) * NC + c];
+    Yc[q] = fma(lp[j], ycb, PF[q]);
+    const R yn = fma(LM[q], Yc[q], F[q]);
+    Zc[q] = fma(lp[WB - 1 - j], zcb, fma(K[WB - 1 - j], yn, Ws[q]));
+  }
+}
+
 }  // namespace circ
 
 template <typename R, int S, int L, int KIND, int WB, int NC>
@@ -568,10 +755,14 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   // so a warp's HP chunks read one 32-wide row (conflict-free)
   R *tile = reinterpret_cast<R *>(circ_smem);
   constexpr int XS = WB > 16 ? WB : 16;         // exchange rows (chunks of a block, or gathered blocks)
-  R *xF = tile + (size_t)3 * S * ROWS * NC;    // [2S][XS][NC] (an exchange of NG solves uses [NG][max(WB, cs)])
-  R *xW = xF + (size_t)2 * S * XS * NC;
-  R *blk = xW + (size_t)2 * S * XS * NC;       // [3 exchanges][2][2S][NC]
-  R *car = blk + (size_t)3 * 2 * 2 * S * NC;   // [2][2S][NC]
+  constexpr size_t EX = (size_t)2 * 2 * S * XS * NC;  // one exchange buffer
+  // two exchange buffers.  cs > 1: they alternate between receiving the
+  // cluster's composites and composing the block's chunks (push exchange).
+  // cs = 1: buf0 = [F, W][2S][XS][NC], buf1 = the block composites
+  // [3 exchanges][2][2S][NC]
+  R *buf0 = tile + (size_t)3 * S * ROWS * NC;
+  R *buf1 = buf0 + EX;
+  R *car = buf1 + EX;                          // [2][2S][NC]
   constexpr int TS = 2 * (WB + 1) + 35;
   R *tab = car + (size_t)2 * 2 * S * NC;       // [S * 3 matrices][TS]: the exchange's coefficient tables
   for (int e = tid; e < S * 3 * TS; e += WB * NC) {
@@ -597,13 +788,42 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   // field's mbarrier (phase = this block's group count & 1)
   constexpr bool TMA = (NC == 32);
   __shared__ __align__(8) unsigned long long fbar[3];
-  if constexpr (TMA) {
+  // push exchanges: xbar[b] completes when the other blocks' composites are in buf[b]
+  __shared__ __align__(8) unsigned long long xbar[2];
+  __shared__ int wait_fail;  // a bounded wait of this block gave up: later waits return at once
+  if (tid == 0) wait_fail = 0;
+  // solves of exchange number x (LAST: P, then T and S; MIDDLE: T and S twice, then P)
+  auto ng_of = [&](int x) { return KIND == SWEEP_LAST ? ((x & 1) ? 2 * S : S) : (x % 3 == 2 ? S : 2 * S); };
+  if (TMA || cs > 1) {
     if (tid == 0) {
-      for (int f = 0; f < 3; ++f) mbar_init(&fbar[f], 1);
+      if constexpr (TMA)
+        for (int f = 0; f < 3; ++f) mbar_init(&fbar[f], 1);
+      if (cs > 1) {
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
+      }
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      if (cs > 1) {  // armed for exchanges 0 and 1
+        mbar_expect_tx(&xbar[0], (unsigned)((cs - 1) * 2 * ng_of(0) * NC * (int)sizeof(R)));
+        mbar_expect_tx(&xbar[1], (unsigned)((cs - 1) * 2 * ng_of(1) * NC * (int)sizeof(R)));
+      }
     }
-    __syncthreads();
+    // every block's barriers exist (and are armed) before any block pushes
+    if (cs > 1) cg::this_cluster().sync();
+    else __syncthreads();
   }
+  int xc = 0;  // exchanges so far
+  // one exchange of NG solves (blk_slot: composites slot of the one-block path)
+  auto exchange = [&](auto mi, const auto &F, const auto &W, auto &Yc, auto &Zc, int blk_slot) {
+    constexpr int NG = sizeof(F) / sizeof(R);
+    if (cs > 1)
+      strided_exchange_push<R, WB, NC, NG>(A, mi, F, W, Yc, Zc, buf0, buf1, xbar, xc, ng_of(xc + 2), car, tab, j, c,
+                                           w, h, rank, tid, &wait_fail);
+    else
+      strided_exchange<R, WB, NC, NG>(A, mi, F, W, Yc, Zc, buf0, buf0 + EX / 2,
+                                      buf1 + (size_t)blk_slot * 2 * 2 * S * NC, car, tab, j, c, w, h, rank);
+    ++xc;
+  };
   // stage field fld of group g into its buffer (TMA, or cp.async with 16-byte
   // pieces: always one commit group, empty past the last group, so the wait
   // counts hold)
@@ -639,7 +859,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   // cp.async, `pending` is how many later commit groups may stay in flight
   auto wait_field = [&](int fld, int pending) {
     if constexpr (TMA) {
-      if (!mbar_wait(&fbar[fld], (unsigned)(it & 1))) atomicOr(&g_circ_status, 1);
+      if (!mbar_wait(&fbar[fld], (unsigned)(it & 1), &wait_fail)) atomicOr(&g_circ_status, 1);
     } else {
       if (pending >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
       else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -679,8 +899,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           F[2 * s + 1] = y1; W[2 * s + 1] = w1;
         }
         auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
-        strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)fld * 2 * 2 * S * NC, car, tab,
-                                       j, c, w, h, rank);
+        exchange(mi, F, W, Yc, Zc, fld);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
@@ -725,8 +944,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           W[s] = w;
         }
         auto mi = [&](int q) { return q * 3; };
-        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * 2 * S * NC, car, tab, j, c,
-                                   w, h, rank);
+        exchange(mi, F, W, Yc, Zc, 2);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &M = A.mat[s][0];
@@ -778,7 +996,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           W[s] = w;
         }
         auto mi = [&](int q) { return q * 3 + 0; };
-        strided_exchange<R, WB, NC, S>(A, mi, F, W, Yc, Zc, xF, xW, blk, car, tab, j, c, w, h, rank);
+        exchange(mi, F, W, Yc, Zc, 0);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const CircMat<R> &M = A.mat[s][0];
@@ -827,8 +1045,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
         }
       }
       auto mi = [&](int q) { return (q >> 1) * 3 + ((q & 1) ? 2 : 1); };
-      strided_exchange<R, WB, NC, 2 * S>(A, mi, F, W, Yc, Zc, xF, xW, blk + (size_t)2 * 2 * S * NC, car, tab, j, c,
-                                     w, h, rank);
+      exchange(mi, F, W, Yc, Zc, 1);
       // ---- U_{n+1} = T_d f1 - S_d f2
 #pragma unroll
       for (int s = 0; s < S; ++s) {

@@ -142,16 +142,17 @@ cudaError_t launch_circ(const CircArgs<double> &a, int nspecies, int L, int kind
 
 // strided sweeps: NC lines x WB chunks per block (WB NC threads); the tile
 // holds the 3 input fields of every species for the block's WB L rows, then
-// the exchange buffers of up to 2 s solves, the block summaries published to
-// the cluster (one set per exchange) and the block carries
+// two exchange buffers of up to 2 s solves (receive / compose, alternating),
+// the block carries and the exchange coefficient tables
 inline size_t circ_strided_smem(int nspecies, int L, int WB, int NC, size_t real_bytes) {
   const size_t tile = (size_t)3 * nspecies * WB * L * NC * real_bytes;
   const size_t exch = (size_t)2 * 2 * nspecies * (WB > 16 ? WB : 16) * NC * real_bytes;
-  const size_t blk = (size_t)3 * 2 * 2 * nspecies * NC * real_bytes;
   const size_t car = (size_t)2 * 2 * nspecies * NC * real_bytes;
   const size_t tab = (size_t)nspecies * 3 * (2 * (WB + 1) + 35) * real_bytes;
-  return tile + exch + blk + car + tab;
+  return tile + 2 * exch + car + tab;
 }
+// static shared memory of the strided kernels (mbarriers)
+constexpr size_t CIRC_STRIDED_STATIC_SMEM = 128;
 cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                                   int &nclusters);
 cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
