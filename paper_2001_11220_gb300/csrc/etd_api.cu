@@ -370,7 +370,7 @@ bool plan_axis_circ(Instance &I, int a, int L, int wb, int nc) {
   // persistent: the blocks resident at once, each walking the line groups
   const long long ngroups = (P.nlines + P.nlb - 1) / P.nlb;
   int per_sm = 0, dev = 0, nsm = 0;
-  if (circ_first_capacity(I.real_bytes, I.S, L, P.nthreads, P.smem, per_sm) != cudaSuccess ||
+  if (circ_first_capacity(I.real_bytes, I.S, L, P.nthreads, I.rkind, P.smem, per_sm) != cudaSuccess ||
       cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -422,12 +422,14 @@ bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc) {
     C.cs = (int)cs;
     C.wb = wb;
     C.ncol = nc;
+    C.rkind = I.rkind;
     e = circ_cluster_capacity(C, I.S, L, P.kind, P.nthreads, P.smem, ncl);
   } else {
     CircArgs<float> C{};
     C.cs = (int)cs;
     C.wb = wb;
     C.ncol = nc;
+    C.rkind = I.rkind;
     e = circ_cluster_capacity(C, I.S, L, P.kind, P.nthreads, P.smem, ncl);
   }
   if (e != cudaSuccess) {

@@ -7,29 +7,31 @@ namespace etd {
 
 namespace {
 
-template <typename K>
-cudaError_t ensure_dyn_smem(K fn, size_t smem) {
+template <typename R>
+cudaError_t ensure_dyn_smem(CircKernel<R> fn, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename R, int S, int L>
-cudaError_t launch_first(const CircArgs<R> &a, int nthreads, size_t smem, int nblocks, cudaStream_t s) {
-  auto fn = nthreads == 512 ? circ_first_kernel<R, S, L, 512> : circ_first_kernel<R, S, L, 256>;
+template <typename R>
+cudaError_t launch_first(CircKernel<R> fn, const CircArgs<R> &a, int nthreads, size_t smem, int nblocks,
+                         cudaStream_t s) {
   cudaError_t e = ensure_dyn_smem(fn, smem);
   if (e != cudaSuccess) return e;
   fn<<<nblocks, nthreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename R, int S, int L, int KIND, int WB, int NC>
-cudaError_t launch_strided(const CircArgs<R> &a, size_t smem, int nblocks, cudaStream_t s, int *capacity) {
-  auto fn = circ_strided_kernel<R, S, L, KIND, WB, NC>;
+// capacity != nullptr: only report the clusters (cs > 1) or blocks per SM
+// (cs = 1) that fit at once
+template <typename R>
+cudaError_t launch_strided(CircKernel<R> fn, const CircArgs<R> &a, size_t smem, int nblocks, cudaStream_t s,
+                           int *capacity) {
   cudaError_t e = ensure_dyn_smem(fn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nblocks, 1, 1);
-  cfg.blockDim = dim3(WB * NC, 1, 1);
+  cfg.blockDim = dim3((unsigned)(a.wb * a.ncol), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -52,7 +54,7 @@ cudaError_t launch_strided(const CircArgs<R> &a, size_t smem, int nblocks, cudaS
     cfg.gridDim = dim3((unsigned)(a.cs > 1 ? a.cs : 1), 1, 1);
     if (a.cs <= 1) {
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, WB * NC, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, a.wb * a.ncol, smem);
       *capacity = per_sm;
       return e;
     }
@@ -63,19 +65,24 @@ cudaError_t launch_strided(const CircArgs<R> &a, size_t smem, int nblocks, cudaS
   return cudaGetLastError();
 }
 
-// strided sweeps, (chunks, lines) per block: FP32 (L = 16) 16 x 16, 16 x 32,
-// 8 x 32, 32 x 16; FP64 (L = 8) 8 x 32, 16 x 16
+// strided kernels, (chunks, lines) per block: FP32 (L = 16) 16 x 16, 16 x 32,
+// 8 x 32, 32 x 16; FP64 (L = 8) 8 x 32, 16 x 16.  A kernel with the reaction
+// fixed at compile time where one is compiled (FP32, two species), else the
+// generic one.
 template <typename R>
-cudaError_t strided_any(const CircArgs<R> &a, int nspecies, int L, int kind, size_t smem, int nblocks,
-                        cudaStream_t s, int *capacity) {
+CircKernel<R> strided_kernel(int nspecies, int L, int kind, int wb, int nc, int rkind) {
   constexpr int LL = sizeof(R) == 4 ? 16 : 8;
-  if (L != LL) return cudaErrorInvalidValue;
-  const int key = (a.wb * 100 + a.ncol) * 100 + nspecies * 10 + kind;
-#define ETD_CIRC_STRIDED(WB_, NC_)                                                                         \
-  case (WB_ * 100 + NC_) * 100 + 11: return launch_strided<R, 1, LL, SWEEP_MIDDLE, WB_, NC_>(a, smem, nblocks, s, capacity); \
-  case (WB_ * 100 + NC_) * 100 + 12: return launch_strided<R, 1, LL, SWEEP_LAST, WB_, NC_>(a, smem, nblocks, s, capacity);   \
-  case (WB_ * 100 + NC_) * 100 + 21: return launch_strided<R, 2, LL, SWEEP_MIDDLE, WB_, NC_>(a, smem, nblocks, s, capacity); \
-  case (WB_ * 100 + NC_) * 100 + 22: return launch_strided<R, 2, LL, SWEEP_LAST, WB_, NC_>(a, smem, nblocks, s, capacity);
+  if (L != LL) return nullptr;
+  if constexpr (sizeof(R) == 4) {
+    if (nspecies == 2)
+      if (CircKernel<float> k = circ_strided_kernel_rk(kind, wb, nc, rkind)) return k;
+  }
+  const int key = (wb * 100 + nc) * 100 + nspecies * 10 + kind;
+#define ETD_CIRC_STRIDED(WB_, NC_)                                                             \
+  case (WB_ * 100 + NC_) * 100 + 11: return circ_strided_kernel<R, 1, LL, SWEEP_MIDDLE, WB_, NC_>; \
+  case (WB_ * 100 + NC_) * 100 + 12: return circ_strided_kernel<R, 1, LL, SWEEP_LAST, WB_, NC_>;   \
+  case (WB_ * 100 + NC_) * 100 + 21: return circ_strided_kernel<R, 2, LL, SWEEP_MIDDLE, WB_, NC_>; \
+  case (WB_ * 100 + NC_) * 100 + 22: return circ_strided_kernel<R, 2, LL, SWEEP_LAST, WB_, NC_>;
   if constexpr (sizeof(R) == 4) {
     switch (key) {
       ETD_CIRC_STRIDED(16, 16)
@@ -92,31 +99,48 @@ cudaError_t strided_any(const CircArgs<R> &a, int nspecies, int L, int kind, siz
     }
   }
 #undef ETD_CIRC_STRIDED
-  return cudaErrorInvalidValue;
+  return nullptr;
+}
+
+// first-axis kernels: FP32 L = 8, 16; FP64 L = 4, 8; 256 or 512 threads
+template <typename R>
+CircKernel<R> first_kernel(int nspecies, int L, int nthreads, int rkind) {
+  if constexpr (sizeof(R) == 4) {
+    if (nspecies == 2)
+      if (CircKernel<float> k = circ_first_kernel_rk(L, nthreads, rkind)) return k;
+  }
+  const bool big = nthreads == 512;
+  const int key = nspecies * 100 + L;
+#define ETD_FIRST_FN(S_, L_) (big ? circ_first_kernel<R, S_, L_, 512> : circ_first_kernel<R, S_, L_, 256>)
+  if constexpr (sizeof(R) == 4) {
+    switch (key) {
+      case 108: return ETD_FIRST_FN(1, 8);
+      case 116: return ETD_FIRST_FN(1, 16);
+      case 208: return ETD_FIRST_FN(2, 8);
+      case 216: return ETD_FIRST_FN(2, 16);
+      default: return nullptr;
+    }
+  } else {
+    switch (key) {
+      case 104: return ETD_FIRST_FN(1, 4);
+      case 108: return ETD_FIRST_FN(1, 8);
+      case 204: return ETD_FIRST_FN(2, 4);
+      case 208: return ETD_FIRST_FN(2, 8);
+      default: return nullptr;
+    }
+  }
+#undef ETD_FIRST_FN
 }
 
 template <typename R>
 cudaError_t launch_any(const CircArgs<R> &a, int nspecies, int L, int kind, int nthreads, size_t smem, int nblocks,
                        cudaStream_t s) {
-  if (kind != SWEEP_FIRST) return strided_any<R>(a, nspecies, L, kind, smem, nblocks, s, nullptr);
-  const int key = nspecies * 100 + L;
-  if constexpr (sizeof(R) == 4) {
-    switch (key) {
-      case 108: return launch_first<R, 1, 8>(a, nthreads, smem, nblocks, s);
-      case 116: return launch_first<R, 1, 16>(a, nthreads, smem, nblocks, s);
-      case 208: return launch_first<R, 2, 8>(a, nthreads, smem, nblocks, s);
-      case 216: return launch_first<R, 2, 16>(a, nthreads, smem, nblocks, s);
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    switch (key) {
-      case 104: return launch_first<R, 1, 4>(a, nthreads, smem, nblocks, s);
-      case 108: return launch_first<R, 1, 8>(a, nthreads, smem, nblocks, s);
-      case 204: return launch_first<R, 2, 4>(a, nthreads, smem, nblocks, s);
-      case 208: return launch_first<R, 2, 8>(a, nthreads, smem, nblocks, s);
-      default: return cudaErrorInvalidValue;
-    }
+  if (kind != SWEEP_FIRST) {
+    CircKernel<R> fn = strided_kernel<R>(nspecies, L, kind, a.wb, a.ncol, a.rkind);
+    return fn ? launch_strided<R>(fn, a, smem, nblocks, s, nullptr) : cudaErrorInvalidValue;
   }
+  CircKernel<R> fn = first_kernel<R>(nspecies, L, nthreads, a.rkind);
+  return fn ? launch_first<R>(fn, a, nthreads, smem, nblocks, s) : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -133,41 +157,26 @@ cudaError_t launch_circ(const CircArgs<double> &a, int nspecies, int L, int kind
 cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                                   int &nclusters) {
   (void)nthreads;
-  return strided_any<float>(a, nspecies, L, kind, smem, 1, nullptr, &nclusters);
+  CircKernel<float> fn = strided_kernel<float>(nspecies, L, kind, a.wb, a.ncol, a.rkind);
+  return fn ? launch_strided<float>(fn, a, smem, 1, nullptr, &nclusters) : cudaErrorInvalidValue;
 }
 cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                                   int &nclusters) {
   (void)nthreads;
-  return strided_any<double>(a, nspecies, L, kind, smem, 1, nullptr, &nclusters);
+  CircKernel<double> fn = strided_kernel<double>(nspecies, L, kind, a.wb, a.ncol, a.rkind);
+  return fn ? launch_strided<double>(fn, a, smem, 1, nullptr, &nclusters) : cudaErrorInvalidValue;
 }
 
-cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthreads, size_t smem, int &blocks_per_sm) {
+cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthreads, int rkind, size_t smem,
+                                int &blocks_per_sm) {
   blocks_per_sm = 0;
-  const void *fn = nullptr;
-  const int key = nspecies * 100 + L;
-  const bool big = nthreads == 512;
-#define ETD_FIRST_FN(R_, S_, L_) \
-  (big ? (const void *)circ_first_kernel<R_, S_, L_, 512> : (const void *)circ_first_kernel<R_, S_, L_, 256>)
-  if (real_bytes == 4) {
-    switch (key) {
-      case 108: fn = ETD_FIRST_FN(float, 1, 8); break;
-      case 116: fn = ETD_FIRST_FN(float, 1, 16); break;
-      case 208: fn = ETD_FIRST_FN(float, 2, 8); break;
-      case 216: fn = ETD_FIRST_FN(float, 2, 16); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    switch (key) {
-      case 104: fn = ETD_FIRST_FN(double, 1, 4); break;
-      case 108: fn = ETD_FIRST_FN(double, 1, 8); break;
-      case 204: fn = ETD_FIRST_FN(double, 2, 4); break;
-      case 208: fn = ETD_FIRST_FN(double, 2, 8); break;
-      default: return cudaErrorInvalidValue;
-    }
+  const void *fn = real_bytes == 4 ? (const void *)first_kernel<float>(nspecies, L, nthreads, rkind)
+                                   : (const void *)first_kernel<double>(nspecies, L, nthreads, rkind);
+  if (!fn) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
-#undef ETD_FIRST_FN
-  cudaError_t e = ensure_dyn_smem(fn, smem);
-  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, nthreads, smem);
 }
 
@@ -218,16 +227,7 @@ bool circ_encode_maps(CircArgs<float> &a, int nspecies, int rows) { return encod
 bool circ_encode_maps(CircArgs<double> &a, int nspecies, int rows) { return encode_maps<double>(a, nspecies, rows); }
 
 int circ_take_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_circ_status, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  if (v) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_circ_status, &zero, sizeof(int));
-  }
-  return v;
+  return take_status_here() | circ_take_status_rk_first() | circ_take_status_rk_strided();
 }
 
 }  // namespace etd

@@ -26,8 +26,23 @@
 
 namespace etd {
 
-// non-zero after a kernel's bounded wait for a TMA copy gave up
-__device__ int g_circ_status;
+// non-zero after a kernel's bounded wait gave up (1: a tile copy, 2: an
+// exchange); one per translation unit that compiles these kernels, read and
+// cleared through take_status_here()
+static __device__ int g_circ_status;
+
+static inline int take_status_here() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_circ_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_circ_status, &zero, sizeof(int));
+  }
+  return v;
+}
 
 namespace circ {
 
@@ -37,48 +52,53 @@ __device__ __forceinline__ float rdivc(float a, float b) { return __fdividef(a, 
 __device__ __forceinline__ double rdivc(double a, double b) { return a / b; }
 
 // F(u) of the autonomous reactions (Section 8's models; periodic problems
-// carry no manufactured source)
-template <typename R, int S>
-__device__ __forceinline__ void reaction(const CircArgs<R> &A, const R (&u)[S], R (&f)[S]) {
-  switch (A.rkind) {
-    case 1:
+// carry no manufactured source).  K: the reaction kind (etd_reaction_kind).
+template <typename R, int S, int K>
+__device__ __forceinline__ void reaction_kind(const CircArgs<R> &A, const R (&u)[S], R (&f)[S]) {
+  if constexpr (K == 1) {
 #pragma unroll
-      for (int s = 0; s < S; ++s) f[s] = fma(A.rpR[0], u[s], A.rpR[1]);
-      return;
-    case 2:
-      if constexpr (S == 2) {  // Brusselator: a + u^2 v - (b+1) u ; b u - u^2 v
-        const R uuv = u[0] * u[0] * u[1];
-        f[0] = A.rpR[0] + uuv - (A.rpR[1] + R(1)) * u[0];
-        f[1] = A.rpR[1] * u[0] - uuv;
-        return;
-      }
-      break;
-    case 3:
-      if constexpr (S == 2) {  // Schnakenberg: g (a - u + u^2 v) ; g (b - u^2 v)
-        const R uuv = u[0] * u[0] * u[1];
-        f[0] = A.rpR[2] * (A.rpR[0] - u[0] + uuv);
-        f[1] = A.rpR[2] * (A.rpR[1] - uuv);
-        return;
-      }
-      break;
-    case 4:
-      if constexpr (S == 2) {  // Gray-Scott: -u v^2 + F (1-u) ; u v^2 - (F+kappa) v
-        const R uvv = u[0] * u[1] * u[1];
-        f[0] = A.rpR[0] * (R(1) - u[0]) - uvv;
-        f[1] = uvv - (A.rpR[0] + A.rpR[1]) * u[1];
-        return;
-      }
-      break;
-    case 5:  // enzyme kinetics without a source term
-      f[0] = -rdivc(u[0], R(1) + u[0]);
+    for (int s = 0; s < S; ++s) f[s] = fma(A.rpR[0], u[s], A.rpR[1]);
+    return;
+  } else if constexpr (K == 2 && S == 2) {  // Brusselator: a + u^2 v - (b+1) u ; b u - u^2 v
+    const R uuv = u[0] * u[0] * u[1];
+    f[0] = A.rpR[0] + uuv - (A.rpR[1] + R(1)) * u[0];
+    f[1] = A.rpR[1] * u[0] - uuv;
+    return;
+  } else if constexpr (K == 3 && S == 2) {  // Schnakenberg: g (a - u + u^2 v) ; g (b - u^2 v)
+    const R uuv = u[0] * u[0] * u[1];
+    f[0] = A.rpR[2] * (A.rpR[0] - u[0] + uuv);
+    f[1] = A.rpR[2] * (A.rpR[1] - uuv);
+    return;
+  } else if constexpr (K == 4 && S == 2) {  // Gray-Scott: -u v^2 + F (1-u) ; u v^2 - (F+kappa) v
+    const R uvv = u[0] * u[1] * u[1];
+    f[0] = A.rpR[0] * (R(1) - u[0]) - uvv;
+    f[1] = uvv - (A.rpR[0] + A.rpR[1]) * u[1];
+    return;
+  } else if constexpr (K == 5) {  // enzyme kinetics without a source term
+    f[0] = -rdivc(u[0], R(1) + u[0]);
 #pragma unroll
-      for (int s = 1; s < S; ++s) f[s] = R(0);
-      return;
-    default:
-      break;
+    for (int s = 1; s < S; ++s) f[s] = R(0);
+    return;
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s) f[s] = R(0);
   }
-#pragma unroll
-  for (int s = 0; s < S; ++s) f[s] = R(0);
+}
+// RK >= 0: the kind fixed at compile time; RK < 0: chosen per call from A.rkind
+template <typename R, int S, int RK>
+__device__ __forceinline__ void reaction(const CircArgs<R> &A, const R (&u)[S], R (&f)[S]) {
+  if constexpr (RK >= 0) {
+    reaction_kind<R, S, RK>(A, u, f);
+  } else {
+    switch (A.rkind) {
+      case 1: reaction_kind<R, S, 1>(A, u, f); return;
+      case 2: reaction_kind<R, S, 2>(A, u, f); return;
+      case 3: reaction_kind<R, S, 3>(A, u, f); return;
+      case 4: reaction_kind<R, S, 4>(A, u, f); return;
+      case 5: reaction_kind<R, S, 5>(A, u, f); return;
+      default: reaction_kind<R, S, 0>(A, u, f); return;
+    }
+  }
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -209,7 +229,7 @@ __host__ __device__ constexpr int qmat(int q) { return q == 4 ? 0 : (q & 1) ? 2 
 // threads).  Persistent: block b takes the line groups b, b + gridDim.x, ...
 // and stages the next group's chunks (cp.async into the other half of its
 // double buffer) while it solves the current one.
-template <typename R, int S, int L, int NT>
+template <typename R, int S, int L, int NT, int RK = -1>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const __grid_constant__ CircArgs<R> A) {
   using namespace circ;
   extern __shared__ __align__(16) unsigned char circ_smem[];
@@ -263,7 +283,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
     R u[S], f[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) u[s] = su(s, t);
-    reaction<R, S>(A, u, f);
+    reaction<R, S, RK>(A, u, f);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const R b[NQ] = {u[s], u[s], f[s], f[s], fma(A.kR, f[s], u[s])};
@@ -278,22 +298,38 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
 
   // ---- round 1: forward carries Yc_j (inclusive scan of F, cyclic closure)
   R Yc[S][NQ];
+  if (G == 32) {  // whole warps per line: every step of the scan runs (no per-step test)
 #pragma unroll
-  for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const CircMat<R> &M = A.mat[s][qmat(q)];
-      R v = ty[s][q];
+      for (int q = 0; q < NQ; ++q) {
+        const CircMat<R> &M = A.mat[s][qmat(q)];
+        R v = ty[s][q];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const int d = 1 << k;
-        if (d < G) {
-          const R o = __shfl_up_sync(FULL, v, d, G);
-          if (gl >= d) v = fma(M.sc[k], o, v);
+        for (int k = 0; k < 5; ++k) {
+          const R o = __shfl_up_sync(FULL, v, 1 << k);
+          v = gl >= (1 << k) ? fma(M.sc[k], o, v) : v;
         }
+        ty[s][q] = v;
       }
-      ty[s][q] = v;  // inclusive prefix within the warp
-    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const CircMat<R> &M = A.mat[s][qmat(q)];
+        R v = ty[s][q];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const int d = 1 << k;
+          if (d < G) {
+            const R o = __shfl_up_sync(FULL, v, d, G);
+            if (gl >= d) v = fma(M.sc[k], o, v);
+          }
+        }
+        ty[s][q] = v;  // inclusive prefix within the warp
+      }
+  }
   R Cw[S][NQ], Tot[S][NQ];
   if (nw > 1) {
     R *t1 = tot + ((size_t)(lb * nw + w) * S) * NQ;
@@ -343,22 +379,38 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
 
   // ---- round 2: backward carries Zc_j (suffix scan of G = W + kappa Yc)
   R Zc[S][NQ];
+  if (G == 32) {
 #pragma unroll
-  for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const CircMat<R> &M = A.mat[s][qmat(q)];
-      R v = fma(M.kap, Yc[s][q], tw[s][q]);
+      for (int q = 0; q < NQ; ++q) {
+        const CircMat<R> &M = A.mat[s][qmat(q)];
+        R v = fma(M.kap, Yc[s][q], tw[s][q]);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const int d = 1 << k;
-        if (d < G) {
-          const R o = __shfl_down_sync(FULL, v, d, G);
-          if (gl + d < G) v = fma(M.sc[k], o, v);
+        for (int k = 0; k < 5; ++k) {
+          const R o = __shfl_down_sync(FULL, v, 1 << k);
+          v = gl + (1 << k) < 32 ? fma(M.sc[k], o, v) : v;
         }
+        tw[s][q] = v;
       }
-      tw[s][q] = v;  // inclusive suffix within the warp
-    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const CircMat<R> &M = A.mat[s][qmat(q)];
+        R v = fma(M.kap, Yc[s][q], tw[s][q]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const int d = 1 << k;
+          if (d < G) {
+            const R o = __shfl_down_sync(FULL, v, d, G);
+            if (gl + d < G) v = fma(M.sc[k], o, v);
+          }
+        }
+        tw[s][q] = v;  // inclusive suffix within the warp
+      }
+  }
   if (nw > 1) {
     R *t2 = tot + ((size_t)A.lpb * nw * S) * NQ + ((size_t)(lb * nw + w) * S) * NQ;
     if (lane == 0)
@@ -406,67 +458,72 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
       Zc[s][q] = fma(lp[m - 1 - j], z0, nx);
     }
 
-  // ---- pass 2: recurrences from the carries, combination, 32-byte stores
+  // ---- pass 2: recurrences from the carries, combination, 32-byte stores.
+  // Order: R on U_n per species; P on U_n + k F(U_n) for all species at once,
+  // evaluating F once per position and leaving it in the thread's staging
+  // slot in place of U_n (no later pass reads U_n); R on F per species.
   if (ok) {
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const CircMat<R> &MP = A.mat[s][0], &MT = A.mat[s][1], &MS = A.mat[s][2];
-    R fs[L];
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      R u[S], f[S];
-#pragma unroll
-      for (int r = 0; r < S; ++r) u[r] = su(r, t);
-      reaction<R, S>(A, u, f);
-      fs[t] = f[s];
-    }
-    R zt[L], ys[L];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {  // h = 0: right-hand side U_n, h = 1: F(U_n)
-      R y = Yc[s][2 * h];
+    auto sslot = [&](int s) -> R * { return stage + ((size_t)s * nthr + tid) * CSZ; };
+    // R = 9T - 8S of right-hand side h (0: U_n, 1: F) from the slot, species s
+    auto solve_R = [&](int s, int h) {
+      const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
+      const R *b = sslot(s);
+      R zt[L], ys[L];
+      R y = Yc[s][2 * h], y2 = Yc[s][2 * h + 1];
 #pragma unroll
       for (int t = 0; t < L; ++t) {
-        y = fma(MT.lam, y, h ? fs[t] : su(s, t));
+        y = fma(MT.lam, y, b[t]);
         zt[t] = y;
+        y2 = fma(MS.lam, y2, b[t]);
+        ys[t] = y2;
       }
-      R z = Zc[s][2 * h];
+      R z = Zc[s][2 * h], z2 = Zc[s][2 * h + 1];
 #pragma unroll
       for (int t = L - 1; t >= 0; --t) {
         z = fma(MT.lam, z, zt[t]);
-        zt[t] = z;
-      }
-      y = Yc[s][2 * h + 1];
-#pragma unroll
-      for (int t = 0; t < L; ++t) {
-        y = fma(MS.lam, y, h ? fs[t] : su(s, t));
-        ys[t] = y;
-      }
-      z = Zc[s][2 * h + 1];
-#pragma unroll
-      for (int t = L - 1; t >= 0; --t) {
-        z = fma(MS.lam, z, ys[t]);
-        zt[t] = fma(A.cT[s], zt[t], -A.cS[s] * z);  // R = 9T - 8S
+        z2 = fma(MS.lam, z2, ys[t]);
+        zt[t] = fma(A.cT[s], z, -A.cS[s] * z2);
       }
       R *o = A.out[h] + s * A.N + base;
 #pragma unroll
       for (int t = 0; t < L; t += 32 / (int)sizeof(R)) st32(o + t, zt + t);
-    }
-    R y = Yc[s][4];
+    };
 #pragma unroll
-    for (int t = 0; t < L; ++t) {
-      y = fma(MP.lam, y, fma(A.kR, fs[t], su(s, t)));
-      zt[t] = y;
-    }
-    R z = Zc[s][4];
+    for (int s = 0; s < S; ++s) solve_R(s, 0);
+    {
+      R zp[S][L];
+      R y[S];
 #pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-      z = fma(MP.lam, z, zt[t]);
-      zt[t] = A.cP[s] * z;
-    }
-    R *o = A.out[2] + s * A.N + base;
+      for (int s = 0; s < S; ++s) y[s] = Yc[s][4];
 #pragma unroll
-    for (int t = 0; t < L; t += 32 / (int)sizeof(R)) st32(o + t, zt + t);
-  }
+      for (int t = 0; t < L; ++t) {
+        R u[S], f[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u[s] = sslot(s)[t];
+        reaction<R, S, RK>(A, u, f);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          y[s] = fma(A.mat[s][0].lam, y[s], fma(A.kR, f[s], u[s]));
+          zp[s][t] = y[s];
+          sslot(s)[t] = f[s];
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const CircMat<R> &MP = A.mat[s][0];
+        R z = Zc[s][4];
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+          z = fma(MP.lam, z, zp[s][t]);
+          zp[s][t] = A.cP[s] * z;
+        }
+        R *o = A.out[2] + s * A.N + base;
+#pragma unroll
+        for (int t = 0; t < L; t += 32 / (int)sizeof(R)) st32(o + t, zp[s] + t);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) solve_R(s, 1);
   }  // ok
   }  // line groups
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -730,7 +787,7 @@ __device__ __forceinline__ void strided_exchange_push(const CircArgs<R> &A, MatI
 
 }  // namespace circ
 
-template <typename R, int S, int L, int KIND, int WB, int NC>
+template <typename R, int S, int L, int KIND, int WB, int NC, int RK = -1>
 __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_constant__ CircArgs<R> A) {
   using namespace circ;
   namespace cg = cooperative_groups;
@@ -1028,7 +1085,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
         R u[S], fr[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) u[s] = Ustar[s][t];
-        reaction<R, S>(A, u, fr);
+        reaction<R, S, RK>(A, u, fr);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           R *cu = Tc(0, s) + t * 32, *cf = Tc(1, s) + t * 32;

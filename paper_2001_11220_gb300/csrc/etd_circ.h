@@ -158,7 +158,17 @@ cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L,
 cudaError_t circ_cluster_capacity(const CircArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                                   int &nclusters);
 
-cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthreads, size_t smem, int &blocks_per_sm);
+cudaError_t circ_first_capacity(int real_bytes, int nspecies, int L, int nthreads, int rkind, size_t smem,
+                                int &blocks_per_sm);
+
+// kernels of one element type share this signature
+template <typename R> using CircKernel = void (*)(CircArgs<R>);
+// FP32 two-species kernels with the reaction kind (2, 3, 4) fixed at compile
+// time, for the shapes the planner prefers; nullptr where none is compiled
+CircKernel<float> circ_first_kernel_rk(int L, int nthreads, int rkind);
+CircKernel<float> circ_strided_kernel_rk(int kind, int wb, int nc, int rkind);
+int circ_take_status_rk_first();
+int circ_take_status_rk_strided();
 
 // shared memory of a contiguous circulant sweep block of nthreads threads
 inline size_t circ_first_smem(int nspecies, int L, int nthreads, int m, int lpb, size_t real_bytes) {
