@@ -246,7 +246,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
   R *stage0 = reinterpret_cast<R *>(circ_smem);         // [2 buffers][S][nthr][CSZ]
   R *tot = stage0 + (size_t)2 * S * nthr * CSZ;         // [2][lpb][nw][S][NQ]
   const long long ngrp = (A.nlines + A.lpb - 1) / A.lpb;
-  // stage U_n of line group gi into buffer bi: thread-private padded slot per species
+  // A slot holds NGR 16-byte granules; granule g sits at position g ^ sw, so
+  // the 8 lanes of a quarter warp reading granule g of their slots hit 8
+  // different 4-bank groups (unswizzled, slots 64 or 32 bytes apart collide)
+  constexpr int NGR = CSZ / VW;
+  const int sw = NGR > 1 ? ((tid / (8 / NGR)) & (NGR - 1)) : 0;
+  using V16 = std::conditional_t<sizeof(R) == 4, float4, double2>;  // 16 bytes
+  // stage U_n of line group gi into buffer bi: thread-private slot per species
   auto stage = [&](long long gi, int bi) {
     const long long ln = gi * A.lpb + lb;
     if (gi < ngrp && ln < A.nlines) {
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
       for (int s = 0; s < S; ++s)
 #pragma unroll
         for (int v = 0; v < L; v += VW)
-          cp_async16(dst + ((size_t)s * nthr + tid) * CSZ + v, A.in[0] + s * A.N + b0 + v);
+          cp_async16(dst + ((size_t)s * nthr + tid) * CSZ + ((v / VW) ^ sw) * VW, A.in[0] + s * A.N + b0 + v);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
@@ -270,7 +276,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this thread's chunk of the current group
   R *stage = stage0 + (size_t)bi * S * nthr * CSZ;
   const long long base = line * (long long)A.p + (long long)j * L;
-  auto su = [&](int s, int t) -> R { return stage[((size_t)s * nthr + tid) * CSZ + t]; };
+  // granule g of species s in this thread's slot
+  auto gran = [&](int s, int g) -> R * { return stage + ((size_t)s * nthr + tid) * CSZ + (g ^ sw) * VW; };
+  // the slot of species s as L values (16-byte loads)
+  auto load_slot = [&](int s, R (&v)[L]) {
+#pragma unroll
+    for (int g = 0; g < NGR; ++g) {
+      const V16 q = *reinterpret_cast<const V16 *>(gran(s, g));
+      if constexpr (VW == 4) {
+        v[4 * g] = q.x; v[4 * g + 1] = q.y; v[4 * g + 2] = q.z; v[4 * g + 3] = q.w;
+      } else {
+        v[2 * g] = q.x; v[2 * g + 1] = q.y;
+      }
+    }
+  };
 
   // ---- pass 1: zero-carry summaries of every solve
   R ty[S][NQ], tw[S][NQ];
@@ -278,11 +297,23 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) ty[s][q] = tw[s][q] = R(0);
+  R ub[S][VW];  // the current granule of every species
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     R u[S], f[S];
+    if (t % VW == 0) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) u[s] = su(s, t);
+      for (int s = 0; s < S; ++s) {
+        const V16 q = *reinterpret_cast<const V16 *>(gran(s, t / VW));
+        if constexpr (VW == 4) {
+          ub[s][0] = q.x; ub[s][1] = q.y; ub[s][2] = q.z; ub[s][3] = q.w;
+        } else {
+          ub[s][0] = q.x; ub[s][1] = q.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = ub[s][t % VW];
     reaction<R, S, RK>(A, u, f);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -463,11 +494,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
   // evaluating F once per position and leaving it in the thread's staging
   // slot in place of U_n (no later pass reads U_n); R on F per species.
   if (ok) {
-    auto sslot = [&](int s) -> R * { return stage + ((size_t)s * nthr + tid) * CSZ; };
+
     // R = 9T - 8S of right-hand side h (0: U_n, 1: F) from the slot, species s
     auto solve_R = [&](int s, int h) {
       const CircMat<R> &MT = A.mat[s][1], &MS = A.mat[s][2];
-      const R *b = sslot(s);
+      R b[L];
+      load_slot(s, b);
       R zt[L], ys[L];
       R y = Yc[s][2 * h], y2 = Yc[s][2 * h + 1];
 #pragma unroll
@@ -495,17 +527,38 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
       R y[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) y[s] = Yc[s][4];
+      R ub[S][VW], fb[S][VW];
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         R u[S], f[S];
+        if (t % VW == 0) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) u[s] = sslot(s)[t];
+          for (int s = 0; s < S; ++s) {
+            const V16 q = *reinterpret_cast<const V16 *>(gran(s, t / VW));
+            if constexpr (VW == 4) {
+              ub[s][0] = q.x; ub[s][1] = q.y; ub[s][2] = q.z; ub[s][3] = q.w;
+            } else {
+              ub[s][0] = q.x; ub[s][1] = q.y;
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) u[s] = ub[s][t % VW];
         reaction<R, S, RK>(A, u, f);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           y[s] = fma(A.mat[s][0].lam, y[s], fma(A.kR, f[s], u[s]));
           zp[s][t] = y[s];
-          sslot(s)[t] = f[s];
+          fb[s][t % VW] = f[s];
+        }
+        if (t % VW == VW - 1) {  // F replaces U_n in the slot, one granule at a time
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            V16 q;
+            if constexpr (VW == 4) q = make_float4(fb[s][0], fb[s][1], fb[s][2], fb[s][3]);
+            else q = make_double2(fb[s][0], fb[s][1]);
+            *reinterpret_cast<V16 *>(gran(s, t / VW)) = q;
+          }
         }
       }
 #pragma unroll
@@ -973,11 +1026,13 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
             ys[t] = y2;
           }
           R z = Zc[2 * s], z2 = Zc[2 * s + 1];
+          R *op = out + (long long)(L - 1) * st;  // row t of this chunk, stepped down
 #pragma unroll
           for (int t = L - 1; t >= 0; --t) {
             z = fma(MT.lam, z, zt[t]);
             z2 = fma(MS.lam, z2, ys[t]);
-            out[(long long)t * st] = fma(A.cT[s], z, -A.cS[s] * z2);  // R = 9T - 8S
+            *op = fma(A.cT[s], z, -A.cS[s] * z2);  // R = 9T - 8S
+            op -= st;
           }
         }
         __syncthreads();  // every thread is done with this field's buffer
@@ -1015,10 +1070,12 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
             ys[t] = y;
           }
           R z = Zc[s];
+          R *op = out + (long long)(L - 1) * st;  // row t of this chunk, stepped down
 #pragma unroll
           for (int t = L - 1; t >= 0; --t) {
             z = fma(M.lam, z, ys[t]);
-            out[(long long)t * st] = A.cP[s] * z;
+            *op = A.cP[s] * z;
+            op -= st;
           }
         }
         __syncthreads();
@@ -1119,11 +1176,13 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
         }
         R z = Zc[2 * s], z2 = Zc[2 * s + 1];
         R *out = A.out[0] + s * A.N + mybase;
+        R *op = out + (long long)(L - 1) * st;  // row t of this chunk, stepped down
 #pragma unroll
         for (int t = L - 1; t >= 0; --t) {
           z = fma(MT.lam, z, zt[t]);
           z2 = fma(MS.lam, z2, ys[t]);
-          out[(long long)t * st] = fma(A.iaT[s], z, -A.iaS[s] * z2);
+          *op = fma(A.iaT[s], z, -A.iaS[s] * z2);
+          op -= st;
         }
       }
       __syncthreads();  // f1, f2 of g fully read: refill with the next group's c_U, c_f

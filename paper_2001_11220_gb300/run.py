@@ -2,6 +2,8 @@
 profiling captures).
 
     python -m paper_2001_11220_gb300.run --workload mms3d --p 256 --precision fp32 --steps 4
+    python -m paper_2001_11220_gb300.run --workload grayscott3d --p 256 --steps 2 --grad
+      (--grad: the misfit gradient over the steps, one checkpoint segment)
 """
 from __future__ import annotations
 
@@ -34,6 +36,7 @@ def main():
     ap.add_argument("--p", type=int, default=256)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--grad", action="store_true")
     args = ap.parse_args()
     import torch
 
@@ -44,8 +47,12 @@ def main():
     U = torch.tensor(W.initial_state(w), device="cuda", dtype=ctx.dtype)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for n in range(args.steps):
-        ctx.step(U, n * w.k)
+    if args.grad:
+        target = torch.tensor(W.initial_state(w.with_(seed=w.seed + 1)), device="cuda", dtype=ctx.dtype)
+        ctx.grad(U, 0.0, target, args.steps, args.steps)
+    else:
+        for n in range(args.steps):
+            ctx.step(U, n * w.k)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     print(f"{w.name} {args.precision}: {args.steps} steps in {dt * 1e3:.2f} ms, info {ctx.info()}, "
