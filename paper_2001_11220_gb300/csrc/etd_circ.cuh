@@ -967,6 +967,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   int it = 0;            // groups this block has processed (mbarrier phase)
   // wait until field fld of the current group is in shared memory; with
   // cp.async, `pending` is how many later commit groups may stay in flight
+  // (TMA: every thread observes the field's mbarrier phase itself, no block barrier)
   auto wait_field = [&](int fld, int pending) {
     if constexpr (TMA) {
       if (!mbar_wait(&fbar[fld], (unsigned)(it & 1), &wait_fail)) atomicOr(&g_circ_status, 1);
@@ -974,8 +975,13 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
       if (pending >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
       else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
       else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
     }
+  };
+  // the block is done with field fld of this group: refill its buffer with group gn
+  auto refill = [&](int fld, int gn) {
     __syncthreads();
+    stage(fld, gn);
   };
 
   if constexpr (KIND == SWEEP_MIDDLE) {
@@ -1035,8 +1041,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
             op -= st;
           }
         }
-        __syncthreads();  // every thread is done with this field's buffer
-        stage(fld, g + ncl);
+        refill(fld, g + ncl);  // every thread is done with this field's buffer
       }
       // P_2 on w
       {
@@ -1078,8 +1083,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
             op -= st;
           }
         }
-        __syncthreads();
-        stage(2, g + ncl);
+        refill(2, g + ncl);
       }
       ++it;
     }
@@ -1129,8 +1133,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           }
         }
       }
-      __syncthreads();  // w of g fully read: refill with the next group's
-      stage(2, g + ncl);
+      refill(2, g + ncl);  // w of g fully read: refill with the next group's
       // ---- F(U*, t_{n+1}); f1, f2 over the staged c_U, c_f; summaries of T f1, S f2
       wait_field(0, 1);  // c_U, c_f of g
       wait_field(1, 1);
@@ -1185,8 +1188,7 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
           op -= st;
         }
       }
-      __syncthreads();  // f1, f2 of g fully read: refill with the next group's c_U, c_f
-      stage(0, g + ncl);
+      refill(0, g + ncl);  // f1, f2 of g fully read: refill with the next group's c_U, c_f
       stage(1, g + ncl);
       ++it;
     }
