@@ -1129,6 +1129,7 @@ void etd_destroy(etd_ctx *ctx) {
   if (ctx->adj_part) cudaFree(ctx->adj_part);
   if (ctx->ckpt) cudaFree(ctx->ckpt);
   if (ctx->seg) cudaFree(ctx->seg);
+  if (ctx->seg_mid) cudaFree(ctx->seg_mid);
   for (auto &rec : ctx->prof_events) {
     cudaEventDestroy(rec.second.first);
     cudaEventDestroy(rec.second.second);

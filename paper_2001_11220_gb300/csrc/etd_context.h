@@ -164,6 +164,8 @@ struct etd_ctx {
   size_t ckpt_states = 0;
   void *seg = nullptr;            // states of one recomputed segment
   size_t seg_states = 0;
+  void *seg_mid = nullptr;        // first (and middle) sweep outputs of every step of the segment
+  size_t seg_mid_steps = 0;
 };
 
 namespace etd {

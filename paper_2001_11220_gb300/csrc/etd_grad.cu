@@ -200,14 +200,36 @@ cudaError_t forward_intermediates(const Instance &I, const R *Un, double t, R *f
   return cudaSuccess;
 }
 
+// One forward step U_{n+1} = step(U_n) out of place, keeping the first
+// sweep's outputs in fa and (3D) the middle sweep's in fb: the inputs of the
+// step's later sweeps, which its adjoint reads.
 template <typename R>
-cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double t, const R *ubar_next, R *ubar_out) {
-  cudaStream_t s = ctx->stream;
-  const size_t F = (size_t)I.S * I.N;
-  R *ws = (R *)ctx->adj_ws;
-  R *fa = ws, *fb = ws + 3 * F, *cb = ws + 6 * F;
+cudaError_t step_keep_t(const Instance &I, const R *Un, R *Unext, double t, R *fa, R *fb, cudaStream_t s) {
   cudaError_t e = forward_intermediates<R>(I, Un, t, fa, fb, s);
   if (e != cudaSuccess) return e;
+  const size_t F = (size_t)I.S * I.N;
+  const R *z = (I.dim == 3) ? fb : fa;
+  const int a = I.dim - 1;
+  SweepArgs<R> A;
+  fill_args<R>(I, a, 0, A);
+  A.in[0] = z;
+  A.in[1] = z + F;
+  A.in[2] = z + 2 * F;
+  A.out[0] = Unext;
+  A.t_eval = t + I.k;
+  A.exp_mt = std::exp(-A.t_eval);
+  A.exp_mtR = (R)A.exp_mt;
+  return run_sweep<R>(I, a, A, s);
+}
+
+// The adjoint sweeps of step n from the kept intermediates fa, fb of U_n.
+template <typename R>
+cudaError_t adjoint_sweeps_t(etd_ctx *ctx, const Instance &I, const R *Un, double t, const R *ubar_next, R *ubar_out,
+                             const R *fa, const R *fb) {
+  cudaStream_t s = ctx->stream;
+  const size_t F = (size_t)I.S * I.N;
+  R *cb = (R *)ctx->adj_ws + 6 * F;
+  cudaError_t e = cudaSuccess;
   const R *z = (I.dim == 3) ? fb : fa;  // inputs of the last forward sweep
   for (int a = I.dim - 1; a >= 0; --a) {
     const AxisPlan &P = I.aplan[a];
@@ -261,6 +283,33 @@ cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double 
   return cudaSuccess;
 }
 
+template <typename R>
+cudaError_t adjoint_step_t(etd_ctx *ctx, const Instance &I, const R *Un, double t, const R *ubar_next, R *ubar_out) {
+  const size_t F = (size_t)I.S * I.N;
+  R *ws = (R *)ctx->adj_ws;
+  R *fa = ws, *fb = ws + 3 * F;
+  cudaError_t e = forward_intermediates<R>(I, Un, t, fa, fb, ctx->stream);
+  if (e != cudaSuccess) return e;
+  return adjoint_sweeps_t<R>(ctx, I, Un, t, ubar_next, ubar_out, fa, fb);
+}
+
+cudaError_t step_keep(const Instance &I, const void *Un, void *Unext, double t, void *fa, void *fb, cudaStream_t s) {
+  if (I.real_bytes == 8)
+    return step_keep_t<double>(I, (const double *)Un, (double *)Unext, t, (double *)fa, (double *)fb, s);
+  return step_keep_t<float>(I, (const float *)Un, (float *)Unext, t, (float *)fa, (float *)fb, s);
+}
+cudaError_t keep_intermediates(const Instance &I, const void *Un, double t, void *fa, void *fb, cudaStream_t s) {
+  if (I.real_bytes == 8) return forward_intermediates<double>(I, (const double *)Un, t, (double *)fa, (double *)fb, s);
+  return forward_intermediates<float>(I, (const float *)Un, t, (float *)fa, (float *)fb, s);
+}
+cudaError_t adjoint_sweeps(etd_ctx *ctx, const Instance &I, const void *Un, double t, const void *ub_next,
+                           void *ub_out, const void *fa, const void *fb) {
+  if (I.real_bytes == 8)
+    return adjoint_sweeps_t<double>(ctx, I, (const double *)Un, t, (const double *)ub_next, (double *)ub_out,
+                                    (const double *)fa, (const double *)fb);
+  return adjoint_sweeps_t<float>(ctx, I, (const float *)Un, t, (const float *)ub_next, (float *)ub_out,
+                                 (const float *)fa, (const float *)fb);
+}
 cudaError_t adjoint_step(etd_ctx *ctx, const Instance &I, const void *Un, double t, const void *ub_next, void *ub_out) {
   if (I.real_bytes == 8)
     return adjoint_step_t<double>(ctx, I, (const double *)Un, t, (const double *)ub_next, (double *)ub_out);
@@ -371,18 +420,53 @@ etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target
     e = cudaMemcpyAsync(ub, ubarN, bytes, cudaMemcpyDeviceToDevice, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "final cotangent");
+  // Intermediates kept during the segment recompute (the first sweep's outputs
+  // and, in 3D, the middle sweep's of every step of the segment), when they
+  // fit in device memory: the reverse steps then read them instead of running
+  // those sweeps again.  ETD_GRAD_KEEP=0 recomputes them (less memory).
+  const size_t mid_bytes = bytes * 3 * (size_t)(I.dim - 1);
+  const char *kv = std::getenv("ETD_GRAD_KEEP");
+  bool keep = !(kv && kv[0] == '0');
+  if (keep && ctx->seg_mid_steps < (size_t)seglen) {
+    if (ctx->seg_mid) cudaFree(ctx->seg_mid);
+    ctx->seg_mid = nullptr;
+    ctx->seg_mid_steps = 0;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && mid_bytes * seglen + ((size_t)1 << 30) <= fr &&
+        cudaMalloc(&ctx->seg_mid, mid_bytes * seglen) == cudaSuccess)
+      ctx->seg_mid_steps = seglen;
+    else
+      cudaGetLastError();
+  }
+  keep = keep && ctx->seg_mid_steps >= (size_t)seglen;
+  unsigned char *mid = (unsigned char *)ctx->seg_mid;
   // reverse pass, segment by segment: recompute the segment's states from its
   // checkpoint, then walk its steps backwards
   for (int64_t g = nseg - 1; g >= 0 && nsteps > 0; --g) {
     const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
     e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
-    for (int64_t i = 1; i < len && e == cudaSuccess; ++i) {
-      e = cudaMemcpyAsync(sg + bytes * i, sg + bytes * (i - 1), bytes, cudaMemcpyDeviceToDevice, s);
-      if (e == cudaSuccess) e = forward_step(I, sg + bytes * i, t0 + (double)(s0 + i - 1) * I.k, s, nullptr);
+    if (keep) {
+      for (int64_t i = 0; i < len && e == cudaSuccess; ++i) {
+        unsigned char *fa = mid + mid_bytes * i, *fb = fa + 3 * bytes;
+        const double ti = t0 + (double)(s0 + i) * I.k;
+        if (i + 1 < len) e = step_keep(I, sg + bytes * i, sg + bytes * (i + 1), ti, fa, fb, s);
+        else e = keep_intermediates(I, sg + bytes * i, ti, fa, fb, s);
+      }
+    } else {
+      for (int64_t i = 1; i < len && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync(sg + bytes * i, sg + bytes * (i - 1), bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = forward_step(I, sg + bytes * i, t0 + (double)(s0 + i - 1) * I.k, s, nullptr);
+      }
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "segment recompute");
     for (int64_t i = len - 1; i >= 0; --i) {
-      e = adjoint_step(ctx, I, sg + bytes * i, t0 + (double)(s0 + i) * I.k, ub, ub2);
+      const double ti = t0 + (double)(s0 + i) * I.k;
+      if (keep) {
+        unsigned char *fa = mid + mid_bytes * i, *fb = fa + 3 * bytes;
+        e = adjoint_sweeps(ctx, I, sg + bytes * i, ti, ub, ub2, fa, fb);
+      } else {
+        e = adjoint_step(ctx, I, sg + bytes * i, ti, ub, ub2);
+      }
       if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint step");
       std::swap(ub, ub2);
     }
