@@ -397,29 +397,6 @@ etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target
   cudaError_t e = cudaMemsetAsync(ctx->adj_acc, 0, 16 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(run, U0, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "grad setup");
-  // forward pass with checkpoints (U_{g ckpt} for every segment g)
-  for (int64_t g = 0; g < nseg; ++g) {
-    e = cudaMemcpyAsync(ck + bytes * g, run, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "checkpoint copy");
-    const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
-    for (int64_t i = 0; i < len; ++i) {
-      e = forward_step(I, run, t0 + (double)(s0 + i) * I.k, s, nullptr);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "forward step");
-    }
-  }
-  // cotangent of U_N: misfit gradient U_N - target, or the caller's
-  void *ub = ctx->adj_ubar[0], *ub2 = ctx->adj_ubar[1];
-  if (target) {
-    if (I.real_bytes == 8)
-      e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
-                      ctx->adj_acc + 10, ctx->adj_part, s);
-    else
-      e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N,
-                      ctx->adj_acc + 10, ctx->adj_part, s);
-  } else {
-    e = cudaMemcpyAsync(ub, ubarN, bytes, cudaMemcpyDeviceToDevice, s);
-  }
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "final cotangent");
   // Intermediates kept during the segment recompute (the first sweep's outputs
   // and, in 3D, the middle sweep's of every step of the segment), when they
   // fit in device memory: the reverse steps then read them instead of running
@@ -440,12 +417,50 @@ etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target
   }
   keep = keep && ctx->seg_mid_steps >= (size_t)seglen;
   unsigned char *mid = (unsigned char *)ctx->seg_mid;
+  // forward pass with checkpoints (U_{g ckpt} for every segment g); the last
+  // segment keeps its states and intermediates right away, so the reverse
+  // pass does not recompute it
+  for (int64_t g = 0; g < nseg; ++g) {
+    e = cudaMemcpyAsync(ck + bytes * g, run, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "checkpoint copy");
+    const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
+    if (keep && g == nseg - 1) {
+      e = cudaMemcpyAsync(sg, run, bytes, cudaMemcpyDeviceToDevice, s);
+      for (int64_t i = 0; i < len && e == cudaSuccess; ++i) {
+        unsigned char *fa = mid + mid_bytes * i, *fb = fa + 3 * bytes;
+        e = step_keep(I, sg + bytes * i, i + 1 < len ? sg + bytes * (i + 1) : run, t0 + (double)(s0 + i) * I.k, fa,
+                      fb, s);
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "forward step");
+      continue;
+    }
+    for (int64_t i = 0; i < len; ++i) {
+      e = forward_step(I, run, t0 + (double)(s0 + i) * I.k, s, nullptr);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "forward step");
+    }
+  }
+  // cotangent of U_N: misfit gradient U_N - target, or the caller's
+  void *ub = ctx->adj_ubar[0], *ub2 = ctx->adj_ubar[1];
+  if (target) {
+    if (I.real_bytes == 8)
+      e = launch_loss((const double *)run, (const double *)target, (double *)ub, (long long)I.S * I.N,
+                      ctx->adj_acc + 10, ctx->adj_part, s);
+    else
+      e = launch_loss((const float *)run, (const float *)target, (float *)ub, (long long)I.S * I.N,
+                      ctx->adj_acc + 10, ctx->adj_part, s);
+  } else {
+    e = cudaMemcpyAsync(ub, ubarN, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "final cotangent");
   // reverse pass, segment by segment: recompute the segment's states from its
   // checkpoint, then walk its steps backwards
   for (int64_t g = nseg - 1; g >= 0 && nsteps > 0; --g) {
     const int64_t s0 = g * ckpt_every, len = std::min<int64_t>(ckpt_every, nsteps - s0);
-    e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
-    if (keep) {
+    e = cudaSuccess;
+    if (keep && g == nseg - 1) {
+      // kept by the forward pass
+    } else if (keep) {
+      e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
       for (int64_t i = 0; i < len && e == cudaSuccess; ++i) {
         unsigned char *fa = mid + mid_bytes * i, *fb = fa + 3 * bytes;
         const double ti = t0 + (double)(s0 + i) * I.k;
@@ -453,6 +468,7 @@ etd_status grad_core(etd_ctx *ctx, const void *U0, double t0, const void *target
         else e = keep_intermediates(I, sg + bytes * i, ti, fa, fb, s);
       }
     } else {
+      e = cudaMemcpyAsync(sg, ck + bytes * g, bytes, cudaMemcpyDeviceToDevice, s);
       for (int64_t i = 1; i < len && e == cudaSuccess; ++i) {
         e = cudaMemcpyAsync(sg + bytes * i, sg + bytes * (i - 1), bytes, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = forward_step(I, sg + bytes * i, t0 + (double)(s0 + i - 1) * I.k, s, nullptr);
