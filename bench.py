@@ -63,7 +63,7 @@ def _peaks():
 # depends on nothing else but the tile shapes, recorded beside each entry)
 SWEEP_SOURCES = ("etd_internal.h", "etd_tables.h", "etd_sweep.cuh", "etd_sweep_smem.cuh", "etd_sweep_launch.cuh",
                  "etd_sweep_f32.cu", "etd_sweep_f64.cu", "etd_sweep_cluster.cu", "etd_circ.h", "etd_circ.cuh",
-                 "etd_circ.cu")
+                 "etd_circ.cu", "etd_circ_rk_first.cu", "etd_circ_rk_strided.cu")
 
 
 def _csrc_hash() -> str:
@@ -310,12 +310,17 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
     msg = _timed(lambda: c.grad(U, 0.0, tg, 20, 20), stream)
     units = w.npoints * w.nspecies * 20
     alg = c.info()["algorithmic_bytes"]
-    # reverse step (per step of the gradient, FP32, 2 species, N points): recompute x and y
-    # sweeps (4 + 6 fields), ADJ_LAST (reads Ubar', c_U, c_f, w; writes 3: 7 fields),
-    # ADJ_MIDDLE (6 adjoint + 3 forward fields read, 3 written: 12), ADJ_FIRST (3 adjoint + U_n
-    # read, Ubar_n written: 5), plus the checkpoint recomputation of the forward step (14)
-    rev_fields = 4 + 6 + 7 + 12 + 5 + 14
+    # reverse step (per step of the gradient, FP32, 2 species, N points; one checkpoint segment,
+    # whose states and first/middle sweep outputs the forward pass keeps): ADJ_LAST (reads
+    # Ubar', c_U, c_f, w; writes 3: 7 fields), ADJ_MIDDLE (3 adjoint + 3 forward fields read,
+    # 3 written: 9), ADJ_FIRST (3 adjoint + U_n read, Ubar_n written: 5)
+    rev_fields = 7 + 9 + 5
     fb = w.nspecies * w.npoints * 4
+    # one adjoint step alone (etd_step_adjoint: the forward x and y sweeps of U_n, 4 + 6 fields,
+    # then the three adjoint sweeps), CUDA events around the call
+    ubar = torch.ones_like(U)
+    msa = _timed(lambda: c.step_adjoint(U, 0.0, ubar), stream, reps=5)
+    adj_fields = 4 + 6 + rev_fields
     out[f"grayscott3d_{P_3D}_fp32"] = {
         "fwd": units / (msf / 1e3), "fwd_adjoint": units / (msg / 1e3), "unit": UNIT,
         "fwd_ms_per_step": msf / 20, "fwd_adjoint_ms_per_step": msg / 20, "tiles": tiles,
@@ -323,7 +328,12 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "per_sweep": per,
                      "fwd_step_frac": alg / (msf / 20 / 1e3) / 1e9 / peak,
                      "fwd_adjoint_algorithmic_bytes_per_step": alg + rev_fields * fb,
-                     "fwd_adjoint_step_frac": (alg + rev_fields * fb) / (msg / 20 / 1e3) / 1e9 / peak}}
+                     "fwd_adjoint_step_frac": (alg + rev_fields * fb) / (msg / 20 / 1e3) / 1e9 / peak,
+                     "adjoint_step": {"ms": msa, "algorithmic_bytes": adj_fields * fb,
+                                      "achieved_gbs": adj_fields * fb / (msa / 1e3) / 1e9,
+                                      "frac": adj_fields * fb / (msa / 1e3) / 1e9 / peak,
+                                      "note": "etd_step_adjoint: forward x, y sweeps of U_n (10 fields) + "
+                                              "ADJ_LAST 7, ADJ_MIDDLE 9, ADJ_FIRST 5 fields"}}}
     c.close()
     del U, V, tg
     # 2D Brusselator 64^2 Neumann, FP64, 100 steps (T = 1): L2-resident, microseconds per step
