@@ -25,7 +25,7 @@ _HDR = os.path.join(_HERE, "etd_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 DIRICHLET, NEUMANN, PERIODIC = 0, 1, 2
-ZERO, LINEAR, BRUSSELATOR, SCHNAKENBERG, GRAY_SCOTT, ENZYME = range(6)
+ZERO, LINEAR, BRUSSELATOR, SCHNAKENBERG, GRAY_SCOTT, ENZYME, CGL = range(7)
 
 
 def build(force: bool = False) -> str:

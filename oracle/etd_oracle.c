@@ -61,9 +61,9 @@ static int check_problem(const oracle_problem *P) {
   for (int s = 0; s < P->nspecies; ++s)
     if (!(P->D[s] >= 0)) return -1;
   if ((P->reaction == OR_BRUSSELATOR || P->reaction == OR_SCHNAKENBERG ||
-       P->reaction == OR_GRAY_SCOTT) && P->nspecies != 2) return -1;
+       P->reaction == OR_GRAY_SCOTT || P->reaction == OR_CGL) && P->nspecies != 2) return -1;
   if (P->reaction == OR_ENZYME && P->nspecies != 1) return -1;
-  if (P->reaction < 0 || P->reaction > OR_ENZYME) return -1;
+  if (P->reaction < 0 || P->reaction > OR_CGL) return -1;
   return 0;
 }
 
@@ -346,6 +346,19 @@ static void reaction_point(const oracle_problem *P, const double *u, const int *
     G[0][0] = 1.0 - U;
     G[1][0] = -V;
     G[1][1] = -V;
+    break;
+  }
+  case OR_CGL: { /* u = a + i b, r = |u|^2: F = u - (1 + i beta) u r (Section 8, CGL with alpha = 0) */
+    double beta = p[0], a = u[0], b = u[1], r = a * a + b * b;
+    double ca = a - beta * b, cb = beta * a + b; /* (1 + i beta) u */
+    f[0] = a - r * ca;
+    f[1] = b - r * cb;
+    J[0][0] = 1.0 - r - 2.0 * a * ca;
+    J[0][1] = beta * r - 2.0 * b * ca;
+    J[1][0] = -beta * r - 2.0 * a * cb;
+    J[1][1] = 1.0 - r - 2.0 * b * cb;
+    G[0][0] = r * b;
+    G[1][0] = -r * a;
     break;
   }
   case OR_ENZYME: {

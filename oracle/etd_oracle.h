@@ -42,7 +42,9 @@ enum {
   OR_BRUSSELATOR = 2,  /* F_u = a + u^2 v - (b+1) u ; F_v = b u - u^2 v ; p = (a, b) */
   OR_SCHNAKENBERG = 3, /* F_u = g (a - u + u^2 v) ; F_v = g (b - u^2 v) ; p = (a, b, g) */
   OR_GRAY_SCOTT = 4,   /* F_u = -u v^2 + F (1-u) ; F_v = u v^2 - (F+kappa) v ; p = (F, kappa) */
-  OR_ENZYME = 5        /* F = -u/(1+u) + p0 * src(x,t; p1) (Section 8.1, plus manufactured source) */
+  OR_ENZYME = 5,       /* F = -u/(1+u) + p0 * src(x,t; p1) (Section 8.1, plus manufactured source) */
+  OR_CGL = 6           /* complex Ginzburg-Landau with real diffusion (Section 8, alpha = 0): species
+                          0, 1 = Re, Im of u; F = u - (1 + i beta) u |u|^2 ; p = (beta) */
 };
 
 typedef struct {

@@ -20,7 +20,8 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 DIRICHLET, NEUMANN, PERIODIC = 0, 1, 2
-REACTIONS = {"zero": 0, "linear": 1, "brusselator": 2, "schnakenberg": 3, "gray_scott": 4, "enzyme": 5}
+REACTIONS = {"zero": 0, "linear": 1, "brusselator": 2, "schnakenberg": 3, "gray_scott": 4, "enzyme": 5,
+             "cgl": 6}
 BC_NAMES = {DIRICHLET: "dirichlet", NEUMANN: "neumann", PERIODIC: "periodic"}
 
 
@@ -132,6 +133,16 @@ def initial_state(w: Workload, seed: int | None = None) -> np.ndarray:
         U[1][sl] = 0.25
         U += noise * rng.standard_normal(shape)
         return U
+    if w.ic == "cgl_pulses":          # Section 8 (CGL): Gaussian pulses (real part), imaginary part 0
+        g = _grids(w)
+        if w.dim == 2:
+            centres, signs = ((50, 50), (100, 100), (100, 50)), (1.0, -1.0, 1.0)
+        else:
+            centres, signs = ((50, 50, 50), (100, 100, 100)), (1.0, -1.0)
+        re = np.zeros(shape[1:])
+        for c, sg in zip(centres, signs):
+            re += sg * np.exp(-sum((g[a] - c[a]) ** 2 for a in range(w.dim)) / 1000.0)
+        return np.stack([re, np.zeros_like(re)])
     raise ValueError(f"unknown initial-state recipe {w.ic!r}")
 
 
@@ -191,6 +202,22 @@ def enzyme_paper(p: int = 79, k: float = 0.05) -> Workload:
     """Section 8.1: u_t = D Lap u - u/(1+u), D = 0.2, unit square, Dirichlet 0, u(x,0) = 1, T = 1."""
     return Workload("enzyme_paper", (p, p), DIRICHLET, (0.2,), "enzyme", (0.0, 0.0), k,
                     int(round(1.0 / k)), ic="constant", ic_args=((1.0,),))
+
+
+def cgl_2d(p: int = 400, steps: int = 2000, ic: str = "cgl_pulses", beta: float = 1.3, seed: int = 2001) -> Workload:
+    """Section 8: complex Ginzburg-Landau u_t = u + (1 + i alpha) Lap u - (1 + i beta) u |u|^2 with
+    alpha = 0 (real diffusion, D = 1 for Re u and Im u), beta = 1.3, periodic [0, 200]^2, p = 400
+    (h = 1/2), k = 1/20, T = 100 (2000 steps); Gaussian pulses, or ic="normal": N(0, 1) field."""
+    ic_args = ((0.0, 0.0), 1.0) if ic == "normal" else ()
+    return Workload(f"cgl2d_{p}", (p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
+                    length=(200.0, 200.0), ic=ic, ic_args=ic_args, seed=seed)
+
+
+def cgl_3d(p: int = 200, steps: int = 2000, beta: float = 1.3) -> Workload:
+    """Section 8: the same equation on periodic [0, 200]^3, p = 200 (h = 1), k = 1/20, T = 100,
+    Gaussian pulses."""
+    return Workload(f"cgl3d_{p}", (p, p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
+                    length=(200.0, 200.0, 200.0), ic="cgl_pulses")
 
 
 def brusselator_paper(p: int = 81, k: float = 0.1) -> Workload:

@@ -240,7 +240,8 @@ def test_constant_source_constant_state():
 
 @pytest.mark.parametrize("kind,params,S", [(oracle.LINEAR, (-0.7, 0.3), 2), (oracle.BRUSSELATOR, (1.0, 3.4), 2),
                                            (oracle.SCHNAKENBERG, (0.1, 0.9, 5.0), 2),
-                                           (oracle.GRAY_SCOTT, (0.04, 0.06), 2), (oracle.ENZYME, (1.0, 0.8), 1)])
+                                           (oracle.GRAY_SCOTT, (0.04, 0.06), 2), (oracle.ENZYME, (1.0, 0.8), 1),
+                                           (oracle.CGL, (1.3,), 2)])
 def test_reaction_derivatives_fd(kind, params, S):
     P = oracle.Problem(n=(5, 4), bc=(0, 0), D=(0.1,) * S, reaction=kind, params=params, k=0.1)
     U = 0.5 + 0.5 * RNG.random(P.shape)
@@ -462,3 +463,55 @@ def test_threads_do_not_change_results():
     finally:
         oracle.set_threads(prev)
     assert np.array_equal(a, b)
+
+
+# ------------------------------------------------- complex Ginzburg-Landau --
+# Section 8: u_t = u + (1 + i alpha) Lap u - (1 + i beta) u |u|^2 with alpha = 0,
+# carried as two real species (Re u, Im u) with the same real D.
+
+def test_cgl_reaction_hand_values():
+    """F = u - (1 + i beta) u |u|^2 at u = 0.6 + 0.8 i (|u| = 1) with beta = 1.3 is
+    -i beta u = 1.04 - 0.78 i; at u = 0.5 (|u|^2 = 0.25): 0.5 - 0.125 (1 + 1.3 i)
+    = 0.375 - 0.1625 i."""
+    P = oracle.Problem(n=(4, 4), bc=(2, 2), D=(1.0, 1.0), reaction=oracle.CGL, params=(1.3,), k=0.05)
+    for (a, b), (fa, fb) in (((0.6, 0.8), (1.04, -0.78)), ((0.5, 0.0), (0.375, -0.1625))):
+        U = np.stack([np.full((4, 4), a), np.full((4, 4), b)])
+        F = oracle.reaction(P, U, 0.0)
+        assert abs(F[0, 0, 0] - fa) < 1e-15 and abs(F[1, 0, 0] - fb) < 1e-15, (F[:, 0, 0], fa, fb)
+
+
+def test_cgl_uniform_unit_modulus_state_rotates_at_second_order():
+    """A uniform state of modulus 1 has zero Laplacian and F = -i beta u, so the exact
+    solution is u(t) = e^{-i beta t} u0.  The scheme integrates this ODE at second
+    order: halving k divides the error at T = 1 by about 4."""
+    beta, T = 1.3, 1.0
+    u0 = np.exp(0.4j)
+    errs = []
+    for k in (0.05, 0.025, 0.0125):
+        P = oracle.Problem(n=(8, 8), bc=(2, 2), D=(1.0, 1.0), reaction=oracle.CGL, params=(beta,), k=k)
+        U = np.stack([np.full((8, 8), u0.real), np.full((8, 8), u0.imag)])
+        V = oracle.run(P, U, 0.0, int(round(T / k)))
+        exact = u0 * np.exp(-1j * beta * T)
+        errs.append(max(np.max(np.abs(V[0] - exact.real)), np.max(np.abs(V[1] - exact.imag))))
+        assert np.max(np.abs(V - V[:, :1, :1])) < 1e-14   # stays uniform
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_cgl_phase_equivariance():
+    """The equation is invariant under u -> e^{i phi} u, and so is the scheme: real
+    line matrices act on Re u and Im u alike and F(e^{i phi} u) = e^{i phi} F(u).  A
+    rotated initial state gives the rotated solution (to rounding); a wrong sign or a
+    swapped coupling term of F breaks this."""
+    P = oracle.Problem(n=(12, 10), bc=(2, 2), D=(1.0, 1.0), reaction=oracle.CGL, params=(1.3,), k=0.05,
+                       length=(6.0, 5.0))
+    rng = np.random.default_rng(7)
+    U = 0.5 * rng.standard_normal((2, 10, 12))
+    phi = 0.9
+    c, s = np.cos(phi), np.sin(phi)
+    R = np.stack([c * U[0] - s * U[1], s * U[0] + c * U[1]])
+    V = oracle.run(P, U, 0.0, 6)
+    VR = oracle.run(P, R, 0.0, 6)
+    rot = np.stack([c * V[0] - s * V[1], s * V[0] + c * V[1]])
+    assert np.max(np.abs(VR - rot)) < 1e-13 * max(1.0, np.max(np.abs(V)))
+    assert np.max(np.abs(V - U)) > 1e-2   # the run did something
