@@ -364,6 +364,24 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
                                            "step_frac": 8 * cells * 4 / (ms_max / 20 / 1e3) / 1e9 / peak,
                                            "scaling": "strong (instances sharded across ranks)"}
     ens.close()
+    # Section 8's complex Ginzburg-Landau runs (alpha = 0, beta = 1.3, k = 1/20, T = 100, periodic,
+    # Gaussian pulses): 2D [0,200]^2 at p = 400 and 3D [0,200]^3 at p = 200, FP32; the whole
+    # 2000-step run time extrapolated from the timed steps, beside the paper's Fortran times
+    # (Intel i7-4790, Table tableginz / tableginz2) as context
+    for wcgl, nst, paper_s in ((W.cgl_2d(400), 200, {"fortran_1_thread_s": 86.66, "fortran_3_threads_s": 53.98,
+                                                      "matlab_s": 95.65}),
+                               (W.cgl_3d(200), 40, {"fortran_1_thread_s": 8260.91, "fortran_3_threads_s": 5287.64,
+                                                    "matlab_s": 9673.13})):
+        c, U = mk(wcgl, "fp32")
+        ms = _timed(lambda: c.run(U, 0.0, nst), stream)
+        out[f"{wcgl.name}_fp32"] = {"value": wcgl.npoints * wcgl.nspecies * nst / (ms / 1e3), "unit": UNIT,
+                                    "ms_per_step": ms / nst,
+                                    "full_run_s": ms / nst * wcgl.steps / 1e3, "steps_full_run": wcgl.steps,
+                                    "tiles": tiles_of(c.info(), wcgl.dim),
+                                    "step_frac": c.info()["algorithmic_bytes"] / (ms / nst / 1e3) / 1e9 / peak,
+                                    "paper_cpu_context": paper_s}
+        c.close()
+        del U
     return out
 
 

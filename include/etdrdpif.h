@@ -66,14 +66,18 @@ typedef enum { ETD_FP64 = 0, ETD_FP32 = 1 } etd_precision;
  *   ENZYME        F = -u/(1+u) + p0 src(x,t), src the manufactured source
  *                 (p1 Sum_a (pi/L_a)^2 - 1) q + q/(1+q),
  *                 q = e^{-t} Prod_a sin(pi x_a/L_a)                 (s = 1;
- *                 Section 8.1; p0 = 0 gives the paper's enzyme model) */
+ *                 Section 8.1; p0 = 0 gives the paper's enzyme model)
+ *   CGL           complex Ginzburg-Landau of Section 8 with real diffusion
+ *                 (alpha = 0, the paper's runs): species 0, 1 = Re u, Im u,
+ *                 F = u - (1 + i p0) u |u|^2                           (s = 2) */
 typedef enum {
   ETD_REACTION_ZERO = 0,
   ETD_REACTION_LINEAR = 1,
   ETD_REACTION_BRUSSELATOR = 2,
   ETD_REACTION_SCHNAKENBERG = 3,
   ETD_REACTION_GRAY_SCOTT = 4,
-  ETD_REACTION_ENZYME = 5
+  ETD_REACTION_ENZYME = 5,
+  ETD_REACTION_CGL = 6
 } etd_reaction_kind;
 
 typedef struct {

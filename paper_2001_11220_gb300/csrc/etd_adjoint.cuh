@@ -71,6 +71,15 @@ __device__ __forceinline__ void reaction_vjp(const SweepArgs<R> &A, const R (&u)
         pg[1] -= V * yb[1];
       }
       return;
+    case 6:
+      if constexpr (S == 2) {  // CGL (alpha = 0): F = u - (1 + i beta) u |u|^2, r = |u|^2
+        const R beta = (R)A.rp[0], a = u[0], b = u[1];
+        const R r = a * a + b * b, ca = a - beta * b, cb = beta * a + b;
+        out[0] = (R(1) - r - R(2) * a * ca) * yb[0] + (-beta * r - R(2) * a * cb) * yb[1];
+        out[1] = (beta * r - R(2) * b * ca) * yb[0] + (R(1) - r - R(2) * b * cb) * yb[1];
+        pg[0] += r * (b * yb[0] - a * yb[1]);
+      }
+      return;
     case 5: {  // enzyme kinetics + manufactured source
       const R d = R(1) + u[0];
       out[0] = -rdiv(yb[0], d * d);

@@ -70,6 +70,7 @@ etd_status validate_problem(const etd_grid *grid, const double *D, const etd_rea
     case ETD_REACTION_BRUSSELATOR:
     case ETD_REACTION_SCHNAKENBERG:
     case ETD_REACTION_GRAY_SCOTT:
+    case ETD_REACTION_CGL:
       if (S != 2) return fail(nullptr, ETD_ERR_INVALID_ARG, "reaction %d needs 2 species", rx->kind);
       break;
     case ETD_REACTION_ENZYME:

@@ -74,6 +74,11 @@ __device__ __forceinline__ void reaction_kind(const CircArgs<R> &A, const R (&u)
     f[0] = A.rpR[0] * (R(1) - u[0]) - uvv;
     f[1] = uvv - (A.rpR[0] + A.rpR[1]) * u[1];
     return;
+  } else if constexpr (K == 6 && S == 2) {  // CGL (alpha = 0): u - (1 + i beta) u |u|^2, u = u0 + i u1
+    const R beta = A.rpR[0], r = fma(u[0], u[0], u[1] * u[1]);
+    f[0] = fma(-r, fma(-beta, u[1], u[0]), u[0]);
+    f[1] = fma(-r, fma(beta, u[0], u[1]), u[1]);
+    return;
   } else if constexpr (K == 5) {  // enzyme kinetics without a source term
     f[0] = -rdivc(u[0], R(1) + u[0]);
 #pragma unroll
@@ -96,6 +101,7 @@ __device__ __forceinline__ void reaction(const CircArgs<R> &A, const R (&u)[S], 
       case 3: reaction_kind<R, S, 3>(A, u, f); return;
       case 4: reaction_kind<R, S, 4>(A, u, f); return;
       case 5: reaction_kind<R, S, 5>(A, u, f); return;
+      case 6: reaction_kind<R, S, 6>(A, u, f); return;
       default: reaction_kind<R, S, 0>(A, u, f); return;
     }
   }

@@ -150,6 +150,14 @@ __device__ __forceinline__ void reaction_point(const SweepArgs<R> &A, const R (&
         return;
       }
       break;
+    case 6:
+      if constexpr (S == 2) {  // CGL (alpha = 0): u - (1 + i beta) u |u|^2, u = u0 + i u1
+        const R beta = A.rpR[0], r = fma(u[0], u[0], u[1] * u[1]);
+        f[0] = fma(-r, fma(-beta, u[1], u[0]), u[0]);
+        f[1] = fma(-r, fma(beta, u[0], u[1]), u[1]);
+        return;
+      }
+      break;
     case 5:  // enzyme kinetics (Section 8.1) plus the manufactured source
       f[0] = -rdiv(u[0], R(1) + u[0]) + src;
 #pragma unroll

@@ -45,6 +45,8 @@ STEP_CASES = [
          (0.04, 0.06), 0.5, ((0.8, 0.2), 0.05)),
     case("lin3d_neu", (10, 12, 7), W.NEUMANN, (0.3,), "linear", (-0.7, 0.2), 0.1, ((1.0,), 0.2)),
     W.mms_3d(12).with_(name="mms3d_12"),
+    case("cgl2d_per", (24, 20), W.PERIODIC, (1.0, 1.0), "cgl", (1.3,), 0.05, ((0.0, 0.0), 0.5)).with_(
+        length=(12.0, 10.0)),
     # 700-node periodic lines take the warp-cooperative chunk scan; h = 0.1 keeps the
     # dL/dD sum as well conditioned as the cases above (at h = 1/700, r = k D / h^2 ~ 4e5
     # and a one-ulp change of U_n moves the oracle's dL/dD by 3e-12 relative)

@@ -115,6 +115,8 @@ STRIDED_CASES = [
     (case("circ_3d_last", (32, 6, 512), (W.NEUMANN, W.DIRICHLET, W.PERIODIC), (0.02, 0.01), "gray_scott",
           (0.04, 0.06), k=0.5), "--c"),
     (case("circ_3d_all", (64, 128, 128), W.PERIODIC, (0.05, 0.02), "brusselator", (1.0, 3.4)), "ccc"),
+    (case("circ_cgl_xy", (256, 512), W.PERIODIC, (1.0, 1.0), "cgl", (1.3,), ic_args=((0.0, 0.0), 1.0),
+          length=(128.0, 256.0)), "cc"),
 ]
 
 

@@ -80,6 +80,11 @@ ONE_STEP_CASES = [
     case("min3d", (3, 3, 3), (W.DIRICHLET, W.NEUMANN, W.PERIODIC), (0.3, 0.1), "brusselator", (1.0, 3.4)),
     case("sch3d_stiff", (24, 24, 24), W.PERIODIC, (1.0, 10.0), "schnakenberg", (0.1, 0.9, 1000.0), k=1e-3,
          ic="uniform", ic_args=((1.0, 0.9), 1e-3)),
+    # complex Ginzburg-Landau (Section 8, alpha = 0): Re u, Im u as two species, N(0, 1) field
+    case("cgl2d_per", (40, 36), W.PERIODIC, (1.0, 1.0), "cgl", (1.3,), k=0.05, ic_args=((0.0, 0.0), 1.0),
+         length=(20.0, 18.0)),
+    case("cgl3d_per", (16, 12, 10), W.PERIODIC, (1.0, 1.0), "cgl", (1.3,), k=0.05, ic_args=((0.0, 0.0), 0.5),
+         length=(16.0, 12.0, 10.0)),
 ]
 
 
@@ -92,7 +97,7 @@ def test_one_step_fp64_matches_oracle(w):
     assert err <= FP64_TOL, err
 
 
-FP32_CASES = ("bru2d_neu_64", "bru2d_neu_ragged", "enz2d_dir_src", "enz2d_dir_plain", "sch2d_per", "gs2d_mixed",
+FP32_CASES = ("cgl2d_per", "bru2d_neu_64", "bru2d_neu_ragged", "enz2d_dir_src", "enz2d_dir_plain", "sch2d_per", "gs2d_mixed",
               "gs3d_mixed", "mms3d_16", "bru3d_per", "long_per_y")
 
 
@@ -517,3 +522,18 @@ def test_cluster_segmented_sweeps_vs_oracle(w, spec, prec, monkeypatch):
         assert e1 <= FP64_TOL and e3 <= FP64_TOL, (e1, e3)
     else:
         assert e1 <= fp32_step_bound(w) and e3 <= 3 * fp32_step_bound(w), (e1, e3, fp32_step_bound(w))
+
+
+def test_cgl_2d_paper_pulses_fp64_and_fp32():
+    """Section 8's 2D CGL run (periodic [0, 200]^2, alpha = 0, beta = 1.3, k = 1/20,
+    Gaussian pulses) at p = 64 for 40 steps: FP64 matches the oracle, FP32 stays
+    within the derived per-step bound times the linear growth e^T of the equation."""
+    w = W.cgl_2d(64, steps=40)
+    U0 = W.initial_state(w)
+    ref = oracle_run(w, U0, w.steps)
+    g64 = gpu_run(w, U0, w.steps, "fp64")
+    assert rel_err(g64, ref) <= FP64_TOL
+    g32 = gpu_run(w, U0, w.steps, "fp32")
+    e32 = rel_err(g32, ref)
+    print(f"cgl2d_64 40 steps: FP64 {rel_err(g64, ref):.2e}, FP32 {e32:.2e} vs oracle")
+    assert e32 <= w.steps * fp32_step_bound(w) * math.exp(w.steps * w.k)
