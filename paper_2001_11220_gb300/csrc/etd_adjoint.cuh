@@ -155,6 +155,72 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
   }
 }
 
+// ---- circulant line solves of periodic axes (symmetric M: M^T = M), the
+// factorisation of the forward circulant sweeps: pass 1 gives the chunk's
+// zero-carry summaries F (forward value at its end) and W = sum_t lambda^t ytilde_t;
+// one thread per (line, solve) chains the m chunks of its line (cyclic
+// closures by 1/(1 - lambda^p)) and leaves the carries Yc_j (y before chunk j)
+// and Zc_j (z after it) in place of F_j, W_j; pass 2 runs both recurrences.
+template <typename R, int L>
+__device__ __forceinline__ void cpass1(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R &F, R &Wv) {
+  R y = R(0), w = R(0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    y = fma(M.lam, y, b[t]);
+    w = fma(M.pw[t], y, w);
+  }
+  F = y;
+  Wv = w;
+}
+template <typename R, int L>
+__device__ __forceinline__ void cpass2(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R Yc, R Zc,
+                                       R (&x)[L]) {
+  R y = Yc;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    y = fma(M.lam, y, b[t]);
+    x[t] = y;
+  }
+  R z = Zc;
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    z = fma(M.lam, z, x[t]);
+    x[t] = z * M.ialpha;
+  }
+}
+template <typename R, typename CIdx>
+__device__ __forceinline__ void circ_chains(const SweepArgs<R> &A, R *sF, R *sY, int q0, int nq, CIdx cidx) {
+  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    const int ci = cidx(q);
+    const typename SweepArgs<R>::CircLine &M = A.cl[ci / 3][ci % 3];
+    R *F = sF + (q * nlb + l) * pitch;
+    R *Y = sY + (q * nlb + l) * pitch;
+    R t = R(0);
+    for (int j = 0; j < m; ++j) t = fma(M.lamL, t, F[j]);
+    R y = t * M.inv1m;  // y entering chunk 0 (cyclic)
+    for (int j = 0; j < m; ++j) {
+      const R f = F[j];
+      F[j] = y;
+      y = fma(M.lamL, y, f);
+    }
+    R g = R(0);
+    for (int j = m - 1; j >= 0; --j) {
+      const R gj = fma(M.kap, F[j], Y[j]);  // backward value at the chunk start with its forward carry
+      Y[j] = gj;
+      g = fma(M.lamL, g, gj);
+    }
+    R z = g * M.inv1m;  // z after the last chunk (cyclic)
+    for (int j = m - 1; j >= 0; --j) {
+      const R gj = Y[j];
+      Y[j] = z;
+      z = fma(M.lamL, z, gj);
+    }
+  }
+}
+
 // block-wide sum of NV per-thread values, written to this block's slot
 // part[blockIdx.x * NV + i] (reduce_partials adds the slots to the
 // accumulators in a fixed order, so repeated runs give identical sums)
@@ -187,7 +253,8 @@ static __global__ void __launch_bounds__(32 * (MAX_SPECIES + 8)) reduce_partials
   if (lane == 0) acc[i] += s;
 }
 
-template <typename R, int S, int L, bool CONTIG, int KIND>
+// CIRC: periodic axis on the circulant factorisation (A.cl), else the line tables
+template <typename R, int S, int L, bool CONTIG, int KIND, bool CIRC = false>
 __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_constant__ SweepArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NQ = (KIND == ADJ_LAST) ? 6 * S : 10 * S;
@@ -229,6 +296,33 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
     X = sY[q * qstride + myidx];
     sg = sSig[q * nlb + l];
   };
+  // solve q with table M (CIRC: the circulant coefficients cl(q)): summaries,
+  // and the solution from the carries
+  auto pass1q = [&](int q, const MatTab<R> &M, const typename SweepArgs<R>::CircLine &C, const R (&b)[L]) {
+    R F, Y;
+    if constexpr (CIRC) cpass1<R, L>(C, b, F, Y);
+    else apass1<R, L>(M, m, j, b, F, Y);
+    put(q, F, Y);
+  };
+  auto pass1x2q = [&](int q0, int q1, const MatTab<R> &M, const typename SweepArgs<R>::CircLine &C,
+                      const R (&b0)[L], const R (&b1)[L]) {
+    R F0, Y0, F1, Y1;
+    if constexpr (CIRC) {
+      cpass1<R, L>(C, b0, F0, Y0);
+      cpass1<R, L>(C, b1, F1, Y1);
+    } else {
+      apass1x2<R, L>(M, m, j, b0, b1, F0, Y0, F1, Y1);
+    }
+    put(q0, F0, Y0);
+    put(q1, F1, Y1);
+  };
+  auto pass2q = [&](int q, const MatTab<R> &M, const typename SweepArgs<R>::CircLine &C, const R (&b)[L],
+                    R (&x)[L]) {
+    R G, X, sg;
+    carries(q, G, X, sg);
+    if constexpr (CIRC) cpass2<R, L>(C, b, G, X, x);
+    else apass2<R, L>(M, m, j, b, G, X, sg, x);
+  };
   auto qsrc = [&](int t) -> R {
     return (A.phi[0] != nullptr && t < cnt) ? mms_q(A, off0 + (long long)t * st) : R(0);
   };
@@ -256,6 +350,11 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       if (q < 3 * S) return r == 0 ? A.mat[s][0] : A.matT[s][r];
       return r == 2 ? A.matT[s][0] : A.mat[s][r + 1];
     };
+    auto cid = [&](int q) -> int {  // species * 3 + (0: P, 1: T, 2: S) of solve q
+      const int qq = q < 3 * S ? q : q - 3 * S;
+      const int s = qq / 3, r = qq - 3 * (qq / 3);
+      return s * 3 + (q < 3 * S ? r : (r == 2 ? 0 : r + 1));
+    };
     R w[S][L], Us[S][L], a1[S][L], a2[S][L];
     {
       R ub[S][L];
@@ -266,26 +365,19 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       }
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        R F0, Y0, F1, Y1;
-        apass1<R, L>(A.mat[s][0], m, j, w[s], F0, Y0);
-        put(3 * s, F0, Y0);
-        apass1<R, L>(A.matT[s][1], m, j, ub[s], F1, Y1);
-        put(3 * s + 1, F1, Y1);
-        apass1<R, L>(A.matT[s][2], m, j, ub[s], F1, Y1);
-        put(3 * s + 2, F1, Y1);
+        pass1q(3 * s, A.mat[s][0], A.cl[s][0], w[s]);
+        pass1q(3 * s + 1, A.matT[s][1], A.cl[s][1], ub[s]);
+        pass1q(3 * s + 2, A.matT[s][2], A.cl[s][2], ub[s]);
       }
       __syncthreads();
-      scan_solves<R>(A, sF, sY, sSig, 0, 3 * S, mat);
+      if constexpr (CIRC) circ_chains<R>(A, sF, sY, 0, 3 * S, cid);
+      else scan_solves<R>(A, sF, sY, sSig, 0, 3 * S, mat);
       __syncthreads();
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        R G, X, sg;
-        carries(3 * s, G, X, sg);
-        apass2<R, L>(A.mat[s][0], m, j, w[s], G, X, sg, Us[s]);
-        carries(3 * s + 1, G, X, sg);
-        apass2<R, L>(A.matT[s][1], m, j, ub[s], G, X, sg, a1[s]);
-        carries(3 * s + 2, G, X, sg);
-        apass2<R, L>(A.matT[s][2], m, j, ub[s], G, X, sg, a2[s]);
+        pass2q(3 * s, A.mat[s][0], A.cl[s][0], w[s], Us[s]);
+        pass2q(3 * s + 1, A.matT[s][1], A.cl[s][1], ub[s], a1[s]);
+        pass2q(3 * s + 2, A.matT[s][2], A.cl[s][2], ub[s], a2[s]);
 #pragma unroll
         for (int t = 0; t < L; ++t) a2[s][t] = -a2[s][t];  // f2bar = S^T (-Ubar)
       }
@@ -330,28 +422,22 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R F0, Y0;
-      apass1<R, L>(A.mat[s][1], m, j, f1[s], F0, Y0);
-      put(3 * S + 3 * s, F0, Y0);
-      apass1<R, L>(A.mat[s][2], m, j, f2[s], F0, Y0);
-      put(3 * S + 3 * s + 1, F0, Y0);
-      apass1<R, L>(A.matT[s][0], m, j, usb[s], F0, Y0);
-      put(3 * S + 3 * s + 2, F0, Y0);
+      pass1q(3 * S + 3 * s, A.mat[s][1], A.cl[s][1], f1[s]);
+      pass1q(3 * S + 3 * s + 1, A.mat[s][2], A.cl[s][2], f2[s]);
+      pass1q(3 * S + 3 * s + 2, A.matT[s][0], A.cl[s][0], usb[s]);
     }
     __syncthreads();
-    scan_solves<R>(A, sF, sY, sSig, 3 * S, 3 * S, mat);
+    if constexpr (CIRC) circ_chains<R>(A, sF, sY, 3 * S, 3 * S, cid);
+    else scan_solves<R>(A, sF, sY, sSig, 3 * S, 3 * S, mat);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R x[L], G, X, sg;
-      carries(3 * S + 3 * s, G, X, sg);
-      apass2<R, L>(A.mat[s][1], m, j, f1[s], G, X, sg, x);
+      R x[L];
+      pass2q(3 * S + 3 * s, A.mat[s][1], A.cl[s][1], f1[s], x);
       dterm(s, a1[s], f1[s], x, R(1));
-      carries(3 * S + 3 * s + 1, G, X, sg);
-      apass2<R, L>(A.mat[s][2], m, j, f2[s], G, X, sg, x);
+      pass2q(3 * S + 3 * s + 1, A.mat[s][2], A.cl[s][2], f2[s], x);
       dterm(s, a2[s], f2[s], x, R(1));
-      carries(3 * S + 3 * s + 2, G, X, sg);
-      apass2<R, L>(A.matT[s][0], m, j, usb[s], G, X, sg, x);  // wbar
+      pass2q(3 * S + 3 * s + 2, A.matT[s][0], A.cl[s][0], usb[s], x);  // wbar
       dterm(s, x, w[s], Us[s], R(1));
       store_chunk<R, L, CONTIG>(x, A.out[2] + s * N, off0, st, cnt);
     }
@@ -367,6 +453,10 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
       if (r == 9) return A.mat[s][0];           // P
       if (r < 4) return A.matT[s][1 + (r & 1)];  // 0, 2: T^T ; 1, 3: S^T
       return A.mat[s][1 + ((r - 5) & 1)];       // 5, 7: T ; 6, 8: S
+    };
+    auto cid = [&](int q) -> int {  // species * 3 + (0: P, 1: T, 2: S) of solve q
+      const int s = q / 10, r = q - 10 * (q / 10);
+      return s * 3 + ((r == 4 || r == 9) ? 0 : (r < 4 ? 1 + (r & 1) : 1 + ((r - 5) & 1)));
     };
     R cb[S][L], fb[S][L], wb[S][L], xu[S][L], xf[S][L];
 #pragma unroll
@@ -402,64 +492,45 @@ __global__ void __launch_bounds__(ETD_MAX_THREADS) adjoint_kernel(const __grid_c
     };
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R F0, Y0, F1, Y1, xw[L];
-      apass1x2<R, L>(A.matT[s][1], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
-      put(10 * s + 0, F0, Y0);
-      put(10 * s + 2, F1, Y1);
-      apass1x2<R, L>(A.matT[s][2], m, j, cb[s], fb[s], F0, Y0, F1, Y1);
-      put(10 * s + 1, F0, Y0);
-      put(10 * s + 3, F1, Y1);
-      apass1<R, L>(A.matT[s][0], m, j, wb[s], F0, Y0);
-      put(10 * s + 4, F0, Y0);
-      apass1x2<R, L>(A.mat[s][1], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
-      put(10 * s + 5, F0, Y0);
-      put(10 * s + 7, F1, Y1);
-      apass1x2<R, L>(A.mat[s][2], m, j, xu[s], xf[s], F0, Y0, F1, Y1);
-      put(10 * s + 6, F0, Y0);
-      put(10 * s + 8, F1, Y1);
+      R xw[L];
+      pass1x2q(10 * s + 0, 10 * s + 2, A.matT[s][1], A.cl[s][1], cb[s], fb[s]);
+      pass1x2q(10 * s + 1, 10 * s + 3, A.matT[s][2], A.cl[s][2], cb[s], fb[s]);
+      pass1q(10 * s + 4, A.matT[s][0], A.cl[s][0], wb[s]);
+      pass1x2q(10 * s + 5, 10 * s + 7, A.mat[s][1], A.cl[s][1], xu[s], xf[s]);
+      pass1x2q(10 * s + 6, 10 * s + 8, A.mat[s][2], A.cl[s][2], xu[s], xf[s]);
       xw_at(s, xw);
-      apass1<R, L>(A.mat[s][0], m, j, xw, F0, Y0);
-      put(10 * s + 9, F0, Y0);
+      pass1q(10 * s + 9, A.mat[s][0], A.cl[s][0], xw);
     }
     __syncthreads();
-    scan_solves<R>(A, sF, sY, sSig, 0, NQ, mat);
+    if constexpr (CIRC) circ_chains<R>(A, sF, sY, 0, NQ, cid);
+    else scan_solves<R>(A, sF, sY, sSig, 0, NQ, mat);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      R aT[L], aS[L], x[L], G, X, sg;
+      R aT[L], aS[L], x[L];
       // cbar_U: lambda_T = 9 T^T cb, lambda_S = -8 S^T cb
-      carries(10 * s + 0, G, X, sg);
-      apass2<R, L>(A.matT[s][1], m, j, cb[s], G, X, sg, aT);
-      carries(10 * s + 5, G, X, sg);
-      apass2<R, L>(A.mat[s][1], m, j, xu[s], G, X, sg, x);
+      pass2q(10 * s + 0, A.matT[s][1], A.cl[s][1], cb[s], aT);
+      pass2q(10 * s + 5, A.mat[s][1], A.cl[s][1], xu[s], x);
       dterm(s, aT, xu[s], x, R(9));
-      carries(10 * s + 1, G, X, sg);
-      apass2<R, L>(A.matT[s][2], m, j, cb[s], G, X, sg, aS);
-      carries(10 * s + 6, G, X, sg);
-      apass2<R, L>(A.mat[s][2], m, j, xu[s], G, X, sg, x);
+      pass2q(10 * s + 1, A.matT[s][2], A.cl[s][2], cb[s], aS);
+      pass2q(10 * s + 6, A.mat[s][2], A.cl[s][2], xu[s], x);
       dterm(s, aS, xu[s], x, R(-8));
 #pragma unroll
       for (int t = 0; t < L; ++t) cb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
       // cbar_f
-      carries(10 * s + 2, G, X, sg);
-      apass2<R, L>(A.matT[s][1], m, j, fb[s], G, X, sg, aT);
-      carries(10 * s + 7, G, X, sg);
-      apass2<R, L>(A.mat[s][1], m, j, xf[s], G, X, sg, x);
+      pass2q(10 * s + 2, A.matT[s][1], A.cl[s][1], fb[s], aT);
+      pass2q(10 * s + 7, A.mat[s][1], A.cl[s][1], xf[s], x);
       dterm(s, aT, xf[s], x, R(9));
-      carries(10 * s + 3, G, X, sg);
-      apass2<R, L>(A.matT[s][2], m, j, fb[s], G, X, sg, aS);
-      carries(10 * s + 8, G, X, sg);
-      apass2<R, L>(A.mat[s][2], m, j, xf[s], G, X, sg, x);
+      pass2q(10 * s + 3, A.matT[s][2], A.cl[s][2], fb[s], aS);
+      pass2q(10 * s + 8, A.mat[s][2], A.cl[s][2], xf[s], x);
       dterm(s, aS, xf[s], x, R(-8));
 #pragma unroll
       for (int t = 0; t < L; ++t) fb[s][t] = fma(R(9), aT[t], R(-8) * aS[t]);
       // wbar
       R xw[L];
       xw_at(s, xw);
-      carries(10 * s + 4, G, X, sg);
-      apass2<R, L>(A.matT[s][0], m, j, wb[s], G, X, sg, aT);
-      carries(10 * s + 9, G, X, sg);
-      apass2<R, L>(A.mat[s][0], m, j, xw, G, X, sg, x);
+      pass2q(10 * s + 4, A.matT[s][0], A.cl[s][0], wb[s], aT);
+      pass2q(10 * s + 9, A.mat[s][0], A.cl[s][0], xw, x);
       dterm(s, aT, xw, x, R(1));
 #pragma unroll
       for (int t = 0; t < L; ++t) wb[s][t] = aT[t];

@@ -5,6 +5,7 @@ namespace etd {
 
 cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s) {
+  if (a.circ_adj) return launch_adjoint_circ(a, nspecies, L, kind, nthreads, smem, s);
 #define CALL(S_, L_, K_) launch_adj_one<float, S_, L_, K_>(a, nthreads, smem, s)
   ETD_ADJ_DISPATCH(CALL)
 #undef CALL

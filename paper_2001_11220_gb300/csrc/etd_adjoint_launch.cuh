@@ -6,10 +6,10 @@
 
 namespace etd {
 
-template <typename R, int S, int L, int KIND>
+template <typename R, int S, int L, int KIND, bool CIRC = false>
 cudaError_t launch_adj_one(const SweepArgs<R> &a, int nthreads, size_t smem, cudaStream_t s) {
   constexpr bool CONTIG = (KIND == ADJ_FIRST);
-  auto fn = adjoint_kernel<R, S, L, CONTIG, KIND>;
+  auto fn = adjoint_kernel<R, S, L, CONTIG, KIND, CIRC>;
   cudaError_t e = ensure_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
   fn<<<a.nblocks, nthreads, smem, s>>>(a);

@@ -94,6 +94,10 @@ struct Instance {
   AxisPlan aplan[3];
   MatTab<float> atab32[2][3][MAX_SPECIES][3];
   MatTab<double> atab64[2][3][MAX_SPECIES][3];
+  // adjoint on the circulant factorisation (periodic axes with n a multiple of the chunk length)
+  bool acirc[3] = {false, false, false};
+  SweepArgs<float>::CircLine acl32[3][MAX_SPECIES][3];
+  SweepArgs<double>::CircLine acl64[3][MAX_SPECIES][3];
   DeviceArena arena;                               // source tables, adjoint tables
   void *axis_tables[3] = {nullptr, nullptr, nullptr};  // forward line tables of each axis (one block)
   // circulant plans: kernel arguments with every coefficient filled in (only

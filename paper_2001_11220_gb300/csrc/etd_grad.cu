@@ -12,12 +12,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/etdrdpif.h"
 #include "etd_context.h"
 #include "etd_internal.h"
 #include "etd_tables.h"
+#include "etd_circ.h"
 
 namespace etd {
 bool plan_axis(Instance &I, int a, int L, int max_threads);
@@ -115,6 +117,28 @@ etd_status prepare_adjoint(etd_ctx *ctx, Instance &I) {
         return fail(ctx, ETD_ERR_UNSUPPORTED, "adjoint: axis %d with n = %lld does not fit one block", a,
                     (long long)I.n[a]);
       const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+      // periodic axes whose lines are whole chunks run the circulant adjoint
+      // (ETD_ADJ_CIRC=0 keeps the tables)
+      const char *ac = std::getenv("ETD_ADJ_CIRC");
+      I.acirc[a] = !(ac && ac[0] == '0') && I.bc[a] == BC_PERIODIC && I.n[a] % L == 0 &&
+                   L == (I.real_bytes == 4 ? 8 : 4);
+      if (I.acirc[a])
+        for (int s = 0; s < I.S; ++s)
+          for (int g = 0; g < 3; ++g) {
+            CircHost H;
+            circ_coeffs((I.k / gammas[g]) * I.D[s] / (h * h), (int)I.n[a], L, H);
+            auto fill = [&](auto &C) {
+              using RR = std::remove_reference_t<decltype(C.lam)>;
+              C.lam = (RR)H.lam;
+              C.lamL = (RR)H.lamL;
+              C.kap = (RR)H.kap;
+              C.inv1m = (RR)H.inv1m;
+              C.ialpha = (RR)(1.0 / H.alpha);
+              for (int t = 0; t < 16; ++t) C.pw[t] = (RR)H.pw[t];
+            };
+            fill(I.acl32[a][s][g]);
+            fill(I.acl64[a][s][g]);
+          }
       cudaError_t err = cudaSuccess;
       for (int s = 0; s < I.S; ++s)
         for (int g = 0; g < 3; ++g)
@@ -246,7 +270,12 @@ cudaError_t adjoint_sweeps_t(etd_ctx *ctx, const Instance &I, const R *Un, doubl
         }
       }
       A.invD[sp] = 1.0 / I.D[sp];
+      for (int g = 0; g < 3; ++g) {
+        if constexpr (sizeof(R) == 8) A.cl[sp][g] = I.acl64[a][sp][g];
+        else A.cl[sp][g] = I.acl32[a][sp][g];
+      }
     }
+    A.circ_adj = I.acirc[a] ? 1 : 0;
     A.acc = ctx->adj_acc;
     A.part = ctx->adj_part;
     if (P.kind == ADJ_LAST) {

@@ -123,6 +123,14 @@ template <typename R> struct SweepArgs {
   double *part;                    // per-block partial sums [nblocks][MAX_SPECIES + 8], added to acc
                                    // in a fixed order by a second launch (reproducible sums)
   double invD[MAX_SPECIES];        // 1 / D_s
+  int circ_adj = 0;  // adjoint sweep on the circulant factorisation (cl below), else the tables
+  // adjoint sweeps of periodic axes on the circulant factorisation
+  // M = alpha (I - lambda E)(I - lambda E^{-1}) (M is symmetric, so M^T = M):
+  // per [species][0: P, 1: T, 2: S]
+  struct CircLine {
+    R lam, lamL, kap, inv1m, ialpha;  // lambda, lambda^L, sum_{s<L} lambda^{2s+1}, 1/(1 - lambda^p), 1/alpha
+    R pw[16];                          // lambda^t, t < L
+  } cl[MAX_SPECIES][3];
 };
 
 // Launch phases of a segmented sweep.  FIRST/MIDDLE: SEG_SUMMARY writes the
@@ -211,6 +219,11 @@ cudaError_t launch_seg_carry(const SweepArgs<double> &a, int nspecies, int kind,
 
 cudaError_t launch_adjoint(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);
+// the adjoint sweeps on the circulant factorisation (a.circ_adj; FP32 L = 8, FP64 L = 4)
+cudaError_t launch_adjoint_circ(const SweepArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                cudaStream_t s);
+cudaError_t launch_adjoint_circ(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
+                                cudaStream_t s);
 cudaError_t launch_adjoint(const SweepArgs<double> &a, int nspecies, int L, int kind, int nthreads, size_t smem,
                            cudaStream_t s);
 // part: at least loss_blocks(n) doubles of per-block partial sums

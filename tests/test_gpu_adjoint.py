@@ -47,6 +47,11 @@ STEP_CASES = [
     W.mms_3d(12).with_(name="mms3d_12"),
     case("cgl2d_per", (24, 20), W.PERIODIC, (1.0, 1.0), "cgl", (1.3,), 0.05, ((0.0, 0.0), 0.5)).with_(
         length=(12.0, 10.0)),
+    # periodic axes with whole chunks take the circulant adjoint (every axis here)
+    case("gs3d_per_circ", (16, 8, 24), W.PERIODIC, (0.02, 0.01), "gray_scott", (0.04, 0.06), 0.5,
+         ((0.8, 0.2), 0.05)),
+    case("sch2d_per_circ", (32, 40), W.PERIODIC, (0.01, 0.1), "schnakenberg", (0.1, 0.9, 10.0), 0.02,
+         ((1.0, 0.9), 0.05)),
     # 700-node periodic lines take the warp-cooperative chunk scan; h = 0.1 keeps the
     # dL/dD sum as well conditioned as the cases above (at h = 1/700, r = k D / h^2 ~ 4e5
     # and a one-ulp change of U_n moves the oracle's dL/dD by 3e-12 relative)
@@ -244,3 +249,29 @@ def test_grad_fp32_repeatable():
     ctx.close()
     assert a[0] == b[0] and torch.equal(a[1], b[1])
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_circulant_adjoint_matches_table_adjoint(prec, monkeypatch):
+    """On periodic axes with whole chunks the adjoint sweeps run on the circulant
+    factorisation; the line-table kernels (ETD_ADJ_CIRC=0) solve the same systems.
+    Both gradients of a 3D Gray-Scott run agree to rounding (FP64) or within the
+    FP32 precision."""
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    w = W.gray_scott_3d(16, steps=3).with_(k=0.5, D=(0.01, 0.005))
+    U0 = W.initial_state(w)
+    tgt = W.initial_state(w, seed=99)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("ETD_ADJ_CIRC", flag)
+        ctx = EtdRdpIf.from_workload(w, prec)
+        U = torch.tensor(U0, device="cuda", dtype=ctx.dtype)
+        T = torch.tensor(tgt, device="cuda", dtype=ctx.dtype)
+        loss, dU0, dD, dp = ctx.grad(U, 0.0, T, 3, 2)
+        out[flag] = (loss, dU0.double().cpu().numpy(), dD, dp)
+        ctx.close()
+    a, b = out["1"], out["0"]
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert abs(a[0] - b[0]) <= tol * abs(b[0])
+    assert np.max(np.abs(a[1] - b[1])) <= tol * np.max(np.abs(b[1]))
+    assert np.max(np.abs(a[2] - b[2])) <= tol * 10 * np.max(np.abs(b[2]))
