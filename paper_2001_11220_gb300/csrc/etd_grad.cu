@@ -48,7 +48,13 @@ bool plan_adjoint_axis(Instance &I, int a, int L, int nlb_force = 0) {
   P.nlines = I.N / n;
   P.pitch = exchange_pitch(P.m);
   const long long avail = (a == 0) ? P.nlines : st;
-  int nlb = pow2_floor_i(std::min<long long>(32, ETD_MAX_BLOCK_THREADS / P.m));
+  // ETD_ADJ_THREADS=256|128 caps the block (more resident blocks per SM, same 128 registers)
+  int maxt = ETD_MAX_BLOCK_THREADS;
+  if (const char *t = std::getenv("ETD_ADJ_THREADS")) {
+    const int v = atoi(t);
+    if ((v == 128 || v == 256) && P.m <= v) maxt = v;
+  }
+  int nlb = pow2_floor_i(std::min<long long>(32, maxt / P.m));
   if (nlb_force > 0 && nlb_force <= nlb) nlb = nlb_force;
   while (nlb > 1 && nlb / 2 >= avail) nlb /= 2;
   while (nlb > 1 && adjoint_smem_bytes(P.kind, I.S, nlb, P.pitch, I.real_bytes) > 200 * 1024) nlb /= 2;
