@@ -413,6 +413,16 @@ bool plan_axis_circ_strided(Instance &I, int a, int L, int wb, int nc) {
   const long long ngroups = (long long)P.nlo_blocks * (I.N / (st * n));
   if (ngroups > INT_MAX / 2) return false;
   P.smem = circ_strided_smem(I.S, L, wb, nc, I.real_bytes);
+  // lean: the exchange tables stay in global memory when that is what lets a
+  // second block share the SM (228 KB per SM, 1 KB reserved per block);
+  // ETD_CIRC_LEAN=0 / 1 forbids / forces it
+  {
+    const size_t lean = circ_strided_smem(I.S, L, wb, nc, I.real_bytes, true);
+    const size_t per_sm = 228 * 1024, blk = CIRC_STRIDED_STATIC_SMEM + 1024;
+    const char *lv = std::getenv("ETD_CIRC_LEAN");
+    P.circ_lean = lv ? (lv[0] == '1') : (2 * (P.smem + blk) > per_sm && 2 * (lean + blk) <= per_sm);
+    if (P.circ_lean) P.smem = lean;
+  }
   if (P.smem + CIRC_STRIDED_STATIC_SMEM > 227 * 1024) return false;
   // persistent launch: as many clusters (cs > 1) or blocks as the device holds
   // at once, each walking the line groups
@@ -603,7 +613,11 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
         per = std::max(per, H[s][g].lpow.size() + H[s][g].kch.size());
       }
     const size_t rb = I.real_bytes;
-    std::vector<unsigned char> img((size_t)I.S * 3 * per * rb, 0);
+    // lean strided plans: the exchange tables follow the power tables
+    const int WBt = P.mx, TSt = 2 * (WBt + 1) + 35;
+    const size_t tab_off = (size_t)I.S * 3 * per * rb;
+    const size_t tab_n = (P.circ_lean && a > 0) ? (size_t)circ_tab_entries(I.S, WBt) : 0;
+    std::vector<unsigned char> img(tab_off + tab_n * rb, 0);
     for (int s = 0; s < I.S; ++s)
       for (int g = 0; g < 3; ++g)
         for (size_t i = 0; i < H[s][g].lpow.size() + H[s][g].kch.size(); ++i) {
@@ -616,6 +630,26 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
             memcpy(d, &v, 4);
           }
         }
+    for (size_t e = 0; e < tab_n; ++e) {  // the kernel's shared-memory table layout, per matrix
+      const int mxi = (int)(e / TSt), o = (int)(e % TSt);
+      const CircHost &Hm = H[mxi / 3][mxi % 3];
+      double v;
+      if (o <= WBt) v = Hm.kch[o];
+      else if (o <= 2 * WBt + 1) v = Hm.lpow[o - (WBt + 1)];
+      else if (o < 2 * WBt + 2 + 17) {
+        const int b = o - (2 * WBt + 2);
+        v = b * WBt <= P.m ? Hm.kch[b * WBt] : 0.0;
+      } else if (o < 2 * WBt + 2 + 34) {
+        const int b = o - (2 * WBt + 2 + 17);
+        v = b * WBt <= P.m ? Hm.lpow[b * WBt] : 0.0;
+      } else v = Hm.kch[P.m];
+      unsigned char *d = img.data() + tab_off + e * rb;
+      if (rb == 8) memcpy(d, &v, 8);
+      else {
+        const float f = (float)v;
+        memcpy(d, &f, 4);
+      }
+    }
     err = cudaMalloc(&I.circ_tables[a], img.size());
     if (err != cudaSuccess) return cuda_fail(ctx, err, "circulant power tables");
     err = cudaMemcpy(I.circ_tables[a], img.data(), img.size(), cudaMemcpyHostToDevice);
@@ -652,6 +686,7 @@ etd_status build_axis_tables(etd_ctx *ctx, Instance &I, int a) {
           C.kch[s][g] = C.lpow[s][g] + H[s][g].lpow.size();
         }
       }
+      C.tabg = tab_n ? (const R *)((unsigned char *)I.circ_tables[a] + tab_off) : nullptr;
     };
     if (rb == 8) fill(I.circ64[a], 0.0);
     else fill(I.circ32[a], 0.0f);

@@ -881,7 +881,10 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   R *car = buf1 + EX;                          // [2][2S][NC]
   constexpr int TS = 2 * (WB + 1) + 35;
   R *tab = car + (size_t)2 * 2 * S * NC;       // [S * 3 matrices][TS]: the exchange's coefficient tables
-  for (int e = tid; e < S * 3 * TS; e += WB * NC) {
+  // A.tabg: the same tables prepared in global memory (blocks lean enough for
+  // two per SM read them through L1 and have no shared copy)
+  const R *tabp = A.tabg ? A.tabg : tab;
+  for (int e = tid; !A.tabg && e < S * 3 * TS; e += WB * NC) {
     const int mx = e / TS, o = e - mx * TS;
     const R *kch = A.kch[mx / 3][mx % 3], *lpw = A.lpow[mx / 3][mx % 3];
     R v;
@@ -933,11 +936,11 @@ __global__ void __launch_bounds__(WB * NC) circ_strided_kernel(const __grid_cons
   auto exchange = [&](auto mi, const auto &F, const auto &W, auto &Yc, auto &Zc, int blk_slot) {
     constexpr int NG = sizeof(F) / sizeof(R);
     if (cs > 1)
-      strided_exchange_push<R, WB, NC, NG>(A, mi, F, W, Yc, Zc, buf0, buf1, xbar, xc, ng_of(xc + 2), car, tab, j, c,
+      strided_exchange_push<R, WB, NC, NG>(A, mi, F, W, Yc, Zc, buf0, buf1, xbar, xc, ng_of(xc + 2), car, tabp, j, c,
                                            w, h, rank, tid, &wait_fail);
     else
       strided_exchange<R, WB, NC, NG>(A, mi, F, W, Yc, Zc, buf0, buf0 + EX / 2,
-                                      buf1 + (size_t)blk_slot * 2 * 2 * S * NC, car, tab, j, c, w, h, rank);
+                                      buf1 + (size_t)blk_slot * 2 * 2 * S * NC, car, tabp, j, c, w, h, rank);
     ++xc;
   };
   // stage field fld of group g into its buffer (TMA, or cp.async with 16-byte

@@ -74,6 +74,7 @@ template <typename R> struct CircArgs {
   CircMat<R> mat[MAX_SPECIES][3];                        // [species][0: P, 1: T, 2: S]
   const R *lpow[MAX_SPECIES][3];                         // Lambda^i, i = 0 .. m + 32 (device)
   const R *kch[MAX_SPECIES][3];                          // K_{nL} = sum_{s<nL} lambda^{2s+1}, n = 0 .. m
+  const R *tabg;      // strided sweeps: the exchange tables in global memory, or NULL (a shared copy)
 };
 
 // host-side coefficients of one matrix (FP64)
@@ -144,13 +145,15 @@ cudaError_t launch_circ(const CircArgs<double> &a, int nspecies, int L, int kind
 // holds the 3 input fields of every species for the block's WB L rows, then
 // two exchange buffers of up to 2 s solves (receive / compose, alternating),
 // the block carries and the exchange coefficient tables
-inline size_t circ_strided_smem(int nspecies, int L, int WB, int NC, size_t real_bytes) {
+inline size_t circ_strided_smem(int nspecies, int L, int WB, int NC, size_t real_bytes, bool lean = false) {
   const size_t tile = (size_t)3 * nspecies * WB * L * NC * real_bytes;
   const size_t exch = (size_t)2 * 2 * nspecies * (WB > 16 ? WB : 16) * NC * real_bytes;
   const size_t car = (size_t)2 * 2 * nspecies * NC * real_bytes;
-  const size_t tab = (size_t)nspecies * 3 * (2 * (WB + 1) + 35) * real_bytes;
+  const size_t tab = lean ? 0 : (size_t)nspecies * 3 * (2 * (WB + 1) + 35) * real_bytes;
   return tile + 2 * exch + car + tab;
 }
+// the exchange tables of one strided plan: [nspecies * 3][2 (WB + 1) + 35]
+inline int circ_tab_entries(int nspecies, int WB) { return nspecies * 3 * (2 * (WB + 1) + 35); }
 // static shared memory of the strided kernels (mbarriers)
 constexpr size_t CIRC_STRIDED_STATIC_SMEM = 128;
 cudaError_t circ_cluster_capacity(const CircArgs<float> &a, int nspecies, int L, int kind, int nthreads, size_t smem,

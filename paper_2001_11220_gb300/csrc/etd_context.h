@@ -68,6 +68,7 @@ struct AxisPlan {
   size_t seg_bytes = 0;
   StagePlan sp{};      // staged (persistent) kernel plan; sp.staged = 0 -> register kernel
   bool circ = false;   // periodic axis solved by the circulant kernels (etd_circ.cuh); nlb = lines per block
+  bool circ_lean = false;  // strided circulant plan with its exchange tables in global memory (2 blocks per SM)
 };
 
 // one problem: grid, coefficients, tables, plans and scratch
