@@ -321,10 +321,15 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
     ubar = torch.ones_like(U)
     msa = _timed(lambda: c.step_adjoint(U, 0.0, ubar), stream, reps=5)
     adj_fields = 4 + 6 + rev_fields
+    # the full gradient run of the adjoint configuration: 200 steps, checkpoint every 20 (every
+    # segment but the last is recomputed: 14 more fields per step for 9 of the 10 segments)
+    ms200 = _timed(lambda: c.grad(U, 0.0, tg, 200, 20), stream)
     out[f"grayscott3d_{P_3D}_fp32"] = {
         "fwd": units / (msf / 1e3), "fwd_adjoint": units / (msg / 1e3), "unit": UNIT,
         "fwd_ms_per_step": msf / 20, "fwd_adjoint_ms_per_step": msg / 20, "tiles": tiles,
         "fwd_adjoint_over_fwd": msg / msf,
+        "grad_200_steps_ckpt20_ms_per_step": ms200 / 200,
+        "grad_200_steps_ckpt20_over_fwd": (ms200 / 200) / (msf / 20),
         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "per_sweep": per,
                      "fwd_step_frac": alg / (msf / 20 / 1e3) / 1e9 / peak,
                      "fwd_adjoint_algorithmic_bytes_per_step": alg + rev_fields * fb,

@@ -962,8 +962,23 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
         ok = plan_axis_circ(I, a, Lc, 8, 32) || plan_axis_circ(I, a, Lc, 16, 16);
       if (ok) continue;
     }
-    while (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS) && L < 16) L *= 2;
-    if (!plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
+    // small problems (a few blocks per sweep) take the register kernel: the
+    // staged kernel's prefetch pipeline only pays with many tiles per block
+    // (64^2 two-species FP64: 35 against 62 us per step),
+    // with few lines per block, so that the sweep spreads over the SMs
+    const bool small = (long long)I.N * I.S <= (1LL << 17);
+    int nlb_small = 0;
+    if (small) {
+      long long st = 1;
+      for (int b = 0; b < a; ++b) st *= I.n[b];
+      const long long avail = a == 0 ? I.N / I.n[0] : st;
+      nlb_small = 1;
+      while ((long long)nlb_small * 2 * 152 <= avail) nlb_small *= 2;
+    }
+    // short chunks on short lines (64^2 FP64: 35 us per step at L = 4, 53 at 8)
+    if (small && I.n[a] >= 32 && I.n[a] <= 256) L = I.real_bytes == 4 ? 8 : 4;
+    while (!plan_axis_ex(I, a, L, ETD_MAX_BLOCK_THREADS, nlb_small, small, 1) && L < 16) L *= 2;
+    if (!plan_axis_ex(I, a, L, ETD_MAX_BLOCK_THREADS, nlb_small, small, 1) && !plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
       return fail(ctx, ETD_ERR_UNSUPPORTED, "axis %d with n = %lld does not fit one block", a, (long long)I.n[a]);
   }
   etd_status st = build_instance_tables(ctx, I);

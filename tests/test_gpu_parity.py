@@ -537,3 +537,19 @@ def test_cgl_2d_paper_pulses_fp64_and_fp32():
     e32 = rel_err(g32, ref)
     print(f"cgl2d_64 40 steps: FP64 {rel_err(g64, ref):.2e}, FP32 {e32:.2e} vs oracle")
     assert e32 <= w.steps * fp32_step_bound(w) * math.exp(w.steps * w.k)
+
+
+@pytest.mark.parametrize("w", [c for c in ONE_STEP_CASES if c.name in ("bru2d_neu_64", "bru2d_neu_ragged", "gs2d_mixed",
+                                                                       "gs3d_mixed", "bru3d_per", "cgl2d_per")],
+                         ids=lambda w: w.name)
+def test_staged_kernels_forced_fp64_matches_oracle(w, monkeypatch):
+    """The staged (persistent, cp.async double-buffered) table kernels, which small
+    problems no longer take by default, forced on every axis (ETD_TILES kernel code 1)."""
+    monkeypatch.setenv("ETD_TILES", ",".join(["4:0:1:1"] * len(w.n)))
+    U0 = W.initial_state(w)
+    ctx = _api().from_workload(w, "fp64")
+    staged = ctx.info()["staged"][:len(w.n)]
+    ctx.close()
+    assert any(k == 1 for k in staged), staged
+    got = gpu_run(w, U0, 1, "fp64")
+    assert rel_err(got, oracle_run(w, U0, 1)) <= FP64_TOL
