@@ -54,10 +54,20 @@ __device__ __forceinline__ bool ens_wait(const int *ctr, int need, int *status, 
 // kernel; ptxas 13.0 fails on a non-inlined function shared by two kernels)
 // (the dynamic shared memory is named here, not passed in, so that its
 // accesses stay shared-memory instructions rather than generic ones)
+// The item's arguments are copied to shared memory first: the sweep reads
+// dozens of their fields (table pointers, coefficients), which would otherwise
+// be global loads on the critical path.
 template <typename R, int S, int L, bool CONTIG, int KIND, int TAG>
 __device__ __noinline__ void ens_sweep(const SweepArgs<R> *A, int b, double t_eval, R exp_mt) {
   extern __shared__ __align__(16) unsigned char ens_smem[];
-  sweep_block<R, S, L, CONTIG, KIND, 1, false, true>(*A, b, ens_smem, t_eval, exp_mt);
+  static_assert(sizeof(SweepArgs<R>) % 8 == 0, "arguments copied in 8-byte pieces");
+  __shared__ __align__(16) int2 s_args[sizeof(SweepArgs<R>) / 8];
+  const int2 *src = reinterpret_cast<const int2 *>(A);
+  for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs<R>) / 8); i += blockDim.x) s_args[i] = src[i];
+  __syncthreads();
+  sweep_block<R, S, L, CONTIG, KIND, 1, false, true>(*reinterpret_cast<const SweepArgs<R> *>(s_args), b, ens_smem,
+                                                     t_eval, exp_mt);
+  __syncthreads();  // every thread is done with the arguments before the next item's copy
 }
 
 // one work item of axis a with chunk lengths L0 (axis 0) and LS (axes 1, 2)
