@@ -181,9 +181,14 @@ etd_status etd_run_vjp(etd_ctx *ctx, const void *U0, double t0, int64_t nsteps, 
  * (axis, instance, line block) work items from a device queue ordered so
  * that every item's dependencies -- all blocks of the previous sweep of the
  * same instance -- come earlier, and wait for them on per-instance
- * completion counters with a bounded wait.  Multi-step runs are captured
- * into a CUDA graph and replayed.  (ETD_ENSEMBLE_PERSISTENT=0 in the
- * environment at create time selects one launch per sweep kind instead.)
+ * completion counters with a bounded wait.  Periodic axes whose lines are
+ * whole chunks are solved on the circulant factorisation of each line
+ * system (no tables read); other axes use the line tables.  Multi-step runs
+ * are captured into a CUDA graph and replayed.  (In the environment at
+ * create time, ETD_ENSEMBLE_PERSISTENT=0 selects one launch per sweep kind
+ * instead, with tables on every axis; ETD_ENSEMBLE_CIRC=0 keeps the tables
+ * in the persistent step too, which then gives the same bits as the
+ * per-sweep launches.)
  * etd_batch_run takes an array of ninst device state pointers (host array),
  * synchronises the context's stream and returns ETD_ERR_TIMEOUT if a
  * dependency wait gave up (the states are then incomplete; the counters are

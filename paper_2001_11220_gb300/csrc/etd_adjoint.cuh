@@ -155,72 +155,6 @@ __device__ __forceinline__ void scan_solves(const SweepArgs<R> &A, R *sF, R *sY,
   }
 }
 
-// ---- circulant line solves of periodic axes (symmetric M: M^T = M), the
-// factorisation of the forward circulant sweeps: pass 1 gives the chunk's
-// zero-carry summaries F (forward value at its end) and W = sum_t lambda^t ytilde_t;
-// one thread per (line, solve) chains the m chunks of its line (cyclic
-// closures by 1/(1 - lambda^p)) and leaves the carries Yc_j (y before chunk j)
-// and Zc_j (z after it) in place of F_j, W_j; pass 2 runs both recurrences.
-template <typename R, int L>
-__device__ __forceinline__ void cpass1(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R &F, R &Wv) {
-  R y = R(0), w = R(0);
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    y = fma(M.lam, y, b[t]);
-    w = fma(M.pw[t], y, w);
-  }
-  F = y;
-  Wv = w;
-}
-template <typename R, int L>
-__device__ __forceinline__ void cpass2(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R Yc, R Zc,
-                                       R (&x)[L]) {
-  R y = Yc;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    y = fma(M.lam, y, b[t]);
-    x[t] = y;
-  }
-  R z = Zc;
-#pragma unroll
-  for (int t = L - 1; t >= 0; --t) {
-    z = fma(M.lam, z, x[t]);
-    x[t] = z * M.ialpha;
-  }
-}
-template <typename R, typename CIdx>
-__device__ __forceinline__ void circ_chains(const SweepArgs<R> &A, R *sF, R *sY, int q0, int nq, CIdx cidx) {
-  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
-  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
-    const int l = u % nlb;
-    const int q = q0 + u / nlb;
-    const int ci = cidx(q);
-    const typename SweepArgs<R>::CircLine &M = A.cl[ci / 3][ci % 3];
-    R *F = sF + (q * nlb + l) * pitch;
-    R *Y = sY + (q * nlb + l) * pitch;
-    R t = R(0);
-    for (int j = 0; j < m; ++j) t = fma(M.lamL, t, F[j]);
-    R y = t * M.inv1m;  // y entering chunk 0 (cyclic)
-    for (int j = 0; j < m; ++j) {
-      const R f = F[j];
-      F[j] = y;
-      y = fma(M.lamL, y, f);
-    }
-    R g = R(0);
-    for (int j = m - 1; j >= 0; --j) {
-      const R gj = fma(M.kap, F[j], Y[j]);  // backward value at the chunk start with its forward carry
-      Y[j] = gj;
-      g = fma(M.lamL, g, gj);
-    }
-    R z = g * M.inv1m;  // z after the last chunk (cyclic)
-    for (int j = m - 1; j >= 0; --j) {
-      const R gj = Y[j];
-      Y[j] = z;
-      z = fma(M.lamL, z, gj);
-    }
-  }
-}
-
 // block-wide sum of NV per-thread values, written to this block's slot
 // part[blockIdx.x * NV + i] (reduce_partials adds the slots to the
 // accumulators in a fixed order, so repeated runs give identical sums)

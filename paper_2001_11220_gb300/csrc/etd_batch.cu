@@ -16,6 +16,8 @@
 #include "../../include/etdrdpif.h"
 #include "etd_context.h"
 #include "etd_internal.h"
+#include "etd_circ.h"
+#include "etd_tables.h"
 
 namespace etd {
 etd_status validate_problem(const etd_grid *grid, const double *D, const etd_reaction *rx, double k,
@@ -40,6 +42,27 @@ etd_status upload_batch_args(etd_ctx *ctx, void *const *U) {
       const Instance &I = ctx->inst[i];
       SweepArgs<R> &A = args[i];
       fill_args<R>(I, a, 0, A);
+      // persistent step: periodic lines of whole chunks on the circulant
+      // factorisation (ETD_ENSEMBLE_CIRC=0 keeps the tables)
+      const AxisPlan &P = I.plan[a];
+      if (ctx->ens_on && ctx->ens_circ && I.bc[a] == BC_PERIODIC && P.nseg == 1 && P.pk == 1 &&
+          I.n[a] % P.L == 0) {
+        static const double gammas[3] = {1.0, 3.0, 4.0};
+        const double h = grid_h(I.bc[a], I.n[a], I.length[a]);
+        for (int s = 0; s < I.S; ++s)
+          for (int g = 0; g < 3; ++g) {
+            CircHost H;
+            circ_coeffs((I.k / gammas[g]) * I.D[s] / (h * h), (int)I.n[a], P.L, H);
+            auto &C = A.cl[s][g];
+            C.lam = (R)H.lam;
+            C.lamL = (R)H.lamL;
+            C.kap = (R)H.kap;
+            C.inv1m = (R)H.inv1m;
+            C.ialpha = (R)(1.0 / H.alpha);
+            for (int t = 0; t < 16; ++t) C.pw[t] = (R)H.pw[t];
+          }
+        A.circ_fwd = 1;
+      }
       R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
       const int kind = I.plan[a].kind;
       if (kind == SWEEP_FIRST) {
@@ -254,6 +277,8 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
   // one persistent launch per step unless ETD_ENSEMBLE_PERSISTENT=0 (one launch per sweep kind)
   const char *pe = std::getenv("ETD_ENSEMBLE_PERSISTENT");
   ctx->ens_on = !(pe && pe[0] == '0');
+  const char *ec = std::getenv("ETD_ENSEMBLE_CIRC");
+  ctx->ens_circ = !(ec && ec[0] == '0');
   if (const char *w = std::getenv("ETD_ENSEMBLE_WINDOW_MB")) ctx->ens_window_mb = std::max(0.0, atof(w));
   if (const char *t = std::getenv("ETD_ENSEMBLE_THREADS")) {
     const int v = atoi(t);

@@ -145,6 +145,7 @@ struct etd_ctx {
   void *batch_scratch = nullptr;     // scratch of every instance, one allocation
   // persistent ensemble step (one launch per step): work list, counters, status
   bool ens_on = false;               // else one launch per sweep kind
+  bool ens_circ = true;              // periodic whole-chunk lines on the circulant factorisation
   int2 *ens_items = nullptr;         // (axis << 24 | instance, block), dependencies first
   int ens_nitems = 0;
   unsigned *ens_queue = nullptr;     // [2], reset by each launch's last block

@@ -57,7 +57,7 @@ __device__ __forceinline__ bool ens_wait(const int *ctr, int need, int *status, 
 // The item's arguments are copied to shared memory first: the sweep reads
 // dozens of their fields (table pointers, coefficients), which would otherwise
 // be global loads on the critical path.
-template <typename R, int S, int L, bool CONTIG, int KIND, int TAG>
+template <typename R, int S, int L, bool CONTIG, int KIND, int TAG, bool CIRCF>
 __device__ __noinline__ void ens_sweep(const SweepArgs<R> *A, int b, double t_eval, R exp_mt) {
   extern __shared__ __align__(16) unsigned char ens_smem[];
   static_assert(sizeof(SweepArgs<R>) % 8 == 0, "arguments copied in 8-byte pieces");
@@ -65,8 +65,8 @@ __device__ __noinline__ void ens_sweep(const SweepArgs<R> *A, int b, double t_ev
   const int2 *src = reinterpret_cast<const int2 *>(A);
   for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs<R>) / 8); i += blockDim.x) s_args[i] = src[i];
   __syncthreads();
-  sweep_block<R, S, L, CONTIG, KIND, 1, false, true>(*reinterpret_cast<const SweepArgs<R> *>(s_args), b, ens_smem,
-                                                     t_eval, exp_mt);
+  sweep_block<R, S, L, CONTIG, KIND, 1, false, true, CIRCF>(*reinterpret_cast<const SweepArgs<R> *>(s_args), b,
+                                                            ens_smem, t_eval, exp_mt);
   __syncthreads();  // every thread is done with the arguments before the next item's copy
 }
 
@@ -74,12 +74,18 @@ __device__ __noinline__ void ens_sweep(const SweepArgs<R> *A, int b, double t_ev
 template <typename R, int S, int L0, int LS, int DIM>
 __device__ __forceinline__ void ens_item(const EnsArgs<R> &E, int a, int inst, int b) {
   constexpr int TAG = L0 * 100 + LS;
-  if (a == 0)
-    ens_sweep<R, S, L0, true, SWEEP_FIRST, TAG>(E.args[0] + inst, b, E.t_eval[0], E.exp_mt[0]);
-  else if (DIM == 3 && a == 1)
-    ens_sweep<R, S, LS, false, SWEEP_MIDDLE, TAG>(E.args[1] + inst, b, E.t_eval[1], E.exp_mt[1]);
-  else
-    ens_sweep<R, S, LS, false, SWEEP_LAST, TAG>(E.args[DIM - 1] + inst, b, E.t_eval[DIM - 1], E.exp_mt[DIM - 1]);
+  const SweepArgs<R> *A = E.args[a] + inst;
+  const bool circ = A->circ_fwd != 0;  // periodic whole-chunk lines: circulant sweep
+  if (a == 0) {
+    if (circ) ens_sweep<R, S, L0, true, SWEEP_FIRST, TAG, true>(A, b, E.t_eval[0], E.exp_mt[0]);
+    else ens_sweep<R, S, L0, true, SWEEP_FIRST, TAG, false>(A, b, E.t_eval[0], E.exp_mt[0]);
+  } else if (DIM == 3 && a == 1) {
+    if (circ) ens_sweep<R, S, LS, false, SWEEP_MIDDLE, TAG, true>(A, b, E.t_eval[1], E.exp_mt[1]);
+    else ens_sweep<R, S, LS, false, SWEEP_MIDDLE, TAG, false>(A, b, E.t_eval[1], E.exp_mt[1]);
+  } else {
+    if (circ) ens_sweep<R, S, LS, false, SWEEP_LAST, TAG, true>(A, b, E.t_eval[DIM - 1], E.exp_mt[DIM - 1]);
+    else ens_sweep<R, S, LS, false, SWEEP_LAST, TAG, false>(A, b, E.t_eval[DIM - 1], E.exp_mt[DIM - 1]);
+  }
 }
 
 template <typename R, int S, int L0, int LS, int DIM>

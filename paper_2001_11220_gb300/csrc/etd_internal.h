@@ -124,6 +124,7 @@ template <typename R> struct SweepArgs {
                                    // in a fixed order by a second launch (reproducible sums)
   double invD[MAX_SPECIES];        // 1 / D_s
   int circ_adj = 0;  // adjoint sweep on the circulant factorisation (cl below), else the tables
+  int circ_fwd = 0;  // ensemble sweep of periodic whole-chunk lines on the circulant factorisation (cl)
   // adjoint sweeps of periodic axes on the circulant factorisation
   // M = alpha (I - lambda E)(I - lambda E^{-1}) (M is symmetric, so M^T = M):
   // per [species][0: P, 1: T, 2: S]

@@ -1536,6 +1536,219 @@ __device__ __forceinline__ void chunk_sweep(const SweepArgs<R> &A, const ChunkPo
   }
 }
 
+// ---- circulant line solves of periodic axes (symmetric M: M^T = M), the
+// factorisation of the forward circulant sweeps: pass 1 gives the chunk's
+// zero-carry summaries F (forward value at its end) and W = sum_t lambda^t ytilde_t;
+// one thread per (line, solve) chains the m chunks of its line (cyclic
+// closures by 1/(1 - lambda^p)) and leaves the carries Yc_j (y before chunk j)
+// and Zc_j (z after it) in place of F_j, W_j; pass 2 runs both recurrences.
+template <typename R, int L>
+__device__ __forceinline__ void cpass1(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R &F, R &Wv) {
+  R y = R(0), w = R(0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    y = fma(M.lam, y, b[t]);
+    w = fma(M.pw[t], y, w);
+  }
+  F = y;
+  Wv = w;
+}
+template <typename R, int L>
+__device__ __forceinline__ void cpass2(const typename SweepArgs<R>::CircLine &M, const R (&b)[L], R Yc, R Zc,
+                                       R (&x)[L]) {
+  R y = Yc;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    y = fma(M.lam, y, b[t]);
+    x[t] = y;
+  }
+  R z = Zc;
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    z = fma(M.lam, z, x[t]);
+    x[t] = z * M.ialpha;
+  }
+}
+template <typename R, typename CIdx>
+__device__ __forceinline__ void circ_chains(const SweepArgs<R> &A, R *sF, R *sY, int q0, int nq, CIdx cidx) {
+  const int m = A.m, nlb = A.nlb, pitch = A.pitch;
+  for (int u = threadIdx.x; u < nlb * nq; u += blockDim.x) {
+    const int l = u % nlb;
+    const int q = q0 + u / nlb;
+    const int ci = cidx(q);
+    const typename SweepArgs<R>::CircLine &M = A.cl[ci / 3][ci % 3];
+    R *F = sF + (q * nlb + l) * pitch;
+    R *Y = sY + (q * nlb + l) * pitch;
+    R t = R(0);
+    for (int j = 0; j < m; ++j) t = fma(M.lamL, t, F[j]);
+    R y = t * M.inv1m;  // y entering chunk 0 (cyclic)
+    for (int j = 0; j < m; ++j) {
+      const R f = F[j];
+      F[j] = y;
+      y = fma(M.lamL, y, f);
+    }
+    R g = R(0);
+    for (int j = m - 1; j >= 0; --j) {
+      const R gj = fma(M.kap, F[j], Y[j]);  // backward value at the chunk start with its forward carry
+      Y[j] = gj;
+      g = fma(M.lamL, g, gj);
+    }
+    R z = g * M.inv1m;  // z after the last chunk (cyclic)
+    for (int j = m - 1; j >= 0; --j) {
+      const R gj = Y[j];
+      Y[j] = z;
+      z = fma(M.lamL, z, gj);
+    }
+  }
+}
+
+// Whole-line sweep of a periodic axis on the circulant factorisation (the
+// ensemble's periodic instances; lines of whole chunks): the same solves and
+// combinations as chunk_sweep, with constant-coefficient passes and the line
+// chains of circ_chains instead of the line tables.
+template <typename R, int S, int L, int KIND, typename LoadF, typename StoreF>
+__device__ __forceinline__ void circ_chunk_sweep(const SweepArgs<R> &A, const ChunkPos<R, 1> &c, unsigned char *exch,
+                                                 LoadF load, StoreF store) {
+  using CL_ = typename SweepArgs<R>::CircLine;
+  constexpr int NQ = (KIND == SWEEP_LAST) ? 3 * S : 5 * S;
+  const int nlb = A.nlb, pitch = A.pitch;
+  const int myidx = c.l * pitch + c.j, qstride = nlb * pitch;
+  R *sF = reinterpret_cast<R *>(exch);
+  R *sY = sF + NQ * nlb * pitch;
+  auto p1 = [&](int q, const CL_ &M, const R (&b)[L]) {
+    R F, W;
+    cpass1<R, L>(M, b, F, W);
+    if (c.thr_ok) {
+      sF[q * qstride + myidx] = F;
+      sY[q * qstride + myidx] = W;
+    }
+  };
+  auto p2 = [&](int q, const CL_ &M, const R (&b)[L], R (&x)[L]) {
+    cpass2<R, L>(M, b, sF[q * qstride + myidx], sY[q * qstride + myidx], x);
+  };
+  auto react = [&](const R (&u)[S], R (&f)[S], R src) { reaction_point<R, S>(A, u, f, src); };
+  R src[L];
+  chunk_sources<R, L, 1>(A, c.qbase, c.i0, c.cnt, src);
+  if constexpr (KIND == SWEEP_FIRST || KIND == SWEEP_MIDDLE) {
+    // q = 5s + {0: T c_U, 1: S c_U, 2: T c_f, 3: S c_f, 4: P w}
+    auto cid = [](int q) { const int r = q % 5; return (q / 5) * 3 + (r == 4 ? 0 : 1 + (r & 1)); };
+    R cu[S][L], cf[S][L], w[KIND == SWEEP_MIDDLE ? S : 1][L];
+    const R k = A.kR;
+    if constexpr (KIND == SWEEP_FIRST) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) load(0, s, cu[s]);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        R u[S], f[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u[s] = cu[s][t];
+        react(u, f, src[t]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) cf[s][t] = f[s];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        load(0, s, cu[s]);
+        load(1, s, cf[s]);
+        load(2, s, w[s]);
+      }
+    }
+    auto wof = [&](int s, R (&o)[L]) {  // the P right-hand side
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        if constexpr (KIND == SWEEP_MIDDLE) o[t] = w[s][t];
+        else o[t] = fma(k, cf[s][t], cu[s][t]);
+      }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      p1(5 * s + 0, A.cl[s][1], cu[s]);
+      p1(5 * s + 1, A.cl[s][2], cu[s]);
+      p1(5 * s + 2, A.cl[s][1], cf[s]);
+      p1(5 * s + 3, A.cl[s][2], cf[s]);
+      R wt[L];
+      wof(s, wt);
+      p1(5 * s + 4, A.cl[s][0], wt);
+    }
+    __syncthreads();
+    circ_chains<R>(A, sF, sY, 0, NQ, cid);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R wt[L], xa[L], xb[L];
+      wof(s, wt);
+      p2(5 * s + 4, A.cl[s][0], wt, xa);
+      store(2, s, xa);
+      p2(5 * s + 0, A.cl[s][1], cu[s], xa);
+      p2(5 * s + 1, A.cl[s][2], cu[s], xb);
+#pragma unroll
+      for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
+      store(0, s, xa);
+      p2(5 * s + 2, A.cl[s][1], cf[s], xa);
+      p2(5 * s + 3, A.cl[s][2], cf[s], xb);
+#pragma unroll
+      for (int t = 0; t < L; ++t) xa[t] = fma(R(9), xa[t], R(-8) * xb[t]);
+      store(1, s, xa);
+    }
+  } else {
+    // q = s (P w), S + 2s (T f1), S + 2s + 1 (S f2)
+    auto cid = [](int q) {
+      if (q < S) return q * 3;
+      const int r = q - S;
+      return (r / 2) * 3 + 1 + (r & 1);
+    };
+    R w[S][L];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      load(2, s, w[s]);
+      p1(s, A.cl[s][0], w[s]);
+    }
+    __syncthreads();
+    circ_chains<R>(A, sF, sY, 0, S, cid);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) p2(s, A.cl[s][0], w[s], w[s]);  // U*
+    R cu[S][L], cf[S][L];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      load(0, s, cu[s]);
+      load(1, s, cf[s]);
+    }
+    const R k = A.kR;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      R u[S], f[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) u[s] = w[s][t];
+      react(u, f, src[t]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const R a = cu[s][t], b = cf[s][t];
+        cu[s][t] = fma(R(9), a, fma(R(2) * k, b, k * f[s]));
+        cf[s][t] = fma(R(8), a, fma(R(1.5) * k, b, R(0.5) * k * f[s]));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      p1(S + 2 * s, A.cl[s][1], cu[s]);
+      p1(S + 2 * s + 1, A.cl[s][2], cf[s]);
+    }
+    __syncthreads();
+    circ_chains<R>(A, sF, sY, S, 2 * S, cid);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      R xa[L], xb[L];
+      p2(S + 2 * s, A.cl[s][1], cu[s], xa);
+      p2(S + 2 * s + 1, A.cl[s][2], cf[s], xb);
+#pragma unroll
+      for (int t = 0; t < L; ++t) xa[t] = xa[t] - xb[t];
+      store(0, s, xa);
+    }
+  }
+}
+
 // line pairs: L positions of two neighbouring lines, 8-byte loads (st2 = stride in pairs)
 template <int L>
 __device__ __forceinline__ void load_pairs(float2 (&v)[L], const float2 *__restrict__ p, int st2, int cnt) {
@@ -1565,7 +1778,9 @@ __device__ __forceinline__ void store_pairs(const float2 (&v)[L], float2 *__rest
 // inputs loaded straight from global memory (vector loads on x, coalesced row
 // segments on strided axes).
 // COH: inputs may have been written earlier in the same launch (coherent loads)
-template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false, bool COH = false>
+// CIRCF: periodic whole-chunk lines on the circulant factorisation (circ_chunk_sweep)
+template <typename R, int S, int L, bool CONTIG, int KIND, int PK = 1, bool CL = false, bool COH = false,
+          bool CIRCF = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsigned char *smem, double t_eval,
                                             R exp_mt) {
   (void)t_eval;
@@ -1653,7 +1868,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs<R> &A, int bid, unsi
     auto store = [&](int f, int s, const R (&v)[L]) {
       store_chunk<R, L, CONTIG>(v, A.out[f] + s * N, off0, st, cnt);
     };
-    chunk_sweep<R, S, L, KIND, 1, CL>(A, c, smem, load, store);
+    if constexpr (CIRCF) circ_chunk_sweep<R, S, L, KIND>(A, c, smem, load, store);
+    else chunk_sweep<R, S, L, KIND, 1, CL>(A, c, smem, load, store);
   }
 }
 

@@ -129,16 +129,19 @@ def _run_ensemble(ws, prec, nsteps, env=None, t0=0.0):
 @pytest.mark.parametrize("dim", [2, 3])
 def test_persistent_step_is_one_launch_and_equals_per_sweep_launches(dim, prec):
     """The persistent step (one launch per step, work queue, completion counters)
-    gives the same states, bit for bit, as one launch per sweep kind, in either
-    work-list order (axis by axis, or instance groups interleaved), and matches
-    the oracle instance by instance."""
+    with the line tables on every instance gives the same states, bit for bit, as
+    one launch per sweep kind; either work-list order (axis by axis, or instance
+    groups interleaved) gives the same states; and the default persistent step,
+    which solves periodic whole-chunk lines on the circulant factorisation,
+    matches the oracle instance by instance."""
     ws = small_ensemble(10, seed=12) if dim == 2 else small_ensemble_3d()
     one, info1 = _run_ensemble(ws, prec, 3)
+    tables, _ = _run_ensemble(ws, prec, 3, {"ETD_ENSEMBLE_CIRC": "0"})
     per_sweep, info2 = _run_ensemble(ws, prec, 3, {"ETD_ENSEMBLE_PERSISTENT": "0"})
     grouped, _ = _run_ensemble(ws, prec, 3, {"ETD_ENSEMBLE_WINDOW_MB": "0.001"})
     assert info1["launches_per_step"] == 1 and info2["launches_per_step"] == dim
-    for w, a, b, c in zip(ws, one, per_sweep, grouped):
-        assert torch.equal(a, b), w.n
+    for w, a, b, c, d in zip(ws, one, per_sweep, grouped, tables):
+        assert torch.equal(d, b), w.n
         assert torch.equal(a, c), w.n
     for w, U in zip(ws, one):
         ref = oracle.run(oracle_problem(w), W.initial_state(w), 0.0, 3)
