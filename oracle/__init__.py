@@ -25,7 +25,7 @@ _HDR = os.path.join(_HERE, "etd_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 DIRICHLET, NEUMANN, PERIODIC = 0, 1, 2
-ZERO, LINEAR, BRUSSELATOR, SCHNAKENBERG, GRAY_SCOTT, ENZYME, CGL = range(7)
+ZERO, LINEAR, BRUSSELATOR, SCHNAKENBERG, GRAY_SCOTT, ENZYME, CGL, NLS = range(8)
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +57,8 @@ class _Problem(ctypes.Structure):
         ("reaction", ctypes.c_int),
         ("params", ctypes.c_double * 8),
         ("k", ctypes.c_double),
+        ("coupled", ctypes.c_int),
+        ("Dc", ctypes.c_double * 4),
     ]
 
 
@@ -66,6 +68,8 @@ class Problem:
 
     n[a] counts grid nodes on axis a in the paper's convention (Section 3,
     Example 1); axis 0 is x, the fastest index of the state U[s][z][y][x].
+    Dc (optional, 2 species): the full 2 x 2 diffusion matrix, row-major, of
+    the coupled systems of Section 8; D then only sets the species count.
     """
 
     n: tuple
@@ -75,6 +79,7 @@ class Problem:
     params: tuple = ()
     k: float = 0.01
     length: tuple = None
+    Dc: tuple = None
     dim: int = field(init=False)
 
     def __post_init__(self):
@@ -111,6 +116,9 @@ class Problem:
         for j in range(8):
             c.params[j] = float(self.params[j]) if j < len(self.params) else 0.0
         c.k = float(self.k)
+        c.coupled = 1 if self.Dc is not None else 0
+        for j in range(4):
+            c.Dc[j] = float(self.Dc[j]) if self.Dc is not None else 0.0
         return c
 
     def h(self, axis: int) -> float:

@@ -58,12 +58,19 @@ static int check_problem(const oracle_problem *P) {
     if (P->bc[a] < 0 || P->bc[a] > 2) return -1;
     if (!(P->length[a] > 0)) return -1;
   }
-  for (int s = 0; s < P->nspecies; ++s)
-    if (!(P->D[s] >= 0)) return -1;
+  if (P->coupled) {
+    if (P->nspecies != 2) return -1;
+    for (int j = 0; j < 4; ++j)
+      if (!isfinite(P->Dc[j])) return -1;
+  } else {
+    for (int s = 0; s < P->nspecies; ++s)
+      if (!(P->D[s] >= 0)) return -1;
+  }
   if ((P->reaction == OR_BRUSSELATOR || P->reaction == OR_SCHNAKENBERG ||
-       P->reaction == OR_GRAY_SCOTT || P->reaction == OR_CGL) && P->nspecies != 2) return -1;
+       P->reaction == OR_GRAY_SCOTT || P->reaction == OR_CGL || P->reaction == OR_NLS) &&
+      P->nspecies != 2) return -1;
   if (P->reaction == OR_ENZYME && P->nspecies != 1) return -1;
-  if (P->reaction < 0 || P->reaction > OR_CGL) return -1;
+  if (P->reaction < 0 || P->reaction > OR_NLS) return -1;
   return 0;
 }
 
@@ -171,6 +178,84 @@ int oracle_line_solve(int p, int bc, double r, int transpose, const double *b, d
   return 0;
 }
 
+/* ------------------------------------- coupled lines (Section 8, 2 x 2 D) -- */
+
+/* Gaussian elimination with partial pivoting, A = P L U in place (row-major
+ * m x m; piv[i] = the row swapped into position i at step i).  Returns -1 on
+ * a zero pivot. */
+static int dense_lu(int m, double *A, int *piv) {
+  for (int c = 0; c < m; ++c) {
+    int r = c;
+    for (int i = c + 1; i < m; ++i)
+      if (fabs(A[(long)i * m + c]) > fabs(A[(long)r * m + c])) r = i;
+    piv[c] = r;
+    if (A[(long)r * m + c] == 0.0) return -1;
+    if (r != c)
+      for (int j = 0; j < m; ++j) {
+        double t = A[(long)c * m + j];
+        A[(long)c * m + j] = A[(long)r * m + j];
+        A[(long)r * m + j] = t;
+      }
+    for (int i = c + 1; i < m; ++i) {
+      double l = A[(long)i * m + c] / A[(long)c * m + c];
+      A[(long)i * m + c] = l;
+      for (int j = c + 1; j < m; ++j) A[(long)i * m + j] -= l * A[(long)c * m + j];
+    }
+  }
+  return 0;
+}
+
+/* solve with the factors of dense_lu: x = A^{-1} b in place */
+static void dense_lu_solve(int m, const double *LU, const int *piv, double *x) {
+  for (int c = 0; c < m; ++c) {
+    double t = x[c];
+    x[c] = x[piv[c]];
+    x[piv[c]] = t;
+  }
+  for (int i = 1; i < m; ++i)
+    for (int j = 0; j < i; ++j) x[i] -= LU[(long)i * m + j] * x[j];
+  for (int i = m - 1; i >= 0; --i) {
+    for (int j = i + 1; j < m; ++j) x[i] -= LU[(long)i * m + j] * x[j];
+    x[i] /= LU[(long)i * m + i];
+  }
+}
+
+/* The 2p x 2p matrix of one coupled line, unknowns ordered (node i, species s)
+ * -> 2 i + s: I + rr (B (x) Dc) with B = h^2 B_p of Example 1 (read off
+ * line_matrix at r = 1 minus the identity) and rr = (k/gamma)/h^2
+ * (transpose != 0: its transpose).  A is m x m, m = 2p, row-major. */
+static void coupled_line_matrix(const oracle_problem *P, int p, int bc, double rr, int transpose, double *A) {
+  double *lo = (double *)malloc(sizeof(double) * p);
+  double *di = (double *)malloc(sizeof(double) * p);
+  double *up = (double *)malloc(sizeof(double) * p);
+  double tr, bl;
+  line_matrix(p, bc, 1.0, 0, lo, di, up, &tr, &bl);
+  const long m = 2L * p;
+  memset(A, 0, sizeof(double) * m * m);
+  for (int i = 0; i < p; ++i) {
+    for (int j = 0; j < p; ++j) {
+      double b = 0.0;
+      if (j == i) b = di[i] - 1.0;
+      else if (j == i - 1) b = lo[i];
+      else if (j == i + 1) b = up[i];
+      if (i == 0 && j == p - 1) b += tr;
+      if (i == p - 1 && j == 0) b += bl;
+      if (b == 0.0) continue;
+      for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) {
+          long row = 2L * i + s, col = 2L * j + t;
+          double v = rr * b * P->Dc[2 * s + t];
+          if (transpose) A[col * m + row] += v;
+          else A[row * m + col] += v;
+        }
+    }
+  }
+  for (long q = 0; q < m; ++q) A[q * m + q] += 1.0;
+  free(lo);
+  free(di);
+  free(up);
+}
+
 /* ------------------------------------------------ axis operators (Eq. Ai) -- */
 
 /* out = (I + (k/gamma) A_a)^{-1} in, one line of axis a at a time.  A_a acts
@@ -184,6 +269,38 @@ int oracle_axis_solve(const oracle_problem *P, int a, double gamma, int transpos
   long st = axis_stride(P, a);
   long nhigh = N / (st * p);
   double h = oracle_h(P, a);
+  if (P->coupled) {
+    /* both species of a line form one system (Section 8: D not diagonal) */
+    const int m = 2 * p;
+    double *LU = (double *)malloc(sizeof(double) * (size_t)m * m);
+    int *piv = (int *)malloc(sizeof(int) * m);
+    coupled_line_matrix(P, p, P->bc[a], (P->k / gamma) / (h * h), transpose, LU);
+    int bad = dense_lu(m, LU, piv);
+    if (!bad) {
+#pragma omp parallel
+      {
+        double *line = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (long q = 0; q < nhigh * st; ++q) {
+          long hi = q / st, lo = q % st;
+          long base = lo + hi * st * p;
+          for (int i = 0; i < p; ++i) {
+            line[2 * i] = in[base + i * st];
+            line[2 * i + 1] = in[N + base + i * st];
+          }
+          dense_lu_solve(m, LU, piv, line);
+          for (int i = 0; i < p; ++i) {
+            out[base + i * st] = line[2 * i];
+            out[N + base + i * st] = line[2 * i + 1];
+          }
+        }
+        free(line);
+      }
+    }
+    free(LU);
+    free(piv);
+    return bad ? -1 : 0;
+  }
   for (int s = 0; s < P->nspecies; ++s) {
     double r = (P->k / gamma) * P->D[s] / (h * h);
     const double *src = in + s * N;
@@ -258,6 +375,17 @@ static void axis_laplacian(const oracle_problem *P, int a, const double *in, dou
 int oracle_axis_apply(const oracle_problem *P, int a, const double *in, double *out) {
   if (check_problem(P) || a < 0 || a >= P->dim) return -1;
   long N = npoints(P);
+  if (P->coupled) {
+    double *lap = (double *)malloc(sizeof(double) * 2 * N);
+    axis_laplacian(P, a, in, lap);
+    for (long i = 0; i < N; ++i) {
+      double l0 = lap[i], l1 = lap[N + i];
+      out[i] = P->Dc[0] * l0 + P->Dc[1] * l1;
+      out[N + i] = P->Dc[2] * l0 + P->Dc[3] * l1;
+    }
+    free(lap);
+    return 0;
+  }
   axis_laplacian(P, a, in, out);
   for (int s = 0; s < P->nspecies; ++s)
     for (long i = 0; i < N; ++i) out[s * N + i] *= P->D[s];
@@ -359,6 +487,29 @@ static void reaction_point(const oracle_problem *P, const double *u, const int *
     J[1][1] = 1.0 - r - 2.0 * b * cb;
     G[0][0] = r * b;
     G[1][0] = -r * a;
+    break;
+  }
+  case OR_NLS: { /* Section 8: F = q J u, J = [[0, 1], [-1, 0]], q = p0 + p1 |u|^2 + p2 bfac(x) */
+    double v = u[0], w = u[1], r = v * v + w * w;
+    double bfac = 1.0, cc = 1.0;
+    for (int a = 0; a < P->dim; ++a) {
+      double c = cos(OR_PI * node_x(P, a, idx[a]) / P->length[a]);
+      cc *= c * c;
+    }
+    bfac -= cc;
+    double q = p[0] + p[1] * r + p[2] * bfac;
+    f[0] = q * w;
+    f[1] = -q * v;
+    J[0][0] = 2.0 * p[1] * v * w;
+    J[0][1] = q + 2.0 * p[1] * w * w;
+    J[1][0] = -q - 2.0 * p[1] * v * v;
+    J[1][1] = -2.0 * p[1] * v * w;
+    G[0][0] = w;
+    G[1][0] = -v;
+    G[0][1] = r * w;
+    G[1][1] = -r * v;
+    G[0][2] = bfac * w;
+    G[1][2] = -bfac * v;
     break;
   }
   case OR_ENZYME: {
@@ -560,7 +711,7 @@ static void accumulate_dD(const oracle_problem *P, int a, double gamma, const do
 /* Reverse mode of step_forward, transposing each line of the frame in turn. */
 int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
                         const double *Ubar_next, double *Ubar_n, double *Dbar, double *pbar) {
-  if (check_problem(P)) return -1;
+  if (check_problem(P) || P->coupled) return -1;
   long M = npoints(P) * P->nspecies;
   int d = P->dim;
   double k = P->k;
@@ -638,7 +789,7 @@ int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
 
 int oracle_grad(const oracle_problem *P, const double *U0, double t0, const double *target,
                 long nsteps, double *loss, double *dU0, double *dD, double *dparams) {
-  if (check_problem(P) || nsteps < 0) return -1;
+  if (check_problem(P) || P->coupled || nsteps < 0) return -1;
   long M = npoints(P) * P->nspecies;
   double *states = (double *)malloc(sizeof(double) * (size_t)M * (size_t)(nsteps + 1));
   if (!states) return -2;

@@ -11,6 +11,11 @@
  * systems with dimensional splitting", arXiv 2001.11220):
  *   - the model u_t = D Lap u + F(u) of Section 2 (Eq. model), s species,
  *     diagonal D, homogeneous Dirichlet / Neumann / periodic boundaries;
+ *   - the coupled two-species form of Section 8 (complex Ginzburg-Landau
+ *     with D = 1 + i alpha, the cubic Schrodinger equation with a
+ *     non-diagonal D): a full 2 x 2 diffusion matrix, whose line systems
+ *     I + (k/gamma)/h^2 (B_p (x) D) are solved as one 2p x 2p system per
+ *     line (dense LU with partial pivoting, formed once per axis and pole);
  *   - the 1D matrices B_p of Section 3, Example 1 and the Kronecker operator
  *     A_i of Eq. (Ai), applied line by line;
  *   - the fully discrete ETD-RDP-IF scheme of the framed box in Section 6
@@ -43,8 +48,11 @@ enum {
   OR_SCHNAKENBERG = 3, /* F_u = g (a - u + u^2 v) ; F_v = g (b - u^2 v) ; p = (a, b, g) */
   OR_GRAY_SCOTT = 4,   /* F_u = -u v^2 + F (1-u) ; F_v = u v^2 - (F+kappa) v ; p = (F, kappa) */
   OR_ENZYME = 5,       /* F = -u/(1+u) + p0 * src(x,t; p1) (Section 8.1, plus manufactured source) */
-  OR_CGL = 6           /* complex Ginzburg-Landau with real diffusion (Section 8, alpha = 0): species
-                          0, 1 = Re, Im of u; F = u - (1 + i beta) u |u|^2 ; p = (beta) */
+  OR_CGL = 6,          /* complex Ginzburg-Landau (Section 8): species 0, 1 = Re, Im of u;
+                          F = u - (1 + i beta) u |u|^2 ; p = (beta) */
+  OR_NLS = 7           /* cubic Schrodinger (Section 8): species 0, 1 = v, w (Psi = v + i w);
+                          F = q J u with J = [[0, 1], [-1, 0]] and
+                          q = p0 + p1 |u|^2 + p2 (1 - prod_a cos^2(pi x_a / L_a)) */
 };
 
 typedef struct {
@@ -57,6 +65,8 @@ typedef struct {
   int reaction;      /* OR_* reaction kind */
   double params[8];  /* reaction parameters */
   double k;          /* time step */
+  int coupled;       /* 1: species 0 and 1 diffuse through the full matrix Dc (s = 2; D unused) */
+  double Dc[4];      /* 2 x 2 diffusion matrix, row-major: u_t = Dc Lap u + F(u) */
 } oracle_problem;
 
 /* spacing h of axis a (Section 3, Example 1) */
@@ -67,11 +77,14 @@ double oracle_h(const oracle_problem *P, int axis);
 int oracle_line_solve(int p, int bc, double r, int transpose, const double *b, double *x);
 
 /* all lines of one axis, all species: out = (I + (k/gamma) A_axis)^{-1} in
- * (transpose: the transposed operator).  in and out may alias. */
+ * (transpose: the transposed operator).  in and out may alias.  Coupled
+ * problems solve both species of a line together (returns -1 if that
+ * 2p x 2p matrix is singular). */
 int oracle_axis_solve(const oracle_problem *P, int axis, double gamma, int transpose,
                       const double *in, double *out);
 
-/* out = A_axis in  (the Kronecker operator of Eq. (Ai) for one axis, times D) */
+/* out = A_axis in  (the Kronecker operator of Eq. (Ai) for one axis, times D;
+ * for coupled problems species r of the output sums Dc[r][s] B_p u_s) */
 int oracle_axis_apply(const oracle_problem *P, int axis, const double *in, double *out);
 
 /* pointwise reaction F(U, t) over the grid (Section 2) */
@@ -87,7 +100,8 @@ int oracle_step(const oracle_problem *P, double *U, double t);
 int oracle_run(const oracle_problem *P, double *U, double t0, long nsteps);
 
 /* reverse mode of one step: given U_n (at time t) and Ubar_{n+1}, return
- * Ubar_n and accumulate Dbar[s] (d/dD_s) and pbar[j] (d/dparams_j). */
+ * Ubar_n and accumulate Dbar[s] (d/dD_s) and pbar[j] (d/dparams_j).
+ * Diagonal D only (returns -1 for coupled problems; so does oracle_grad). */
 int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
                         const double *Ubar_next, double *Ubar_n, double *Dbar, double *pbar);
 

@@ -39,9 +39,11 @@ def B_p(p: int, bc: int, h: float) -> np.ndarray:
 
 
 def A_i(P: oracle.Problem, i: int) -> np.ndarray:
-    """Eq. (Ai): I x ... x B_p (position d-i+1) x ... x I x D, i = 1..d (axis i-1)."""
+    """Eq. (Ai): I x ... x B_p (position d-i+1) x ... x I x D, i = 1..d (axis i-1).
+    D is diag(P.D), or the full 2 x 2 matrix P.Dc of the coupled systems of
+    Section 8 (the same Kronecker slot)."""
     d = P.dim
-    Dm = np.diag(P.D)
+    Dm = np.diag(P.D) if getattr(P, "Dc", None) is None else np.asarray(P.Dc, dtype=np.float64).reshape(2, 2)
     factors = []
     for pos in range(1, d + 1):          # spatial Kronecker positions 1..d
         axis = d - pos                    # position d-i+1 holds axis i-1

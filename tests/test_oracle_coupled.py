@@ -1,0 +1,231 @@
+"""Pins for the oracle's coupled two-species systems of Section 8: the complex
+Ginzburg-Landau equation with D = 1 + i alpha and the cubic Schrodinger
+equation, whose diffusion matrix is not diagonal.  The complex state
+u = u_0 + i u_1 is carried as two real species; a 2 x 2 matrix
+[[p, -q], [q, p]] is the complex coefficient p + i q.
+
+  * dense solves of the Kronecker-assembled Eq. (Ai) with D in the last slot
+    (numpy LAPACK)                               -> line gathering, ordering, transposes;
+  * a diagonal matrix reduces to two uncoupled species (the Thomas path, pinned
+    elsewhere);
+  * Fourier / cosine / sine eigenmodes: each line operator multiplies the
+    complex amplitude by a closed-form scalar, and the phase-equivariant
+    reactions keep a mode a mode, so n steps reduce to a scalar complex
+    recurrence of the framed scheme of Section 6 (written here from the frame,
+    with the paper's rational functions of the eigenvalue);
+  * the exact 2D Schrodinger solution of Section 8, e^{-it} cos(pi x) cos(pi y),
+    reached at second order;
+  * hand values and finite differences of the Schrodinger reaction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import dense_reference as dr
+
+RNG = np.random.default_rng(2001)
+TWO_PI2 = 2.0 * math.pi ** 2
+
+
+def rot(p, q):
+    """2 x 2 real form of the complex diffusion coefficient p + i q (row-major)."""
+    return (p, -q, q, p)
+
+
+def cplx_state(Z):
+    return np.stack([Z.real, Z.imag])
+
+
+def as_complex(U):
+    return U[0] + 1j * U[1]
+
+
+# ------------------------------------------------------------ line solves --
+
+@pytest.mark.parametrize("dims,bcs", [((5, 4), (0, 1)), ((6, 5), (2, 2)), ((4, 3, 5), (1, 2, 0))])
+@pytest.mark.parametrize("Dc", [rot(1.0, 0.7), rot(0.0, 1.0), (0.4, 0.3, -0.2, 0.9)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_coupled_axis_solve_vs_kronecker_dense(dims, bcs, Dc, transpose):
+    P = oracle.Problem(n=dims, bc=bcs, D=(1.0, 1.0), Dc=Dc, k=0.07, length=(1.0, 1.3, 0.8)[: len(dims)])
+    U = RNG.standard_normal(P.shape)
+    for axis in range(P.dim):
+        for gamma in (1.0, 3.0, 4.0):
+            got = oracle.axis_solve(P, axis, gamma, U, transpose=transpose)
+            ref = dr.from_paper(P, dr.solve(P, axis + 1, gamma, dr.to_paper(P, U), transpose))
+            assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)), (axis, gamma)
+
+
+def test_coupled_axis_apply_vs_kronecker_dense():
+    P = oracle.Problem(n=(4, 5, 3), bc=(1, 2, 0), D=(1.0, 1.0), Dc=(0.4, -1.1, 0.7, 0.2), k=0.1)
+    U = RNG.standard_normal(P.shape)
+    for axis in range(3):
+        ref = dr.from_paper(P, dr.A_i(P, axis + 1) @ dr.to_paper(P, U))
+        assert np.allclose(oracle.axis_apply(P, axis, U), ref, rtol=1e-13, atol=1e-11)
+
+
+@pytest.mark.parametrize("bcs", [(0, 1), (2, 2), (1, 2, 0)])
+def test_diagonal_coupling_is_two_uncoupled_species(bcs):
+    n = (6, 5, 4)[: len(bcs)]
+    kw = dict(n=n, bc=bcs, reaction=oracle.BRUSSELATOR, params=(1.0, 3.4), k=0.02)
+    Pu = oracle.Problem(D=(0.7, 0.2), **kw)
+    Pc = oracle.Problem(D=(1.0, 1.0), Dc=(0.7, 0.0, 0.0, 0.2), **kw)
+    U = 1.0 + 0.3 * RNG.random(Pu.shape)
+    a, b = oracle.run(Pu, U, 0.0, 3), oracle.run(Pc, U, 0.0, 3)
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+
+
+def test_coupled_adjoint_is_refused():
+    P = oracle.Problem(n=(4, 4), bc=(2, 2), D=(1.0, 1.0), Dc=rot(1.0, 0.5), reaction=oracle.CGL, params=(1.3,), k=0.1)
+    U = RNG.standard_normal(P.shape)
+    with pytest.raises(ValueError):
+        oracle.step_adjoint(P, U, 0.0, U)
+
+
+# ------------------------------------------------------ eigenmode recurrence --
+
+def mode_recurrence(a, nsteps, k, d, mus, f):
+    """The framed scheme of Section 6 on one mode: every line operator
+    (I + (k/gamma) A_a)^{-1} is 1/(1 + k d mu_a / gamma); axes in order
+    (x first, the last axis carries U*, F(U*) and the T/S corrector)."""
+    def ops(mu):
+        return [1.0 / (1.0 + k * d * mu / g) for g in (1.0, 3.0, 4.0)]
+    for _ in range(nsteps):
+        f0 = f(a)
+        cU, cf, w = a, f0, a + k * f0
+        for mu in mus[:-1]:
+            P1, T, S = ops(mu)
+            R = 9 * T - 8 * S
+            cU, cf, w = R * cU, R * cf, P1 * w
+        P1, T, S = ops(mus[-1])
+        fs = f(P1 * w)
+        a = T * (9 * cU + 2 * k * cf + k * fs) - S * (8 * cU + 1.5 * k * cf + 0.5 * k * fs)
+    return a
+
+
+def cgl_f(beta):
+    return lambda a: a - (1 + 1j * beta) * a * abs(a) ** 2
+
+
+def nls_f(p0, p1):
+    return lambda a: -1j * (p0 + p1 * abs(a) ** 2) * a
+
+
+@pytest.mark.parametrize("case", ["cgl2d", "cgl3d", "nls2d", "nls3d"])
+def test_periodic_plane_wave_follows_scalar_recurrence(case):
+    """u = a e^{i kappa.x} on a periodic grid: the Laplacian's eigenvalue on each
+    axis is 4 sin^2(pi m / p) / h^2 and |u| is uniform, so the state stays a plane
+    wave whose amplitude follows the scalar recurrence.  A transposed coupling
+    (p - i q instead of p + i q), a wrong sign in F or a swapped R/P would change
+    the amplitude at first order."""
+    if case.startswith("cgl"):
+        Dc, d, kind, params, f = rot(1.0, 0.8), 1.0 + 0.8j, oracle.CGL, (1.3,), cgl_f(1.3)
+    else:
+        Dc, d, kind, params, f = rot(0.0, 1.0), 1.0j, oracle.NLS, (0.4, -1.0, 0.0), nls_f(0.4, -1.0)
+    dim = 3 if case.endswith("3d") else 2
+    n, L, ms = (12, 10, 8)[:dim], (6.0, 5.0, 4.0)[:dim], (2, 1, 3)[:dim]
+    P = oracle.Problem(n=n, bc=(2,) * dim, D=(1.0, 1.0), Dc=Dc, reaction=kind, params=params, k=0.05, length=L)
+    grids = np.meshgrid(*[P.coords(a) for a in reversed(range(dim))], indexing="ij")
+    phase = sum(2 * math.pi * ms[a] / L[a] * grids[dim - 1 - a] for a in range(dim))
+    a0 = 0.6 * np.exp(0.3j)
+    V = oracle.run(P, cplx_state(a0 * np.exp(1j * phase)), 0.0, 7)
+    mus = [4 * math.sin(math.pi * ms[a] / n[a]) ** 2 / P.h(a) ** 2 for a in range(dim)]
+    an = mode_recurrence(a0, 7, P.k, d, mus, f)
+    Z = as_complex(V)
+    assert np.max(np.abs(Z - an * np.exp(1j * phase))) < 1e-13, (an, Z.ravel()[:2])
+    assert abs(an - a0) > 1e-2
+
+
+@pytest.mark.parametrize("bc", [oracle.NEUMANN, oracle.DIRICHLET])
+@pytest.mark.parametrize("Dc,d", [(rot(0.0, 1.0), 1.0j), (rot(1.0, -0.6), 1.0 - 0.6j)])
+def test_cosine_and_sine_modes_follow_scalar_recurrence(bc, Dc, d):
+    """Linear reaction F = -i p0 u (Schrodinger with q = p0): Neumann nodes
+    x_i = i h carry cos(pi m i / (p - 1)) with eigenvalue 4 sin^2(pi m / (2 (p-1))) / h^2,
+    Dirichlet nodes x_i = (i + 1) h carry sin(pi m (i + 1) / (p + 1)) with
+    4 sin^2(pi m / (2 (p+1))) / h^2 (Example 1's boundary rows)."""
+    n, ms = (9, 7), (2, 3)
+    P = oracle.Problem(n=n, bc=(bc, bc), D=(1.0, 1.0), Dc=Dc, reaction=oracle.NLS, params=(0.7, 0.0, 0.0),
+                       k=0.03, length=(1.0, 0.8))
+    prof, mus = [], []
+    for a in range(2):
+        i = np.arange(n[a])
+        if bc == oracle.NEUMANN:
+            prof.append(np.cos(math.pi * ms[a] * i / (n[a] - 1)))
+            mus.append(4 * math.sin(math.pi * ms[a] / (2 * (n[a] - 1))) ** 2 / P.h(a) ** 2)
+        else:
+            prof.append(np.sin(math.pi * ms[a] * (i + 1) / (n[a] + 1)))
+            mus.append(4 * math.sin(math.pi * ms[a] / (2 * (n[a] + 1))) ** 2 / P.h(a) ** 2)
+    shape = np.outer(prof[1], prof[0])
+    a0 = 0.9 - 0.4j
+    V = oracle.run(P, cplx_state(a0 * shape), 0.0, 5)
+    an = mode_recurrence(a0, 5, P.k, d, mus, nls_f(0.7, 0.0))
+    assert np.max(np.abs(as_complex(V) - an * shape)) < 1e-13
+    assert abs(an - a0) > 1e-2
+
+
+# ---------------------------------------------------- Section 8, Schrodinger --
+
+def nls2d_problem(p, k):
+    """Section 8's 2D example: i Psi_t + Lap Psi = q Psi on the unit square,
+    Neumann, q = B + C |Psi|^2 with B = (1 - 2 pi^2)(1 - cos^2(pi x) cos^2(pi y)),
+    C = 1 - 2 pi^2.  As u_t = D Lap u + F: D = [[0, -1], [1, 0]] (the complex i)
+    and F = q J u."""
+    c = 1.0 - TWO_PI2
+    return oracle.Problem(n=(p, p), bc=(1, 1), D=(1.0, 1.0), Dc=rot(0.0, 1.0), reaction=oracle.NLS,
+                          params=(0.0, c, c), k=k)
+
+
+def nls2d_exact(P, t):
+    x = P.coords(0)
+    y = P.coords(1)
+    return np.exp(-1j * t) * np.outer(np.cos(math.pi * y), np.cos(math.pi * x))
+
+
+def test_nls_2d_exact_solution_second_order():
+    """Psi = e^{-it} cos(pi x) cos(pi y) solves the example exactly; with k = h / 8
+    (the cubic term q |Psi|^2 ~ -18.7 is explicit in the scheme, so k |q| must be
+    well below 1) the error at T = 0.5 falls by about 4 per halving of h
+    (measured orders 2.2 and 2.1 on p = 17, 33, 65)."""
+    T, errs = 0.5, []
+    for p in (17, 33, 65):
+        h = 1.0 / (p - 1)
+        P = nls2d_problem(p, h / 8)
+        V = oracle.run(P, cplx_state(nls2d_exact(P, 0.0)), 0.0, int(round(T / P.k)))
+        errs.append(np.max(np.abs(as_complex(V) - nls2d_exact(P, T))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 < o < 2.4 for o in orders), (errs, orders)
+    assert errs[-1] < 1e-2
+
+
+def test_nls_reaction_hand_values():
+    """q = p0 + p1 |u|^2 + p2 (1 - cos^2(pi x) cos^2(pi y)); F = (q w, -q v).  At
+    u = (0.3, 0.4), |u|^2 = 0.25, node (x, y) = (0.5, 0): the cos product is 0, so
+    q = 0.2 + 0.25 (-2) + 1.5 = 1.2 and F = (0.48, -0.36); at (0, 0) the cos product
+    is 1 and q = -0.3, F = (-0.12, 0.09)."""
+    P = oracle.Problem(n=(3, 3), bc=(1, 1), D=(1.0, 1.0), Dc=rot(0.0, 1.0), reaction=oracle.NLS,
+                       params=(0.2, -2.0, 1.5), k=0.1)
+    U = np.stack([np.full((3, 3), 0.3), np.full((3, 3), 0.4)])
+    F = oracle.reaction(P, U, 0.0)
+    assert np.allclose(F[:, 0, 1], (0.48, -0.36), atol=1e-15, rtol=0)
+    assert np.allclose(F[:, 0, 0], (-0.12, 0.09), atol=1e-15, rtol=0)
+
+
+def test_nls_reaction_derivatives_fd():
+    P = oracle.Problem(n=(5, 4), bc=(1, 2), D=(1.0, 1.0), Dc=rot(0.0, 1.0), reaction=oracle.NLS,
+                       params=(0.3, -0.8, 0.5), k=0.1)
+    U = RNG.standard_normal(P.shape)
+    ybar = RNG.standard_normal(P.shape)
+    out, pbar = oracle.reaction_vjp(P, U, 0.2, ybar)
+    eps = 1e-6
+    V = RNG.standard_normal(P.shape)
+    fd = (np.sum(ybar * oracle.reaction(P, U + eps * V, 0.2)) - np.sum(ybar * oracle.reaction(P, U - eps * V, 0.2))) / (2 * eps)
+    assert abs(fd - np.sum(out * V)) < 1e-7 * max(1, abs(fd))
+    for j in range(3):
+        pp, pm = list(P.params), list(P.params)
+        pp[j] += eps
+        pm[j] -= eps
+        Pp = oracle.Problem(n=P.n, bc=P.bc, D=P.D, Dc=P.Dc, reaction=oracle.NLS, params=pp, k=0.1)
+        Pm = oracle.Problem(n=P.n, bc=P.bc, D=P.D, Dc=P.Dc, reaction=oracle.NLS, params=pm, k=0.1)
+        fdp = (np.sum(ybar * oracle.reaction(Pp, U, 0.2)) - np.sum(ybar * oracle.reaction(Pm, U, 0.2))) / (2 * eps)
+        assert abs(fdp - pbar[j]) < 1e-7 * max(1, abs(fdp)), j
