@@ -158,7 +158,8 @@ def oracle_baseline(w, sample_steps: int = 1, threads: int = 1):
     from paper_2001_11220_gb300 import workloads as W
     oracle.build()
     used = oracle.set_threads(threads)
-    P = oracle.Problem(n=w.n, bc=w.bc, D=w.D, reaction=w.reaction_id, params=w.params, k=w.k, length=w.length)
+    P = oracle.Problem(n=w.n, bc=w.bc, D=w.D, reaction=w.reaction_id, params=w.params, k=w.k, length=w.length,
+                          Dc=w.Dc)
     U0 = W.initial_state(w)
     t = time.perf_counter()
     oracle.run(P, U0, 0.0, sample_steps)
@@ -385,6 +386,24 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
                                     "tiles": tiles_of(c.info(), wcgl.dim),
                                     "step_frac": c.info()["algorithmic_bytes"] / (ms / nst / 1e3) / 1e9 / peak,
                                     "paper_cpu_context": paper_s}
+        c.close()
+        del U
+    # coupled two-species diffusion (complex line kernels, etd_create_coupled): the same CGL runs
+    # with alpha = 0.5 (D = 1 + 0.5 i), and Section 8's 2D Schrodinger run (p = 79, k = 0.0125,
+    # T = 1, Neumann, FP64); per-sweep rooflines from profiled launches
+    for wc, prec, nst in ((W.cgl_2d(400, alpha=0.5), "fp32", 200), (W.cgl_3d(200, alpha=0.5), "fp32", 40),
+                          (W.nls_2d(), "fp64", 80)):
+        c, U = mk(wc, prec, tune=False)
+        rb = 4 if prec == "fp32" else 8
+        ms = _timed(lambda: c.run(U, 0.0, nst), stream)
+        tiles = tiles_of(c.info(), wc.dim)
+        per, _ = sweep_roofline(c, U, wc, 2, rb, peak, f"{wc.name}_{prec}", tiles)
+        out[f"{wc.name}_{prec}"] = {"value": wc.npoints * wc.nspecies * nst / (ms / 1e3), "unit": UNIT,
+                                    "ms_per_step": ms / nst, "us_per_step": ms / nst * 1e3,
+                                    "full_run_s": ms / nst * wc.steps / 1e3, "steps_full_run": wc.steps,
+                                    "tiles": tiles, "kernel": "complex line kernel (staged = 6)",
+                                    "step_frac": c.info()["algorithmic_bytes"] / (ms / nst / 1e3) / 1e9 / peak,
+                                    "per_sweep": per}
         c.close()
         del U
     return out

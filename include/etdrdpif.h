@@ -67,9 +67,14 @@ typedef enum { ETD_FP64 = 0, ETD_FP32 = 1 } etd_precision;
  *                 (p1 Sum_a (pi/L_a)^2 - 1) q + q/(1+q),
  *                 q = e^{-t} Prod_a sin(pi x_a/L_a)                 (s = 1;
  *                 Section 8.1; p0 = 0 gives the paper's enzyme model)
- *   CGL           complex Ginzburg-Landau of Section 8 with real diffusion
- *                 (alpha = 0, the paper's runs): species 0, 1 = Re u, Im u,
- *                 F = u - (1 + i p0) u |u|^2                           (s = 2) */
+ *   CGL           complex Ginzburg-Landau of Section 8: species 0, 1 = Re u,
+ *                 Im u, F = u - (1 + i p0) u |u|^2 (s = 2).  With etd_create
+ *                 the diffusion is real (alpha = 0, the paper's runs); with
+ *                 etd_create_coupled it is 1 + i alpha.
+ *   NLS           cubic Schrodinger of Section 8 (etd_create_coupled only):
+ *                 species 0, 1 = v, w (Psi = v + i w), F = q (w, -v) with
+ *                 q = p0 + p1 (v^2 + w^2) + p2 (1 - Prod_a cos^2(pi x_a/L_a))
+ *                 (s = 2; the paper's 2D example: p0 = 0, p1 = p2 = 1 - 2 pi^2) */
 typedef enum {
   ETD_REACTION_ZERO = 0,
   ETD_REACTION_LINEAR = 1,
@@ -77,7 +82,8 @@ typedef enum {
   ETD_REACTION_SCHNAKENBERG = 3,
   ETD_REACTION_GRAY_SCOTT = 4,
   ETD_REACTION_ENZYME = 5,
-  ETD_REACTION_CGL = 6
+  ETD_REACTION_CGL = 6,
+  ETD_REACTION_NLS = 7
 } etd_reaction_kind;
 
 typedef struct {
@@ -115,7 +121,8 @@ typedef struct {
                                     summary, carry and solve launches), 4: the same in one launch,
                                     the blocks of a line group forming a thread-block cluster,
                                     5: circulant kernel of a periodic axis (constant-coefficient
-                                    factorisation, no line tables) */
+                                    factorisation, no line tables), 6: complex line kernel of a
+                                    coupled context (etd_create_coupled) */
   int32_t pack[3];               /* 2: FP32 register kernel on pairs of neighbouring lines
                                     (lines_per_block then counts pairs), 1: one line per thread;
                                     segmented kernels: chunks per segment */
@@ -134,6 +141,27 @@ typedef struct {
  * default stream).  On success *out owns everything; free with etd_destroy. */
 etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction *reaction,
                       double k, int32_t precision, void *stream, etd_ctx **out);
+
+/* Create a context for a coupled two-species problem of Section 8:
+ * u_t = Dm Lap u + F(u) with the 2 x 2 diffusion matrix Dm (4 host doubles,
+ * row-major) acting on (u_0, u_1).  The kernels take Dm = [[p, -q], [q, p]]
+ * with p >= 0 -- the complex coefficient p + i q on u = u_0 + i u_1: the
+ * complex Ginzburg-Landau equation (p = 1, q = alpha) and the cubic
+ * Schrodinger equation, whose form u_t + J Lap u = q J u with
+ * J = [[0, 1], [-1, 0]] is Dm = -J (p = 0, q = 1).  Every line system
+ * I + (k/gamma)(p + i q)/h^2 B_p is a complex tridiagonal (cyclic) matrix,
+ * LU-factorised in FP64 on the host (strictly diagonally dominant in
+ * modulus, no pivoting) and uploaded in the context's precision; periodic
+ * lines use a per-line Sherman-Morrison correction.  nspecies must be 2 and
+ * the reaction ZERO, LINEAR, CGL or NLS (else ETD_ERR_UNSUPPORTED, as for
+ * another Dm; ETD_ERR_INVALID_ARG for a non-finite Dm or p < 0, and for the
+ * grid / k / precision checks of etd_create).  Lines longer than about
+ * 3200 nodes (FP64) / 6400 (FP32) do not fit the kernel's shared memory:
+ * ETD_ERR_UNSUPPORTED.  The context takes etd_step, etd_run, etd_run_host,
+ * etd_profile*, etd_get_info (staged = 6) and etd_destroy; the adjoint and
+ * gradient calls and etd_autotune return ETD_ERR_UNSUPPORTED. */
+etd_status etd_create_coupled(const etd_grid *grid, const double *Dm, const etd_reaction *reaction,
+                              double k, int32_t precision, void *stream, etd_ctx **out);
 
 /* One ETD-RDP-IF step in place: U (device, layout above) holds U_n at time
  * t_n on entry and U_{n+1} on return (stream-ordered). */

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "ETD_OK", 1: "ETD_ERR_INVALID_ARG", 2: "ETD_ERR_UNSUPPORTED",
 ETD_FP64, ETD_FP32 = 0, 1
 
 # every symbol include/etdrdpif.h declares
-EXPORTS = ["etd_create", "etd_step", "etd_run", "etd_run_host", "etd_step_adjoint", "etd_grad", "etd_run_vjp",
+EXPORTS = ["etd_create", "etd_create_coupled", "etd_step", "etd_run", "etd_run_host", "etd_step_adjoint", "etd_grad", "etd_run_vjp",
            "etd_batch_create", "etd_batch_run", "etd_batch_autotune", "etd_batch_set_wait_limit",
            "etd_batch_debug_hold", "etd_autotune", "etd_set_stream", "etd_profile",
            "etd_profile_read", "etd_get_info", "etd_step_noalloc",
@@ -64,6 +64,8 @@ def load() -> ctypes.CDLL:
     pp = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "etd_create": ([ctypes.POINTER(etd_grid), dptr, ctypes.POINTER(etd_reaction), dbl, i32, vp, pp], i32),
+        "etd_create_coupled": ([ctypes.POINTER(etd_grid), dptr, ctypes.POINTER(etd_reaction), dbl, i32, vp, pp],
+                               i32),
         "etd_step": ([vp, vp, dbl], i32),
         "etd_run": ([vp, vp, dbl, i64], i32),
         "etd_run_host": ([vp, vp, dbl, i64], i32),

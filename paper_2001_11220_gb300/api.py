@@ -45,26 +45,36 @@ def make_reaction(kind, nspecies, params=()) -> B.etd_reaction:
 class EtdRdpIf:
     """One ETD-RDP-IF problem on the current CUDA device."""
 
-    def __init__(self, n, bc, D, reaction="zero", params=(), k=0.01, precision="fp64", length=None, stream=None):
+    def __init__(self, n, bc, D, reaction="zero", params=(), k=0.01, precision="fp64", length=None, stream=None,
+                 Dc=None):
+        """Dc (optional): the 2 x 2 diffusion matrix (row-major) of a coupled
+        two-species problem, etd_create_coupled; D then only fixes the species
+        count (two)."""
         self.lib = B.load()
         self.n = tuple(int(v) for v in n)
         self.D = tuple(float(d) for d in D)
+        self.Dc = None if Dc is None else tuple(float(v) for v in Dc)
         self.k = float(k)
         self.precision = B.ETD_FP64 if precision in ("fp64", B.ETD_FP64) else B.ETD_FP32
         self.dtype = torch.float64 if self.precision == B.ETD_FP64 else torch.float32
         self.shape = (len(self.D),) + tuple(reversed(self.n))
         grid = make_grid(self.n, bc, length)
         rx = make_reaction(reaction, len(self.D), params)
-        Darr = (ctypes.c_double * len(self.D))(*self.D)
         ctx = ctypes.c_void_p()
-        st = self.lib.etd_create(ctypes.byref(grid), Darr, ctypes.byref(rx), self.k, self.precision,
-                                 _stream_handle(stream), ctypes.byref(ctx))
+        if self.Dc is not None:
+            Dm = (ctypes.c_double * 4)(*self.Dc)
+            st = self.lib.etd_create_coupled(ctypes.byref(grid), Dm, ctypes.byref(rx), self.k, self.precision,
+                                             _stream_handle(stream), ctypes.byref(ctx))
+        else:
+            Darr = (ctypes.c_double * len(self.D))(*self.D)
+            st = self.lib.etd_create(ctypes.byref(grid), Darr, ctypes.byref(rx), self.k, self.precision,
+                                     _stream_handle(stream), ctypes.byref(ctx))
         B.check(st, None)
         self.ctx = ctx
 
     @classmethod
     def from_workload(cls, w: Workload, precision="fp64", stream=None) -> "EtdRdpIf":
-        return cls(w.n, w.bc, w.D, w.reaction, w.params, w.k, precision, w.length, stream)
+        return cls(w.n, w.bc, w.D, w.reaction, w.params, w.k, precision, w.length, stream, w.Dc)
 
     def _check_state(self, U: torch.Tensor):
         if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous() and tuple(U.shape) == self.shape):

@@ -76,6 +76,8 @@ etd_status validate_problem(const etd_grid *grid, const double *D, const etd_rea
     case ETD_REACTION_ENZYME:
       if (S != 1) return fail(nullptr, ETD_ERR_INVALID_ARG, "enzyme reaction needs 1 species");
       break;
+    case ETD_REACTION_NLS:
+      return fail(nullptr, ETD_ERR_UNSUPPORTED, "the Schrodinger reaction needs etd_create_coupled");
     default: return fail(nullptr, ETD_ERR_INVALID_ARG, "unknown reaction kind %d", rx->kind);
   }
   for (int j = 0; j < 8; ++j)
@@ -895,7 +897,10 @@ static cudaError_t step_instance(const Instance &I, R *U, double t, cudaStream_t
   return cudaSuccess;
 }
 
+cudaError_t cplx_step(const Instance &I, void *U, double t, cudaStream_t s, etd_ctx *prof);
+
 cudaError_t forward_step(const Instance &I, void *U, double t, cudaStream_t s, etd_ctx *prof) {
+  if (I.coupled) return cplx_step(I, U, t, s, prof);
   if (I.real_bytes == 8) return step_instance<double>(I, (double *)U, t, s, prof);
   return step_instance<float>(I, (float *)U, t, s, prof);
 }
@@ -1143,6 +1148,13 @@ etd_status etd_get_info(const etd_ctx *ctx, etd_info *info) {
     info->pack[a] = I.plan[a].nseg > 1 ? I.plan[a].mx : I.plan[a].pk;
     info->grid_blocks[a] = ctx->batched ? (ctx->ens_on ? ctx->ens_grid : ctx->batch_total_blocks[a])
                                         : I.plan[a].nblocks;
+    if (I.coupled) {  // complex line kernel: one launch per axis
+      info->chunk[a] = I.cax[a].chunk;
+      info->lines_per_block[a] = I.cax[a].nl;
+      info->staged[a] = 6;
+      info->pack[a] = 1;
+      info->grid_blocks[a] = I.cax[a].nblocks;
+    }
   }
   return ETD_OK;
 }

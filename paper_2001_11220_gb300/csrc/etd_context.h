@@ -12,6 +12,7 @@
 
 #include "../../include/etdrdpif.h"
 #include "etd_circ.h"
+#include "etd_cplx.h"
 #include "etd_internal.h"
 
 #define ETD_MAX_BLOCK_THREADS 512
@@ -106,6 +107,10 @@ struct Instance {
   CircArgs<float> circ32[3];
   CircArgs<double> circ64[3];
   void *circ_tables[3] = {nullptr, nullptr, nullptr};
+  // coupled two-species diffusion Dm = [[dcp, -dcq], [dcq, dcp]] (complex p + i q): complex line kernels
+  bool coupled = false;
+  double dcp = 0, dcq = 0;
+  CplxAxis cax[3];
   std::vector<void *> owned;  // cudaMalloc'ed buffers freed by etd_destroy
 };
 

@@ -355,6 +355,7 @@ etd_status check_grad_ctx(etd_ctx *ctx) {
   if (!ctx) return fail(nullptr, ETD_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "gradients of batched contexts are not supported");
   const Instance &I = ctx->inst[0];
+  if (I.coupled) return fail(ctx, ETD_ERR_UNSUPPORTED, "gradients of coupled (complex-diffusion) contexts are not built");
   for (int s = 0; s < I.S; ++s)
     if (!(I.D[s] > 0))
       return fail(ctx, ETD_ERR_UNSUPPORTED, "the adjoint needs D_s > 0 (D[%d] = %g): dL/dD is formed as "

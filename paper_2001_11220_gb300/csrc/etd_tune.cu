@@ -77,6 +77,7 @@ extern "C" etd_status etd_autotune(etd_ctx *ctx, void *U_work) {
   if (ctx->batched) return fail(ctx, ETD_ERR_INVALID_ARG, "etd_autotune on a batched context");
   if (!U_work) return fail(ctx, ETD_ERR_INVALID_ARG, "U_work is NULL");
   Instance &I = ctx->inst[0];
+  if (I.coupled) return fail(ctx, ETD_ERR_UNSUPPORTED, "coupled contexts have one complex line kernel plan");
   drop_graphs(ctx);
   const int Ls32[] = {4, 8, 16}, Ls64[] = {4, 8};
   const int nlbs[] = {4, 8, 16, 32, 64};

@@ -4,6 +4,9 @@ profiling captures).
     python -m paper_2001_11220_gb300.run --workload mms3d --p 256 --precision fp32 --steps 4
     python -m paper_2001_11220_gb300.run --workload grayscott3d --p 256 --steps 2 --grad
       (--grad: the misfit gradient over the steps, one checkpoint segment)
+    python -m paper_2001_11220_gb300.run --workload cgl3d --p 200 --alpha 0.5 --steps 2
+      (complex Ginzburg-Landau; --alpha != 0 couples Re u and Im u: complex line kernels)
+    python -m paper_2001_11220_gb300.run --workload nls2d --p 79 --precision fp64 --steps 80
 """
 from __future__ import annotations
 
@@ -17,8 +20,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def workload(name: str, p: int):
+def workload(name: str, p: int, alpha: float = 0.0):
     from paper_2001_11220_gb300 import workloads as W
+    if name == "cgl2d":
+        return W.cgl_2d(p, alpha=alpha)
+    if name == "cgl3d":
+        return W.cgl_3d(p, alpha=alpha)
+    if name == "nls2d":
+        return W.nls_2d(p)
     if name == "mms3d":
         return W.mms_3d(p)
     if name == "brusselator2d":
@@ -37,12 +46,13 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--grad", action="store_true")
+    ap.add_argument("--alpha", type=float, default=0.0)
     args = ap.parse_args()
     import torch
 
     from paper_2001_11220_gb300 import workloads as W
     from paper_2001_11220_gb300.api import EtdRdpIf
-    w = workload(args.workload, args.p)
+    w = workload(args.workload, args.p, args.alpha)
     ctx = EtdRdpIf.from_workload(w, args.precision)          # default stream: direct launches
     U = torch.tensor(W.initial_state(w), device="cuda", dtype=ctx.dtype)
     torch.cuda.synchronize()

@@ -21,7 +21,7 @@ import numpy as np
 
 DIRICHLET, NEUMANN, PERIODIC = 0, 1, 2
 REACTIONS = {"zero": 0, "linear": 1, "brusselator": 2, "schnakenberg": 3, "gray_scott": 4, "enzyme": 5,
-             "cgl": 6}
+             "cgl": 6, "nls": 7}
 BC_NAMES = {DIRICHLET: "dirichlet", NEUMANN: "neumann", PERIODIC: "periodic"}
 
 
@@ -41,6 +41,7 @@ class Workload:
     ic_args: tuple = ()
     seed: int = 2001
     extra: dict = field(default_factory=dict)
+    Dc: tuple = None         # coupled two-species diffusion matrix (row-major 2 x 2), or None
 
     def __post_init__(self):
         self.n = tuple(int(v) for v in self.n)
@@ -143,7 +144,18 @@ def initial_state(w: Workload, seed: int | None = None) -> np.ndarray:
         for c, sg in zip(centres, signs):
             re += sg * np.exp(-sum((g[a] - c[a]) ** 2 for a in range(w.dim)) / 1000.0)
         return np.stack([re, np.zeros_like(re)])
+    if w.ic == "nls_exact":           # Section 8 (Schrodinger 2D): Psi(0) = cos(pi x) cos(pi y), real
+        return exact_nls(w, 0.0)
     raise ValueError(f"unknown initial-state recipe {w.ic!r}")
+
+
+def exact_nls(w: Workload, t: float) -> np.ndarray:
+    """Section 8's exact Schrodinger solution e^{-it} prod_a cos(pi x_a), as (Re, Im)."""
+    g = _grids(w)
+    c = np.ones(g[0].shape)
+    for a in range(w.dim):
+        c = c * np.cos(math.pi * g[a] / w.length[a])
+    return np.stack([math.cos(t) * c, -math.sin(t) * c])
 
 
 def exact_mms(w: Workload, t: float) -> np.ndarray:
@@ -204,20 +216,39 @@ def enzyme_paper(p: int = 79, k: float = 0.05) -> Workload:
                     int(round(1.0 / k)), ic="constant", ic_args=((1.0,),))
 
 
-def cgl_2d(p: int = 400, steps: int = 2000, ic: str = "cgl_pulses", beta: float = 1.3, seed: int = 2001) -> Workload:
-    """Section 8: complex Ginzburg-Landau u_t = u + (1 + i alpha) Lap u - (1 + i beta) u |u|^2 with
-    alpha = 0 (real diffusion, D = 1 for Re u and Im u), beta = 1.3, periodic [0, 200]^2, p = 400
-    (h = 1/2), k = 1/20, T = 100 (2000 steps); Gaussian pulses, or ic="normal": N(0, 1) field."""
+def _cgl_coupling(alpha: float):
+    """D = 1 + i alpha as the 2 x 2 matrix on (Re u, Im u); None for alpha = 0 (real diffusion)."""
+    return None if alpha == 0.0 else (1.0, -alpha, alpha, 1.0)
+
+
+def cgl_2d(p: int = 400, steps: int = 2000, ic: str = "cgl_pulses", beta: float = 1.3, seed: int = 2001,
+           alpha: float = 0.0) -> Workload:
+    """Section 8: complex Ginzburg-Landau u_t = u + (1 + i alpha) Lap u - (1 + i beta) u |u|^2,
+    beta = 1.3, periodic [0, 200]^2, p = 400 (h = 1/2), k = 1/20, T = 100 (2000 steps); Gaussian
+    pulses, or ic="normal": N(0, 1) field.  alpha = 0 (the paper's runs) is real diffusion (D = 1 on
+    Re u and Im u); alpha != 0 couples them (complex line solves)."""
     ic_args = ((0.0, 0.0), 1.0) if ic == "normal" else ()
-    return Workload(f"cgl2d_{p}", (p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
-                    length=(200.0, 200.0), ic=ic, ic_args=ic_args, seed=seed)
+    name = f"cgl2d_{p}" if alpha == 0.0 else f"cgl2d_{p}_alpha{alpha:g}"
+    return Workload(name, (p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
+                    length=(200.0, 200.0), ic=ic, ic_args=ic_args, seed=seed, Dc=_cgl_coupling(alpha))
 
 
-def cgl_3d(p: int = 200, steps: int = 2000, beta: float = 1.3) -> Workload:
+def cgl_3d(p: int = 200, steps: int = 2000, beta: float = 1.3, alpha: float = 0.0) -> Workload:
     """Section 8: the same equation on periodic [0, 200]^3, p = 200 (h = 1), k = 1/20, T = 100,
     Gaussian pulses."""
-    return Workload(f"cgl3d_{p}", (p, p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
-                    length=(200.0, 200.0, 200.0), ic="cgl_pulses")
+    name = f"cgl3d_{p}" if alpha == 0.0 else f"cgl3d_{p}_alpha{alpha:g}"
+    return Workload(name, (p, p, p), PERIODIC, (1.0, 1.0), "cgl", (beta,), 0.05, steps,
+                    length=(200.0, 200.0, 200.0), ic="cgl_pulses", Dc=_cgl_coupling(alpha))
+
+
+def nls_2d(p: int = 79, k: float = 0.0125, T: float = 1.0) -> Workload:
+    """Section 8's 2D cubic Schrodinger example: i Psi_t + Lap Psi = q Psi on the unit square,
+    Neumann, q = B + C |Psi|^2, B = (1 - 2 pi^2)(1 - cos^2(pi x) cos^2(pi y)), C = 1 - 2 pi^2,
+    exact solution e^{-it} cos(pi x) cos(pi y); h = 1/78 (p = 79 nodes), k = 0.0125, T = 1.
+    As u_t = Dm Lap u + F: Dm = [[0, -1], [1, 0]] (the complex i), F = q (w, -v)."""
+    c = 1.0 - 2.0 * math.pi ** 2
+    return Workload(f"nls2d_{p}", (p, p), NEUMANN, (1.0, 1.0), "nls", (0.0, c, c), k, int(round(T / k)),
+                    ic="nls_exact", Dc=(0.0, -1.0, 1.0, 0.0))
 
 
 def brusselator_paper(p: int = 81, k: float = 0.1) -> Workload:

@@ -17,7 +17,7 @@ import oracle
 def oracle_problem(w) -> oracle.Problem:
     """oracle.Problem for a workloads.Workload."""
     return oracle.Problem(n=w.n, bc=w.bc, D=w.D, reaction=w.reaction_id, params=w.params, k=w.k,
-                          length=w.length)
+                          length=w.length, Dc=w.Dc)
 
 
 def B_p(p: int, bc: int, h: float) -> np.ndarray:

@@ -69,6 +69,36 @@ def test_create_rejects_invalid_problems(lib, kw, status):
     assert lib.etd_last_error(None)
 
 
+def _create_coupled(lib, Dm, kind=6, ns=2, n=(8, 8), bc=(2, 2)):
+    from paper_2001_11220_gb300.api import make_grid, make_reaction
+    g = make_grid(n, bc)
+    r = make_reaction(kind, ns, (1.3,))
+    Darr = (ctypes.c_double * 4)(*Dm)
+    ctx = ctypes.c_void_p()
+    return lib.etd_create_coupled(ctypes.byref(g), Darr, ctypes.byref(r), 0.05, 0, None, ctypes.byref(ctx)), ctx
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(Dm=(1.0, -0.5, 0.4, 1.0)), B.ETD_ERR_UNSUPPORTED),      # not of the form [[p, -q], [q, p]]
+    (dict(Dm=(1.0, 0.0, 0.0, 2.0)), B.ETD_ERR_UNSUPPORTED),       # diagonal but unequal
+    (dict(Dm=(-1.0, -0.5, 0.5, -1.0)), B.ETD_ERR_INVALID_ARG),    # real part p < 0
+    (dict(Dm=(1.0, float("nan"), 0.5, 1.0)), B.ETD_ERR_INVALID_ARG),
+    (dict(Dm=(1.0, -0.5, 0.5, 1.0), kind=2), B.ETD_ERR_UNSUPPORTED),  # Brusselator: not a coupled reaction
+    (dict(Dm=(1.0, -0.5, 0.5, 1.0), ns=1), B.ETD_ERR_INVALID_ARG),
+    (dict(Dm=(1.0, -0.5, 0.5, 1.0), n=(2, 8)), B.ETD_ERR_INVALID_ARG),
+])
+def test_create_coupled_rejects_before_any_device_call(lib, kw, status):
+    st, ctx = _create_coupled(lib, **kw)
+    assert st == status, lib.etd_last_error(None)
+    assert not ctx.value
+
+
+def test_schrodinger_reaction_needs_the_coupled_create(lib):
+    st, ctx = _create(lib, D=(1.0, 1.0), kind=7)
+    assert st == B.ETD_ERR_UNSUPPORTED and not ctx.value
+    assert b"coupled" in lib.etd_last_error(None)
+
+
 def test_dim_must_be_2_or_3(lib):
     g = B.etd_grid()
     g.dim = 4

@@ -37,13 +37,34 @@ def gain(r: float) -> float:
     return 1.0 / math.sqrt(1.0 - lam * lam)
 
 
+def decay_c(r: complex) -> float:
+    """|lam| of the smaller root of lam^2 - (2 + 1/r) lam + 1 = 0 for the
+    complex line matrices tridiag(-r, 1 + 2r, -r) of the coupled systems
+    (r = k (p + i q) / h^2): the roots multiply to 1, so the smaller one has
+    modulus below 1 whenever 2 + 1/r is not in [-2, 2] (Re r >= 0, r != 0)."""
+    if r == 0:
+        return 0.0
+    b = 2.0 + 1.0 / r
+    disc = np.sqrt(complex(b * b - 4.0))
+    return float(min(abs((b - disc) / 2.0), abs((b + disc) / 2.0)))
+
+
 def fp32_step_bound(w, C: float = 3.0) -> float:
     """Relative error bound (max over species of max|diff| / max|U|) of one
-    FP32 step of workload w against the FP64 oracle."""
+    FP32 step of workload w against the FP64 oracle.  Coupled workloads
+    (w.Dc = [[p, -q], [q, p]]) take the decay factor of their complex line
+    matrices, with the same count of recurrences and cancellations, and a
+    factor 2 for the four real products of each complex multiply."""
+    Dc = getattr(w, "Dc", None)
     total = 0.0
     for a in range(w.dim):
-        r = w.k * max(w.D) / w.h(a) ** 2
-        total += 2.0 * (9.0 * gain(r / 3.0) + 8.0 * gain(r / 4.0) + gain(r))
+        if Dc is None:
+            r = w.k * max(w.D) / w.h(a) ** 2
+            total += 2.0 * (9.0 * gain(r / 3.0) + 8.0 * gain(r / 4.0) + gain(r))
+        else:
+            r = w.k * complex(Dc[0], Dc[2]) / w.h(a) ** 2
+            g = [1.0 / math.sqrt(1.0 - decay_c(r / gm) ** 2) for gm in (3.0, 4.0, 1.0)]
+            total += 4.0 * (9.0 * g[0] + 8.0 * g[1] + g[2])
     return C * U_FP32 * total
 
 
