@@ -229,3 +229,37 @@ def test_nls_reaction_derivatives_fd():
         Pm = oracle.Problem(n=P.n, bc=P.bc, D=P.D, Dc=P.Dc, reaction=oracle.NLS, params=pm, k=0.1)
         fdp = (np.sum(ybar * oracle.reaction(Pp, U, 0.2)) - np.sum(ybar * oracle.reaction(Pm, U, 0.2))) / (2 * eps)
         assert abs(fdp - pbar[j]) < 1e-7 * max(1, abs(fdp)), j
+
+
+# ------------------------------------- Section 7's periodic remark: FFT solve --
+
+@pytest.mark.parametrize("p", [3, 8, 37, 256])
+@pytest.mark.parametrize("r", [0.3, 40.0, 4.0e4])
+def test_periodic_line_solve_equals_fft_diagonalisation(p, r):
+    """Section 7 notes that a periodic line matrix is circulant and is inverted by
+    the discrete Fourier transform: x = F^{-1}((F b) / (F a)), a the first column.
+    The oracle solves it by Thomas plus a Sherman-Morrison correction; both are
+    exact, so they agree to rounding (scaled by the condition number ~ 1 + 4r)."""
+    b = RNG.standard_normal(p)
+    a = np.zeros(p)
+    a[0], a[1], a[-1] = 1 + 2 * r, -r, -r
+    ref = np.real(np.fft.ifft(np.fft.fft(b) / np.fft.fft(a)))
+    got = oracle.line_solve(oracle.PERIODIC, r, b)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * (1 + 4 * r) * np.max(np.abs(ref)), (p, r)
+
+
+@pytest.mark.parametrize("Dc,d", [(rot(1.0, 0.8), 1.0 + 0.8j), (rot(0.0, 1.0), 1.0j)])
+def test_coupled_periodic_axis_solve_equals_fft(Dc, d):
+    """The coupled periodic axis solve (the oracle's 2p x 2p block LU) against the
+    FFT diagonalisation of the complex circulant I + (k/gamma) d B_p / h^2 acting
+    on u_0 + i u_1 along x."""
+    P = oracle.Problem(n=(24, 5), bc=(2, 1), D=(1.0, 1.0), Dc=Dc, k=0.3, length=(3.0, 1.0))
+    U = RNG.standard_normal(P.shape)
+    for gamma in (1.0, 3.0, 4.0):
+        rr = (P.k / gamma) * d / P.h(0) ** 2
+        a = np.zeros(24, dtype=complex)
+        a[0], a[1], a[-1] = 1 + 2 * rr, -rr, -rr
+        Z = U[0] + 1j * U[1]
+        ref = np.fft.ifft(np.fft.fft(Z, axis=1) / np.fft.fft(a)[None, :], axis=1)
+        got = oracle.axis_solve(P, 0, gamma, U)
+        assert np.max(np.abs(got[0] + 1j * got[1] - ref)) < 1e-13 * np.max(np.abs(ref))
