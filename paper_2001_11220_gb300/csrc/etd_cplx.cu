@@ -164,8 +164,13 @@ __device__ __forceinline__ C2<R> sm_sigma(const CTab<R> &T, C2<R> x0, C2<R> xp) 
   return cmk<R>((R)(ar * T.inv_x - ai * T.inv_y), (R)(ar * T.inv_y + ai * T.inv_x));
 }
 
+// Nodes per lane: c = ceil(p/32) rounded up to an odd number, so that the
+// 8- or 16-byte slot accesses of the 32 lanes (stride c entries) fall in
+// distinct shared-memory banks.
+__host__ __device__ __forceinline__ int lane_chunk(int p) { return ((p + 31) >> 5) | 1; }
+
 // One complex line solve by one warp, in place: buf = M^{-1} buf.  Lane j
-// owns nodes [j c, (j+1) c), c = ceil(p/32).
+// owns nodes [j c, (j+1) c), c = lane_chunk(p).
 // C > 0: compile-time bound on the chunk length (loops unrolled, so the table
 // and slot loads of a pass issue ahead of the recurrence); C = 0: any length.
 #define CHUNK_FWD(t, i) \
@@ -179,7 +184,7 @@ template <int C, typename R>
 __device__ __forceinline__ void solve1(const CTab<R> &T, int p, int periodic, C2<R> *buf, int lane) {
   using CT = C2<R>;
   __syncwarp();
-  const int c = (p + 31) >> 5;
+  const int c = lane_chunk(p);
   const int lo = min(p, lane * c), hi = min(p, lo + c);
   CT B = cmk<R>(0, 0);
   CHUNK_FWD(t, i) B = csub(buf[i], cmul(ldt(T.ell + i), B));
@@ -215,7 +220,7 @@ __device__ __forceinline__ void solve_pair(const CTab<R> &TA, const CTab<R> &TB,
                                            C2<R> *out, R ca, R cb, int lane) {
   using CT = C2<R>;
   __syncwarp();
-  const int c = (p + 31) >> 5;
+  const int c = lane_chunk(p);
   const int lo = min(p, lane * c), hi = min(p, lo + c);
   CT BA = cmk<R>(0, 0), BB = cmk<R>(0, 0);
   CHUNK_FWD(t, i) {
@@ -268,18 +273,6 @@ __device__ __forceinline__ void solve_pair(const CTab<R> &TA, const CTab<R> &TB,
   __syncwarp();
 }
 
-// node (l, i) of the block's lines: l-th line, i-th node along the axis
-template <bool CONTIG>
-__device__ __forceinline__ void elem_of(int idx, int p, int NL, int &l, int &i) {
-  if (CONTIG) {
-    l = idx / p;
-    i = idx - l * p;
-  } else {
-    l = idx % NL;
-    i = idx / NL;
-  }
-}
-
 template <typename R, int KIND, bool CONTIG, int C>
 __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
   using CT = C2<R>;
@@ -304,10 +297,20 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
     ok = lo0 + l < st;
     return lo0 + l + hi * st * p;
   };
+  // staging walk over the block's (line, node) pairs: along x each line's
+  // nodes are consecutive threads (one division by p); along y / z the NL (a
+  // power of two) neighbouring columns of one node row are (shifts)
+  const int lgnl = __ffs(NL) - 1;
   const int nin = KIND == SWEEP_FIRST ? 1 : 3;
   for (int idx = threadIdx.x; idx < NLp; idx += blockDim.x) {
     int l, i;
-    elem_of<CONTIG>(idx, p, NL, l, i);
+    if (CONTIG) {
+      l = idx / p;
+      i = idx - l * p;
+    } else {
+      l = idx & (NL - 1);
+      i = idx >> lgnl;
+    }
     bool ok;
     const long long g = base_of(l, ok) + i * st;
     for (int f = 0; f < nin; ++f)
@@ -349,7 +352,13 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
   const int nout = KIND == SWEEP_LAST ? 1 : 3;
   for (int idx = threadIdx.x; idx < NLp; idx += blockDim.x) {
     int l, i;
-    elem_of<CONTIG>(idx, p, NL, l, i);
+    if (CONTIG) {
+      l = idx / p;
+      i = idx - l * p;
+    } else {
+      l = idx & (NL - 1);
+      i = idx >> lgnl;
+    }
     bool ok;
     const long long g = base_of(l, ok) + i * st;
     if (!ok) continue;
@@ -441,7 +450,7 @@ etd_status build_cplx_axis(etd_ctx *ctx, Instance &I, int a) {
     D.mu = upload_c<R>(I, T.mu, err);
     if (I.bc[a] == ETD_BC_PERIODIC) D.zed = upload_c<R>(I, T.zed, err);
     // chunk products of the warp scans (lane j: nodes [j c, (j+1) c))
-    const int cc = (p + 31) / 32;
+    const int cc = lane_chunk(p);
     std::vector<cd> af(32, 1.0), ab(32, 1.0);
     for (int j = 0; j < 32; ++j)
       for (int i = j * cc; i < std::min(p, (j + 1) * cc); ++i) {
@@ -497,7 +506,7 @@ bool plan_cplx_axis(Instance &I, int a) {
     while (nl > 1 && ((st + nl - 1) / nl) * nl - st > st / 8) nl /= 2;
   X.nl = nl;
   X.nthreads = 32 * std::min(nl, 8);
-  X.chunk = (p + 31) / 32;
+  X.chunk = lane_chunk(p);
   X.smem = per_line * nl;
   if (a == 0) {
     X.nlo_blocks = 1;
