@@ -50,7 +50,7 @@ static long axis_stride(const oracle_problem *P, int a) {
 }
 
 static int check_problem(const oracle_problem *P) {
-  if (!P || (P->dim != 2 && P->dim != 3)) return -1;
+  if (!P || P->dim < 1 || P->dim > 3) return -1;
   if (P->nspecies < 1 || P->nspecies > 4) return -1;
   if (!(P->k > 0)) return -1;
   for (int a = 0; a < P->dim; ++a) {
@@ -256,6 +256,84 @@ static void coupled_line_matrix(const oracle_problem *P, int p, int bc, double r
   free(up);
 }
 
+/* 2 x 2 helpers, row-major */
+static void m2_mul(const double *A, const double *B, double *C) {
+  double c0 = A[0] * B[0] + A[1] * B[2], c1 = A[0] * B[1] + A[1] * B[3];
+  double c2 = A[2] * B[0] + A[3] * B[2], c3 = A[2] * B[1] + A[3] * B[3];
+  C[0] = c0; C[1] = c1; C[2] = c2; C[3] = c3;
+}
+static int m2_inv(const double *A, double *X) {
+  double det = A[0] * A[3] - A[1] * A[2];
+  if (det == 0.0) return -1;
+  double a0 = A[3] / det, a1 = -A[1] / det, a2 = -A[2] / det, a3 = A[0] / det;
+  X[0] = a0; X[1] = a1; X[2] = a2; X[3] = a3;
+  return 0;
+}
+
+/* The Thomas algorithm of Section 7 in 2 x 2 block form, for a coupled
+ * Dirichlet or Neumann line: blocks L_i = rr lo_i Dc, G_i = I + rr (d_i - 1) Dc,
+ * U_i = rr up_i Dc of I + rr (B (x) Dc) (lo, d, up read off line_matrix at r = 1;
+ * transpose: B^T and Dc^T).  alpha_0 = G_0^{-1} U_0, beta_0 = G_0^{-1} b_0;
+ * alpha_i = (G_i - L_i alpha_{i-1})^{-1} U_i, beta_i = (G_i - L_i alpha_{i-1})^{-1}
+ * (b_i - L_i beta_{i-1}); x_{p-1} = beta_{p-1}, x_i = beta_i - alpha_i x_{i+1}.
+ * b and x hold node i's two species at 2 i, 2 i + 1 (may alias).  Returns -1 on
+ * a singular pivot block. */
+static int block_thomas(const oracle_problem *P, int p, int bc, double rr, int transpose, const double *b,
+                        double *x) {
+  double *lo = (double *)malloc(sizeof(double) * p);
+  double *di = (double *)malloc(sizeof(double) * p);
+  double *up = (double *)malloc(sizeof(double) * p);
+  double *al = (double *)malloc(sizeof(double) * 4 * p);
+  double *be = (double *)malloc(sizeof(double) * 2 * p);
+  double tr, bl, D[4];
+  line_matrix(p, bc, 1.0, transpose, lo, di, up, &tr, &bl);
+  D[0] = P->Dc[0]; D[3] = P->Dc[3];
+  D[1] = transpose ? P->Dc[2] : P->Dc[1];
+  D[2] = transpose ? P->Dc[1] : P->Dc[2];
+  int bad = 0;
+  for (int i = 0; i < p && !bad; ++i) {
+    double G[4], L[4], Uu[4], Gi[4], r[2];
+    for (int j = 0; j < 4; ++j) {
+      G[j] = rr * (di[i] - 1.0) * D[j] + (j == 0 || j == 3 ? 1.0 : 0.0);
+      L[j] = rr * lo[i] * D[j];
+      Uu[j] = rr * up[i] * D[j];
+    }
+    r[0] = b[2 * i];
+    r[1] = b[2 * i + 1];
+    if (i > 0) {
+      double La[4];
+      m2_mul(L, al + 4 * (i - 1), La);
+      for (int j = 0; j < 4; ++j) G[j] -= La[j];
+      const double *bp = be + 2 * (i - 1);
+      r[0] -= L[0] * bp[0] + L[1] * bp[1];
+      r[1] -= L[2] * bp[0] + L[3] * bp[1];
+    }
+    if (m2_inv(G, Gi)) {
+      bad = 1;
+      break;
+    }
+    m2_mul(Gi, Uu, al + 4 * i);
+    be[2 * i] = Gi[0] * r[0] + Gi[1] * r[1];
+    be[2 * i + 1] = Gi[2] * r[0] + Gi[3] * r[1];
+  }
+  if (!bad) {
+    x[2 * (p - 1)] = be[2 * (p - 1)];
+    x[2 * (p - 1) + 1] = be[2 * (p - 1) + 1];
+    for (int i = p - 2; i >= 0; --i) {
+      const double *a = al + 4 * i;
+      double x0 = x[2 * (i + 1)], x1 = x[2 * (i + 1) + 1];
+      x[2 * i] = be[2 * i] - (a[0] * x0 + a[1] * x1);
+      x[2 * i + 1] = be[2 * i + 1] - (a[2] * x0 + a[3] * x1);
+    }
+  }
+  free(lo);
+  free(di);
+  free(up);
+  free(al);
+  free(be);
+  return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------ axis operators (Eq. Ai) -- */
 
 /* out = (I + (k/gamma) A_a)^{-1} in, one line of axis a at a time.  A_a acts
@@ -269,8 +347,35 @@ int oracle_axis_solve(const oracle_problem *P, int a, double gamma, int transpos
   long st = axis_stride(P, a);
   long nhigh = N / (st * p);
   double h = oracle_h(P, a);
+  if (P->coupled && P->bc[a] != OR_PERIODIC) {
+    /* both species of a line form one block-tridiagonal system (Section 8: D
+     * not diagonal), solved by the block Thomas algorithm */
+    const double rr = (P->k / gamma) / (h * h);
+    int bad = 0;
+#pragma omp parallel
+    {
+      double *line = (double *)malloc(sizeof(double) * 2 * p);
+#pragma omp for schedule(static) reduction(| : bad)
+      for (long q = 0; q < nhigh * st; ++q) {
+        long hi = q / st, lo = q % st;
+        long base = lo + hi * st * p;
+        for (int i = 0; i < p; ++i) {
+          line[2 * i] = in[base + i * st];
+          line[2 * i + 1] = in[N + base + i * st];
+        }
+        bad |= block_thomas(P, p, P->bc[a], rr, transpose, line, line) != 0;
+        for (int i = 0; i < p; ++i) {
+          out[base + i * st] = line[2 * i];
+          out[N + base + i * st] = line[2 * i + 1];
+        }
+      }
+      free(line);
+    }
+    return bad ? -1 : 0;
+  }
   if (P->coupled) {
-    /* both species of a line form one system (Section 8: D not diagonal) */
+    /* periodic: both species of a line form one cyclic block system, solved
+     * by dense LU (formed once per call) */
     const int m = 2 * p;
     double *LU = (double *)malloc(sizeof(double) * (size_t)m * m);
     int *piv = (int *)malloc(sizeof(int) * m);

@@ -14,8 +14,11 @@
  *   - the coupled two-species form of Section 8 (complex Ginzburg-Landau
  *     with D = 1 + i alpha, the cubic Schrodinger equation with a
  *     non-diagonal D): a full 2 x 2 diffusion matrix, whose line systems
- *     I + (k/gamma)/h^2 (B_p (x) D) are solved as one 2p x 2p system per
- *     line (dense LU with partial pivoting, formed once per axis and pole);
+ *     I + (k/gamma)/h^2 (B_p (x) D) are solved as one system per line: the
+ *     Thomas algorithm in 2 x 2 block form (Dirichlet, Neumann), dense LU
+ *     with partial pivoting of the 2p x 2p matrix (periodic);
+ *   - d = 1 as well as 2 and 3 (the frame with no splitting: the last-axis
+ *     step alone);
  *   - the 1D matrices B_p of Section 3, Example 1 and the Kronecker operator
  *     A_i of Eq. (Ai), applied line by line;
  *   - the fully discrete ETD-RDP-IF scheme of the framed box in Section 6
@@ -56,7 +59,7 @@ enum {
 };
 
 typedef struct {
-  int dim;           /* 2 or 3 */
+  int dim;           /* 1, 2 or 3 */
   int n[3];          /* p_a: grid nodes per axis (paper convention per boundary type) */
   double length[3];  /* domain length per axis */
   int bc[3];         /* OR_DIRICHLET / OR_NEUMANN / OR_PERIODIC per axis */

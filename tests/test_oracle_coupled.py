@@ -263,3 +263,64 @@ def test_coupled_periodic_axis_solve_equals_fft(Dc, d):
         ref = np.fft.ifft(np.fft.fft(Z, axis=1) / np.fft.fft(a)[None, :], axis=1)
         got = oracle.axis_solve(P, 0, gamma, U)
         assert np.max(np.abs(got[0] + 1j * got[1] - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+# ------------------------------------------- Section 8, 1D Schrodinger soliton --
+
+NLS1D_A, NLS1D_C, NLS1D_H, NLS1D_K, NLS1D_T = 0.01, 0.1, 0.5, 0.01, 108.0
+
+
+def nls1d_golden():
+    """The printed mass and energy values (tests/golden/nls1d_soliton.txt)."""
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "nls1d_soliton.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                q, t, v = line.split()
+                out[(q, int(t))] = float(v)
+    return out
+
+
+def nls1d_problem():
+    """i Psi_t + Psi_xx + |Psi|^2 Psi = 0: D = i (reading of Section 8), F = q J u with
+    q = -|u|^2 (p1 = -1); 361 Neumann nodes on a line of length 180."""
+    return oracle.Problem(n=(361,), bc=(oracle.NEUMANN,), D=(1.0, 1.0), Dc=rot(0.0, 1.0), reaction=oracle.NLS,
+                          params=(0.0, -1.0, 0.0), k=NLS1D_K, length=(180.0,))
+
+
+def nls1d_initial():
+    x = -80.0 + NLS1D_H * np.arange(361)
+    a, c = NLS1D_A, NLS1D_C
+    psi = math.sqrt(2 * a) * np.exp(1j * c * x / 2) / np.cosh(math.sqrt(a) * x)
+    return cplx_state(psi)
+
+
+def nls1d_mass(U):
+    m = U[0] ** 2 + U[1] ** 2
+    return NLS1D_H / 2 * (m[0] + 2 * m[1:-1].sum() + m[-1])
+
+
+def nls1d_energy(U):
+    z = U[0] + 1j * U[1]
+    m2 = np.abs(z) ** 4
+    dz = (z[2:] - z[:-2]) / (2 * NLS1D_H)
+    return NLS1D_H / 2 * (-0.5 * (m2[0] + m2[-1]) + 2 * np.sum(np.abs(dz) ** 2 - 0.5 * m2[1:-1]))
+
+
+def test_nls_1d_soliton_mass_and_energy_match_the_paper():
+    """Section 8's 1D run (10800 steps of the unsplit frame, d = 1): the initial mass and
+    energy reproduce the printed digits (grid and initial state), and after T = 108
+    the energy matches the printed value to 1e-12 (its drift of -8.43e-9 to 0.01 %)
+    and the mass stays within 5e-11 of the printed value (conserved to ~1e-10 by both
+    runs; the remaining difference is rounding over 10800 steps)."""
+    g = nls1d_golden()
+    U0 = nls1d_initial()
+    # printed to 15 decimals: agreement to half a unit of the last printed digit
+    assert abs(nls1d_mass(U0) - g[("M", 0)]) <= 5e-16
+    assert abs(nls1d_energy(U0) - g[("E", 0)]) <= 5e-16
+    U = oracle.run(nls1d_problem(), U0, 0.0, int(round(NLS1D_T / NLS1D_K)))
+    assert abs(nls1d_energy(U) - g[("E", 108)]) < 1e-12, nls1d_energy(U)
+    drift, printed = nls1d_energy(U) - nls1d_energy(U0), g[("E", 108)] - g[("E", 0)]
+    assert abs(drift - printed) < 1e-4 * abs(printed), (drift, printed)
+    assert abs(nls1d_mass(U) - g[("M", 108)]) < 5e-11, nls1d_mass(U)
