@@ -406,6 +406,21 @@ def extra_workloads(EtdRdpIf, W, stream, world, rank, barrier, peak, include_fp6
                                     "per_sweep": per}
         c.close()
         del U
+    # Section 8's 1D Schrodinger soliton (d = 1, one fused sweep per step): the whole run, 10800
+    # steps of 361 Neumann nodes in FP64, replayed from one graph
+    import math
+    import numpy as np
+    x = -80.0 + 0.5 * np.arange(361)
+    psi = math.sqrt(0.02) * np.exp(0.05j * x) / np.cosh(0.1 * x)
+    with torch.cuda.stream(stream):
+        c = EtdRdpIf((361,), (W.NEUMANN,), (1.0, 1.0), "nls", (0.0, -1.0, 0.0), 0.01, "fp64", (180.0,),
+                     stream=stream, Dc=(0.0, -1.0, 1.0, 0.0))
+        U = torch.tensor(np.stack([psi.real, psi.imag]), device="cuda", dtype=torch.float64)
+    ms = _timed(lambda: c.run(U, 0.0, 10800), stream, reps=2)
+    out["nls1d_361_fp64"] = {"value": 361 * 2 * 10800 / (ms / 1e3), "unit": UNIT, "us_per_step": ms * 1e3 / 10800,
+                             "full_run_s": ms / 1e3, "steps_full_run": 10800,
+                             "note": "one 361-node line: a single warp, latency-bound"}
+    c.close()
     return out
 
 

@@ -157,7 +157,9 @@ etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction 
  * another Dm; ETD_ERR_INVALID_ARG for a non-finite Dm or p < 0, and for the
  * grid / k / precision checks of etd_create).  Lines longer than about
  * 3200 nodes (FP64) / 6400 (FP32) do not fit the kernel's shared memory:
- * ETD_ERR_UNSUPPORTED.  The context takes etd_step, etd_run, etd_run_host,
+ * ETD_ERR_UNSUPPORTED.  grid->dim may also be 1 here (one line, the frame
+ * without splitting, as in the paper's 1D Schrodinger run; n[0] and
+ * length[0] as for the other axes).  The context takes etd_step, etd_run, etd_run_host,
  * etd_profile*, etd_get_info (staged = 6) and etd_destroy; the adjoint and
  * gradient calls and etd_autotune return ETD_ERR_UNSUPPORTED. */
 etd_status etd_create_coupled(const etd_grid *grid, const double *Dm, const etd_reaction *reaction,

@@ -46,6 +46,11 @@ namespace {
 
 using namespace etd;
 
+// d = 1: the frame without splitting, one sweep that loads U_n, forms F(U_n)
+// and w* = U_n + k F, and continues as the last-axis sweep with c_U = U_n,
+// c_f = F(U_n)
+constexpr int CPLX_ONLY = 3;
+
 template <typename R> struct C2 { R x, y; };
 
 template <typename R> __device__ __forceinline__ C2<R> cmk(R x, R y) { return C2<R>{x, y}; }
@@ -114,7 +119,8 @@ __device__ __forceinline__ C2<R> reaction_c(const CplxArgs<R> &A, C2<R> u, long 
       R q = A.rp[0] + A.rp[1] * (u.x * u.x + u.y * u.y);
       if (A.cos2[0]) {
         const long long ix = g % A.nx, iy = (g / A.nx) % A.ny, iz = g / (A.nx * A.ny);
-        R c = A.cos2[0][ix] * A.cos2[1][iy];
+        R c = A.cos2[0][ix];
+        if (A.dim >= 2) c *= A.cos2[1][iy];
         if (A.dim == 3) c *= A.cos2[2][iz];
         q += A.rp[2] * (R(1) - c);
       }
@@ -301,7 +307,9 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
   // nodes are consecutive threads (one division by p); along y / z the NL (a
   // power of two) neighbouring columns of one node row are (shifts)
   const int lgnl = __ffs(NL) - 1;
-  const int nin = KIND == SWEEP_FIRST ? 1 : 3;
+  constexpr bool LOADS_U = KIND == SWEEP_FIRST || KIND == CPLX_ONLY;
+  constexpr bool ENDS_STEP = KIND == SWEEP_LAST || KIND == CPLX_ONLY;
+  const int nin = LOADS_U ? 1 : 3;
   for (int idx = threadIdx.x; idx < NLp; idx += blockDim.x) {
     int l, i;
     if (CONTIG) {
@@ -315,7 +323,7 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
     const long long g = base_of(l, ok) + i * st;
     for (int f = 0; f < nin; ++f)
       slot[f * NLp + l * p + i] = ok ? cmk<R>(A.in[f][g], A.in[f][g + N]) : cmk<R>(0, 0);
-    if (KIND == SWEEP_FIRST) {
+    if (LOADS_U) {
       // f0 = F(U_n) into slot 1, w* = U_n + k f0 into slot 2
       const CT u = slot[l * p + i];
       const CT f0 = ok ? reaction_c(A, u, g) : cmk<R>(0, 0);
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
     const long long base = base_of(l, ok);
     if (!ok) continue;
     CT *s0 = slot + l * p, *s1 = s0 + NLp, *s2 = s1 + NLp, *s3 = s2 + NLp;
-    if (KIND == SWEEP_LAST) {
+    if (ENDS_STEP) {
       solve1<C>(A.tab[0], p, A.periodic, s2, lane);  // U* = P w
       for (int i = lane; i < p; i += 32) {
         const CT fs = reaction_c(A, s2[i], base + i * st);
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
     __syncwarp();
   }
   __syncthreads();
-  const int nout = KIND == SWEEP_LAST ? 1 : 3;
+  const int nout = ENDS_STEP ? 1 : 3;
   for (int idx = threadIdx.x; idx < NLp; idx += blockDim.x) {
     int l, i;
     if (CONTIG) {
@@ -363,7 +371,7 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
     const long long g = base_of(l, ok) + i * st;
     if (!ok) continue;
     for (int f = 0; f < nout; ++f) {
-      const CT v = slot[(KIND == SWEEP_LAST ? 3 : f) * NLp + l * p + i];
+      const CT v = slot[(ENDS_STEP ? 3 : f) * NLp + l * p + i];
       A.out[f][g] = v.x;
       A.out[f][g + N] = v.y;
     }
@@ -541,6 +549,7 @@ cudaError_t set_cplx_attrs() {
   cudaError_t e = set_cplx_smem_attr<R, SWEEP_FIRST, true>();
   if (e == cudaSuccess) e = set_cplx_smem_attr<R, SWEEP_MIDDLE, false>();
   if (e == cudaSuccess) e = set_cplx_smem_attr<R, SWEEP_LAST, false>();
+  if (e == cudaSuccess) e = set_cplx_smem_attr<R, CPLX_ONLY, true>();
   return e;
 }
 
@@ -561,9 +570,12 @@ cudaError_t cplx_step_t(const Instance &I, R *U, double t, cudaStream_t s, etd_c
   R *cu = (R *)I.scratch[0], *cf = (R *)I.scratch[1], *w = (R *)I.scratch[2];
   for (int a = 0; a < I.dim; ++a) {
     const CplxAxis &X = I.cax[a];
-    const int kind = a == 0 ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
+    const int kind = I.dim == 1 ? CPLX_ONLY : a == 0 ? SWEEP_FIRST : (a == I.dim - 1 ? SWEEP_LAST : SWEEP_MIDDLE);
     CplxArgs<R> A{};
-    if (kind == SWEEP_FIRST) {
+    if (kind == CPLX_ONLY) {
+      A.in[0] = U;
+      A.out[0] = U;
+    } else if (kind == SWEEP_FIRST) {
       A.in[0] = U;
       A.out[0] = cu; A.out[1] = cf; A.out[2] = w;
     } else if (kind == SWEEP_MIDDLE) {
@@ -590,7 +602,8 @@ cudaError_t cplx_step_t(const Instance &I, R *U, double t, cudaStream_t s, etd_c
                          (const C2<R> *)D.af, (const C2<R> *)D.ab, D.vl[0], D.vl[1], D.inv[0], D.inv[1]};
     }
     for (int b = 0; b < 3; ++b) A.cos2[b] = (const R *)I.cax[b].cos2;
-    if (!A.cos2[0] || !A.cos2[1] || (I.dim == 3 && !A.cos2[2])) A.cos2[0] = nullptr;
+    for (int b = 0; b < I.dim; ++b)
+      if (!A.cos2[b]) A.cos2[0] = nullptr;  // no position term
     A.dim = I.dim;
     A.rkind = I.rkind;
     A.k = (R)I.k;
@@ -598,12 +611,13 @@ cudaError_t cplx_step_t(const Instance &I, R *U, double t, cudaStream_t s, etd_c
     cudaEvent_t ev0;
     cudaError_t e = prof_begin(prof, s, ev0);
     if (e != cudaSuccess) return e;
-    if (kind == SWEEP_FIRST) launch_cplx<R, SWEEP_FIRST, true>(A, X, s);
+    if (kind == CPLX_ONLY) launch_cplx<R, CPLX_ONLY, true>(A, X, s);
+    else if (kind == SWEEP_FIRST) launch_cplx<R, SWEEP_FIRST, true>(A, X, s);
     else if (kind == SWEEP_MIDDLE) launch_cplx<R, SWEEP_MIDDLE, false>(A, X, s);
     else launch_cplx<R, SWEEP_LAST, false>(A, X, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = prof_end(prof, s, kind, ev0);
+    e = prof_end(prof, s, kind == CPLX_ONLY ? SWEEP_LAST : kind, ev0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -635,11 +649,19 @@ extern "C" etd_status etd_create_coupled(const etd_grid *grid, const double *Dm,
   if (kind != ETD_REACTION_ZERO && kind != ETD_REACTION_LINEAR && kind != ETD_REACTION_CGL &&
       kind != ETD_REACTION_NLS)
     return fail(nullptr, ETD_ERR_UNSUPPORTED, "coupled diffusion takes the ZERO, LINEAR, CGL or NLS reaction");
-  // grid, k, precision and parameters as for etd_create
+  // grid, k, precision and parameters as for etd_create; d = 1 is taken here
+  // too (one line: the frame without splitting)
   etd_reaction rz = *reaction;
   rz.kind = ETD_REACTION_ZERO;
   const double Dd[2] = {Dm[0], Dm[0]};
-  etd_status st = validate_problem(grid, Dd, &rz, k, precision);
+  etd_grid g2 = *grid;
+  if (grid->dim == 1) {  // validate axis 0 inside a 2D grid with a minimal second axis
+    g2.dim = 2;
+    g2.n[1] = 3;
+    g2.bc[1] = ETD_BC_NEUMANN;
+    g2.length[1] = 1.0;
+  }
+  etd_status st = validate_problem(&g2, Dd, &rz, k, precision);
   if (st != ETD_OK) return st;
   etd_ctx *ctx = new (std::nothrow) etd_ctx();
   if (!ctx) return fail(nullptr, ETD_ERR_OOM, "host allocation failed");

@@ -86,6 +86,7 @@ def _create_coupled(lib, Dm, kind=6, ns=2, n=(8, 8), bc=(2, 2)):
     (dict(Dm=(1.0, -0.5, 0.5, 1.0), kind=2), B.ETD_ERR_UNSUPPORTED),  # Brusselator: not a coupled reaction
     (dict(Dm=(1.0, -0.5, 0.5, 1.0), ns=1), B.ETD_ERR_INVALID_ARG),
     (dict(Dm=(1.0, -0.5, 0.5, 1.0), n=(2, 8)), B.ETD_ERR_INVALID_ARG),
+    (dict(Dm=(0.0, -1.0, 1.0, 0.0), n=(2,), bc=(1,)), B.ETD_ERR_INVALID_ARG),  # d = 1 line of 2 nodes
 ])
 def test_create_coupled_rejects_before_any_device_call(lib, kw, status):
     st, ctx = _create_coupled(lib, **kw)

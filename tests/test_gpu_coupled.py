@@ -152,3 +152,29 @@ def test_coupled_rejections():
         ctx.autotune(U.clone())
     assert ei.value.status == B.ETD_ERR_UNSUPPORTED
     ctx.close()
+
+
+def test_schrodinger_1d_soliton_matches_the_paper_and_the_oracle():
+    """Section 8's 1D run on the GPU (d = 1: one fused sweep per step, FP64, 10800 steps):
+    the state matches the oracle, and the energy at T = 108 matches the printed value
+    to 1e-12, the mass to 5e-11 (the oracle's golden pin, tests/golden/nls1d_soliton.txt)."""
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    from tests import test_oracle_coupled as C
+    g = C.nls1d_golden()
+    U0 = C.nls1d_initial()
+    nsteps = int(round(C.NLS1D_T / C.NLS1D_K))
+    ctx = EtdRdpIf((361,), (W.NEUMANN,), (1.0, 1.0), "nls", (0.0, -1.0, 0.0), C.NLS1D_K, "fp64", (180.0,),
+                   Dc=(0.0, -1.0, 1.0, 0.0))
+    U = torch.tensor(U0, device="cuda", dtype=torch.float64)
+    ctx.run(U, 0.0, nsteps)
+    torch.cuda.synchronize()
+    info = ctx.info()
+    ctx.close()
+    got = U.cpu().numpy()
+    ref = oracle.run(C.nls1d_problem(), U0, 0.0, nsteps)
+    e = rel_err(got, ref)
+    print(f"nls1d 10800 steps: gpu vs oracle {e:.2e}, E {C.nls1d_energy(got):.15f}, M {C.nls1d_mass(got):.15f}")
+    assert info["launches_per_step"] == 1 and info["staged"][0] == 6
+    assert e <= 1e-10
+    assert abs(C.nls1d_energy(got) - g[("E", 108)]) < 1e-12
+    assert abs(C.nls1d_mass(got) - g[("M", 108)]) < 5e-11
