@@ -64,9 +64,13 @@ CASES = [
           (0.0, NLS_C, NLS_C), k=0.002, ic="nls_exact"),
     # linear reaction, Dirichlet, general p + i q; lines shorter than a warp (p = 5 < 32)
     ccase("lin_dir_2d", (5, 41), W.DIRICHLET, (0.3, -0.5, 0.5, 0.3), "linear", (-0.4, 0.1), k=0.02),
-    # long x lines: several nodes per lane (300 nodes: 10 per lane), 10 FP64 lines per block
+    # long x lines: several nodes per lane (300 nodes: 10 per lane, 11 after rounding to odd)
     ccase("cgl_long_x", (300, 9), (W.PERIODIC, W.NEUMANN), (1.0, 0.5, -0.5, 1.0), "cgl", (0.7,), k=0.05,
           length=(150.0, 4.5)),
+    # lines past the unrolled chunk bounds (1500 and 700 nodes: 47 and 23 per lane, runtime loops),
+    # Neumann x, Dirichlet y
+    ccase("nls_runtime_chunks", (1500, 700), (W.NEUMANN, W.DIRICHLET), (0.0, -1.0, 1.0, 0.0), "nls",
+          (0.2, -1.0, 0.0), k=0.01, length=(30.0, 14.0)),
 ]
 
 
