@@ -229,6 +229,16 @@ etd_status etd_batch_create(int32_t ninst, const etd_grid *grids, const double *
                             void *stream, etd_ctx **out);
 etd_status etd_batch_run(etd_ctx *ctx, void *const *U, double t0, int64_t nsteps);
 
+/* Non-finite detection: scans the state U (device, layout above, the
+ * context's precision) for NaN or infinity on the context's stream and
+ * synchronises.  Returns ETD_OK, or ETD_ERR_NONFINITE with *first_bad (may be
+ * NULL) set to the smallest flat element index s N + point that is not finite
+ * (-1 when all are finite); ETD_ERR_INVALID_ARG for a NULL ctx or U or a
+ * batched context.  A run that diverges (k too large for an explicit
+ * reaction term, a blow-up of the model itself) is caught by calling this on
+ * its result. */
+etd_status etd_check_finite(etd_ctx *ctx, const void *U, int64_t *first_bad);
+
 /* Limit of each dependency wait of the persistent ensemble step, in seconds
  * (default 1; (0, 60]).  ETD_ERR_INVALID_ARG on a single-problem context or
  * a limit outside the range. */

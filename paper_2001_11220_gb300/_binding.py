@@ -20,7 +20,7 @@ ETD_FP64, ETD_FP32 = 0, 1
 # every symbol include/etdrdpif.h declares
 EXPORTS = ["etd_create", "etd_create_coupled", "etd_step", "etd_run", "etd_run_host", "etd_step_adjoint", "etd_grad", "etd_run_vjp",
            "etd_batch_create", "etd_batch_run", "etd_batch_autotune", "etd_batch_set_wait_limit",
-           "etd_batch_debug_hold", "etd_autotune", "etd_set_stream", "etd_profile",
+           "etd_batch_debug_hold", "etd_check_finite", "etd_autotune", "etd_set_stream", "etd_profile",
            "etd_profile_read", "etd_get_info", "etd_step_noalloc",
            "etd_last_error", "etd_destroy"]
 
@@ -67,6 +67,7 @@ def load() -> ctypes.CDLL:
         "etd_create_coupled": ([ctypes.POINTER(etd_grid), dptr, ctypes.POINTER(etd_reaction), dbl, i32, vp, pp],
                                i32),
         "etd_step": ([vp, vp, dbl], i32),
+        "etd_check_finite": ([vp, vp, ctypes.POINTER(i64)], i32),
         "etd_run": ([vp, vp, dbl, i64], i32),
         "etd_run_host": ([vp, vp, dbl, i64], i32),
         "etd_step_adjoint": ([vp, vp, dbl, vp, vp, dptr, dptr], i32),

@@ -150,6 +150,16 @@ class EtdRdpIf:
         B.check(self.lib.etd_profile_read(self.ctx, ms, ln), self.ctx)
         return list(ms), list(ln)
 
+    def check_finite(self, U: torch.Tensor) -> int:
+        """-1 if every element of U is finite, else the smallest flat index of a
+        NaN / infinity (etd_check_finite returns ETD_ERR_NONFINITE there)."""
+        self._check_state(U)
+        first = ctypes.c_int64(-1)
+        st = self.lib.etd_check_finite(self.ctx, ctypes.c_void_p(U.data_ptr()), ctypes.byref(first))
+        if st not in (B.ETD_OK, B.ETD_ERR_NONFINITE):
+            B.check(st, self.ctx)
+        return int(first.value)
+
     def info(self) -> dict:
         inf = B.etd_info()
         B.check(self.lib.etd_get_info(self.ctx, ctypes.byref(inf)), self.ctx)

@@ -138,6 +138,7 @@ struct etd_ctx {
   std::string err = "no error";
   void *host_state = nullptr;           // device copy used by etd_run_host
   std::vector<void *> owned;            // context-level device buffers
+  void *finite_word = nullptr;          // etd_check_finite: smallest non-finite index (owned)
   std::list<std::pair<etd::GraphKey, cudaGraphExec_t>> graphs;  // captured multi-step runs
   // batched launch data: per axis, SweepArgs<R>[ninst] and block prefix sums on the device
   void *batch_args[3] = {nullptr, nullptr, nullptr};
