@@ -208,3 +208,17 @@ def test_cgl_alpha_full_size_plane_wave_follows_scalar_recurrence(prec):
     assert info["staged"] == [6, 6, 6]
     assert err <= tol
     assert abs(an - a0) > 1e-3
+
+
+def test_coupled_host_buffer_run_equals_device_run():
+    """etd_run_host (host state, copies inside the call) on a coupled context gives the
+    same bits as etd_run on a device state."""
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    w = CASES[0]
+    U0 = W.initial_state(w)
+    dev, _ = gpu_run(w, U0, 3)
+    ctx = EtdRdpIf.from_workload(w, "fp64")
+    H = torch.tensor(U0, dtype=torch.float64).pin_memory()
+    ctx.run_host(H, 0.0, 3)
+    ctx.close()
+    assert np.array_equal(H.numpy(), dev)
