@@ -71,6 +71,12 @@ CASES = [
     # Neumann x, Dirichlet y
     ccase("nls_runtime_chunks", (1500, 700), (W.NEUMANN, W.DIRICHLET), (0.0, -1.0, 1.0, 0.0), "nls",
           (0.2, -1.0, 0.0), k=0.01, length=(30.0, 14.0)),
+    # d = 1 (one fused sweep per step): a periodic line (Sherman-Morrison) and a Dirichlet one
+    ccase("cgl_1d_per", (77,), (W.PERIODIC,), (1.0, -0.8, 0.8, 1.0), "cgl", (1.3,), k=0.05, length=(38.5,)),
+    ccase("lin_1d_dir", (45,), (W.DIRICHLET,), (0.3, -0.5, 0.5, 0.3), "linear", (-0.4, 0.1), k=0.02),
+    # the longest FP64 line the kernel's shared memory takes (3000 nodes: one line per block)
+    ccase("nls_max_line", (3000, 3), (W.NEUMANN, W.NEUMANN), (0.0, -1.0, 1.0, 0.0), "nls", (0.2, -1.0, 0.0),
+          k=0.01, length=(60.0, 1.0)),
 ]
 
 
@@ -222,3 +228,17 @@ def test_coupled_host_buffer_run_equals_device_run():
     ctx.run_host(H, 0.0, 3)
     ctx.close()
     assert np.array_equal(H.numpy(), dev)
+
+
+def test_line_too_long_for_shared_memory_is_unsupported():
+    """A 4000-node FP64 line (4 complex slots: 256 KB) exceeds the kernel's shared
+    memory: etd_create_coupled returns ETD_ERR_UNSUPPORTED and allocates nothing."""
+    from paper_2001_11220_gb300 import _binding as B
+    from paper_2001_11220_gb300.api import EtdRdpIf
+    with pytest.raises(B.EtdError) as ei:
+        EtdRdpIf((4000, 3), (W.NEUMANN, W.NEUMANN), (1.0, 1.0), "nls", (0.0, -1.0, 0.0), 0.01, "fp64",
+                 Dc=(0.0, -1.0, 1.0, 0.0))
+    assert ei.value.status == B.ETD_ERR_UNSUPPORTED
+    ctx = EtdRdpIf((4000, 3), (W.NEUMANN, W.NEUMANN), (1.0, 1.0), "nls", (0.0, -1.0, 0.0), 0.01, "fp32",
+                   Dc=(0.0, -1.0, 1.0, 0.0))   # FP32 slots are half the size: fits
+    ctx.close()
