@@ -85,6 +85,9 @@ template <typename R> struct CTab {
   const C2<R> *ell, *ipv, *mu, *zed;
   const C2<R> *af, *ab;  // [32] per-lane chunk products of -l_i and of -mu_i
   double vl_x, vl_y, inv_x, inv_y;
+  // periodic lines: circulant factorisation alpha (I - lam E)(I - lam E^-1)
+  const C2<R> *cpre, *csuf, *cchunk;  // [32] lam^(before lane), lam^(after lane), lam^(lane's nodes)
+  C2<R> lam, ialpha, inv1m;           // lam, 1/alpha, 1/(1 - lam^p)
 };
 
 template <typename R> struct CplxArgs {
@@ -175,8 +178,6 @@ __device__ __forceinline__ C2<R> sm_sigma(const CTab<R> &T, C2<R> x0, C2<R> xp) 
 // distinct shared-memory banks.
 __host__ __device__ __forceinline__ int lane_chunk(int p) { return ((p + 31) >> 5) | 1; }
 
-// One complex line solve by one warp, in place: buf = M^{-1} buf.  Lane j
-// owns nodes [j c, (j+1) c), c = lane_chunk(p).
 // C > 0: compile-time bound on the chunk length (loops unrolled, so the table
 // and slot loads of a pass issue ahead of the recurrence); C = 0: any length.
 #define CHUNK_FWD(t, i) \
@@ -186,9 +187,109 @@ __host__ __device__ __forceinline__ int lane_chunk(int p) { return ((p + 31) >> 
   _Pragma("unroll") for (int t = (C ? C : c) - 1; t >= 0; --t) \
     if (const int i = lo + t; i < hi)
 
+// Periodic lines on the circulant factorisation M = alpha (I - lam E)(I - lam E^-1)
+// (E the cyclic shift, |lam| < 1): M^{-1} b = (1/alpha) z with y_i = b_i + lam y_{i-1}
+// and z_i = y_i + lam z_{i+1}, indices cyclic.  Each lane reduces its chunk with a zero
+// carry; a warp scan gives the zero-carry prefix and the line's total, and the cyclic
+// carry closes it: y_{p-1} = total / (1 - lam^p), so the value entering lane j is
+// prefix_j + lam^(nodes before lane j) y_{p-1}; backwards likewise with z_0.
+template <typename R>
+__device__ __forceinline__ void circ_scan_fwd(C2<R> A, C2<R> B, int lane, C2<R> &ex, C2<R> &tot) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const C2<R> Ap = shfl_up_c(A, off), Bp = shfl_up_c(B, off);
+    if (lane >= off) {
+      B = cadd(cmul(A, Bp), B);
+      A = cmul(A, Ap);
+    }
+  }
+  tot = shfl_c(B, 31);
+  ex = shfl_up_c(B, 1);
+  if (lane == 0) ex = cmk<R>(0, 0);
+}
+template <typename R>
+__device__ __forceinline__ void circ_scan_bwd(C2<R> A, C2<R> B, int lane, C2<R> &ex, C2<R> &tot) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const C2<R> An = shfl_down_c(A, off), Bn = shfl_down_c(B, off);
+    if (lane + off < 32) {
+      B = cadd(cmul(A, Bn), B);
+      A = cmul(A, An);
+    }
+  }
+  tot = shfl_c(B, 0);
+  ex = shfl_down_c(B, 1);
+  if (lane == 31) ex = cmk<R>(0, 0);
+}
+
+// out = ca MA^{-1} srcA + cb MB^{-1} srcB on periodic lines (one chain when NCH = 1:
+// out = MA^{-1} srcA, cb and the B arguments unused); st* hold the first recurrence
+template <int C, int NCH, typename R>
+__device__ __forceinline__ void circ_solve(const CTab<R> &TA, const CTab<R> &TB, int p, const C2<R> *srcA,
+                                           C2<R> *stA, const C2<R> *srcB, C2<R> *stB, C2<R> *out, R ca, R cb,
+                                           int lane) {
+  using CT = C2<R>;
+  __syncwarp();
+  const int c = lane_chunk(p);
+  const int lo = min(p, lane * c), hi = min(p, lo + c);
+  const CT lA = TA.lam, lB = TB.lam;
+  CT BA = cmk<R>(0, 0), BB = cmk<R>(0, 0);
+  CHUNK_FWD(t, i) {
+    BA = cadd(srcA[i], cmul(lA, BA));
+    if (NCH == 2) BB = cadd(srcB[i], cmul(lB, BB));
+  }
+  CT ex, tot, yA, yB = cmk<R>(0, 0);
+  circ_scan_fwd(ldt(TA.cchunk + lane), BA, lane, ex, tot);
+  yA = cadd(ex, cmul(ldt(TA.cpre + lane), cmul(tot, TA.inv1m)));
+  if (NCH == 2) {
+    circ_scan_fwd(ldt(TB.cchunk + lane), BB, lane, ex, tot);
+    yB = cadd(ex, cmul(ldt(TB.cpre + lane), cmul(tot, TB.inv1m)));
+  }
+  CHUNK_FWD(t, i) {
+    const CT a = srcA[i];
+    const CT b = NCH == 2 ? srcB[i] : a;
+    yA = cadd(a, cmul(lA, yA));
+    stA[i] = yA;
+    if (NCH == 2) {
+      yB = cadd(b, cmul(lB, yB));
+      stB[i] = yB;
+    }
+  }
+  BA = cmk<R>(0, 0);
+  BB = cmk<R>(0, 0);
+  CHUNK_BWD(t, i) {
+    BA = cadd(stA[i], cmul(lA, BA));
+    if (NCH == 2) BB = cadd(stB[i], cmul(lB, BB));
+  }
+  CT zA, zB = cmk<R>(0, 0);
+  circ_scan_bwd(ldt(TA.cchunk + lane), BA, lane, ex, tot);
+  zA = cadd(ex, cmul(ldt(TA.csuf + lane), cmul(tot, TA.inv1m)));
+  if (NCH == 2) {
+    circ_scan_bwd(ldt(TB.cchunk + lane), BB, lane, ex, tot);
+    zB = cadd(ex, cmul(ldt(TB.csuf + lane), cmul(tot, TB.inv1m)));
+  }
+  const CT sA = cscale(ca, TA.ialpha), sB = cscale(cb, TB.ialpha);
+  CHUNK_BWD(t, i) {
+    zA = cadd(stA[i], cmul(lA, zA));
+    if (NCH == 2) {
+      zB = cadd(stB[i], cmul(lB, zB));
+      out[i] = cadd(cmul(sA, zA), cmul(sB, zB));
+    } else {
+      out[i] = cmul(sA, zA);
+    }
+  }
+  __syncwarp();
+}
+
+// One complex line solve by one warp, in place: buf = M^{-1} buf.  Lane j
+// owns nodes [j c, (j+1) c), c = lane_chunk(p).
 template <int C, typename R>
 __device__ __forceinline__ void solve1(const CTab<R> &T, int p, int periodic, C2<R> *buf, int lane) {
   using CT = C2<R>;
+  if (periodic) {
+    circ_solve<C, 1>(T, T, p, buf, buf, buf, buf, buf, R(1), R(0), lane);
+    return;
+  }
   __syncwarp();
   const int c = lane_chunk(p);
   const int lo = min(p, lane * c), hi = min(p, lo + c);
@@ -225,6 +326,10 @@ __device__ __forceinline__ void solve_pair(const CTab<R> &TA, const CTab<R> &TB,
                                            const C2<R> *srcA, C2<R> *stA, const C2<R> *srcB, C2<R> *stB,
                                            C2<R> *out, R ca, R cb, int lane) {
   using CT = C2<R>;
+  if (periodic) {
+    circ_solve<C, 2>(TA, TB, p, srcA, stA, srcB, stB, out, ca, cb, lane);
+    return;
+  }
   __syncwarp();
   const int c = lane_chunk(p);
   const int lo = min(p, lane * c), hi = min(p, lo + c);
@@ -467,6 +572,34 @@ etd_status build_cplx_axis(etd_ctx *ctx, Instance &I, int a) {
       }
     D.af = upload_c<R>(I, af, err);
     D.ab = upload_c<R>(I, ab, err);
+    if (I.bc[a] == ETD_BC_PERIODIC) {
+      // circulant factorisation of the cyclic line matrix (1 + 2c) I - c (E + E^-1):
+      // alpha (1 + lam^2) = 1 + 2c, alpha lam = c, i.e. lam + 1/lam = 2 + 1/c, |lam| < 1.
+      // The two roots multiply to 1: take the larger one without cancellation
+      // (b + sqrt(b^2 - 4) with the root's sign aligned to b) and invert it.
+      const cd bq = 2.0 + 1.0 / c;
+      cd disc = std::sqrt(bq * bq - 4.0);
+      if (std::abs(bq - disc) > std::abs(bq + disc)) disc = -disc;
+      const cd lam = 2.0 / (bq + disc);
+      const cd alpha = c / lam;
+      std::vector<cd> pre(32, 1.0), suf(32, 1.0), chk(32, 1.0);
+      for (int j = 0; j < 32; ++j) {
+        const int lo = std::min(p, j * cc), hi = std::min(p, lo + cc);
+        pre[j] = std::pow(lam, lo);
+        suf[j] = std::pow(lam, p - hi);
+        chk[j] = std::pow(lam, hi - lo);
+      }
+      D.cpre = upload_c<R>(I, pre, err);
+      D.csuf = upload_c<R>(I, suf, err);
+      D.cchunk = upload_c<R>(I, chk, err);
+      const cd ia = 1.0 / alpha, i1m = 1.0 / (1.0 - std::pow(lam, p));
+      D.lam[0] = lam.real();
+      D.lam[1] = lam.imag();
+      D.ialpha[0] = ia.real();
+      D.ialpha[1] = ia.imag();
+      D.inv1m[0] = i1m.real();
+      D.inv1m[1] = i1m.imag();
+    }
     D.vl[0] = T.vl.real();
     D.vl[1] = T.vl.imag();
     D.inv[0] = T.inv.real();
@@ -599,7 +732,10 @@ cudaError_t cplx_step_t(const Instance &I, R *U, double t, cudaStream_t s, etd_c
     for (int g = 0; g < 3; ++g) {
       const CplxTabDev &D = X.tab[g];
       A.tab[g] = CTab<R>{(const C2<R> *)D.ell, (const C2<R> *)D.ipv, (const C2<R> *)D.mu, (const C2<R> *)D.zed,
-                         (const C2<R> *)D.af, (const C2<R> *)D.ab, D.vl[0], D.vl[1], D.inv[0], D.inv[1]};
+                         (const C2<R> *)D.af, (const C2<R> *)D.ab, D.vl[0], D.vl[1], D.inv[0], D.inv[1],
+                         (const C2<R> *)D.cpre, (const C2<R> *)D.csuf, (const C2<R> *)D.cchunk,
+                         C2<R>{(R)D.lam[0], (R)D.lam[1]}, C2<R>{(R)D.ialpha[0], (R)D.ialpha[1]},
+                         C2<R>{(R)D.inv1m[0], (R)D.inv1m[1]}};
     }
     for (int b = 0; b < 3; ++b) A.cos2[b] = (const R *)I.cax[b].cos2;
     for (int b = 0; b < I.dim; ++b)

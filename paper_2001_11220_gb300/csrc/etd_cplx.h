@@ -27,6 +27,12 @@ struct CplxTabDev {
   const void *ab = nullptr;   // [32] products of -mu_i over each lane's chunk
   double vl[2] = {0, 0};      // periodic: v_{p-1} (v_0 = 1)
   double inv[2] = {0, 0};     // periodic: 1 / (1 + v.z)
+  // periodic lines on the circulant factorisation M = alpha (I - lam E)(I - lam E^-1)
+  // (E the cyclic shift, |lam| < 1): per-lane powers of lam and the scalars
+  const void *cpre = nullptr;   // [32] lam^(nodes before lane j)
+  const void *csuf = nullptr;   // [32] lam^(nodes after lane j)
+  const void *cchunk = nullptr; // [32] lam^(nodes of lane j)
+  double lam[2] = {0, 0}, ialpha[2] = {0, 0}, inv1m[2] = {0, 0};  // lam, 1/alpha, 1/(1 - lam^p)
 };
 
 // launch plan of one axis sweep of the complex kernel: NL lines per block
