@@ -149,10 +149,11 @@ etd_status etd_create(const etd_grid *grid, const double *D, const etd_reaction 
  * complex Ginzburg-Landau equation (p = 1, q = alpha) and the cubic
  * Schrodinger equation, whose form u_t + J Lap u = q J u with
  * J = [[0, 1], [-1, 0]] is Dm = -J (p = 0, q = 1).  Every line system
- * I + (k/gamma)(p + i q)/h^2 B_p is a complex tridiagonal (cyclic) matrix,
- * LU-factorised in FP64 on the host (strictly diagonally dominant in
- * modulus, no pivoting) and uploaded in the context's precision; periodic
- * lines use a per-line Sherman-Morrison correction.  nspecies must be 2 and
+ * I + (k/gamma)(p + i q)/h^2 B_p is a complex tridiagonal (cyclic) matrix:
+ * Dirichlet / Neumann lines are LU-factorised in FP64 on the host (strictly
+ * diagonally dominant in modulus, no pivoting), periodic lines are factored
+ * exactly as alpha (I - lam E)(I - lam E^-1) (E the cyclic shift, |lam| < 1);
+ * the coefficients are uploaded in the context's precision.  nspecies must be 2 and
  * the reaction ZERO, LINEAR, CGL or NLS (else ETD_ERR_UNSUPPORTED, as for
  * another Dm; ETD_ERR_INVALID_ARG for a non-finite Dm or p < 0, and for the
  * grid / k / precision checks of etd_create).  Lines longer than about

@@ -21,8 +21,8 @@
 // and back substitution x_i = y_i / piv_i - mu_i x_{i+1} are first-order
 // complex recurrences: each lane reduces its chunk to an affine map, a
 // 5-step warp-shuffle scan composes the maps, and each lane re-runs its chunk
-// from the true carry.  Periodic lines add the Sherman-Morrison correction
-// x - sigma z, sigma formed in FP64.
+// from the true carry.  Periodic lines use the circulant factorisation of
+// the cyclic matrix instead (two cyclic first-order recurrences, below).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -82,9 +82,8 @@ template <typename R> __device__ __forceinline__ C2<R> shfl_c(C2<R> a, int src) 
 }
 
 template <typename R> struct CTab {
-  const C2<R> *ell, *ipv, *mu, *zed;
-  const C2<R> *af, *ab;  // [32] per-lane chunk products of -l_i and of -mu_i
-  double vl_x, vl_y, inv_x, inv_y;
+  const C2<R> *ell, *ipv, *mu;  // Dirichlet / Neumann lines: Thomas factors
+  const C2<R> *af, *ab;         // [32] per-lane chunk products of -l_i and of -mu_i
   // periodic lines: circulant factorisation alpha (I - lam E)(I - lam E^-1)
   const C2<R> *cpre, *csuf, *cchunk;  // [32] lam^(before lane), lam^(after lane), lam^(lane's nodes)
   C2<R> lam, ialpha, inv1m;           // lam, 1/alpha, 1/(1 - lam^p)
@@ -163,14 +162,6 @@ __device__ __forceinline__ C2<R> scan_bwd(C2<R> A, C2<R> B, int lane) {
   }
   C2<R> x = shfl_down_c(B, 1);
   return lane == 31 ? cmk<R>(0, 0) : x;
-}
-
-// Sherman-Morrison factor sigma = (x_0 + v_{p-1} x_{p-1}) / (1 + v.z), in FP64
-template <typename R>
-__device__ __forceinline__ C2<R> sm_sigma(const CTab<R> &T, C2<R> x0, C2<R> xp) {
-  const double ar = (double)x0.x + T.vl_x * (double)xp.x - T.vl_y * (double)xp.y;
-  const double ai = (double)x0.y + T.vl_x * (double)xp.y + T.vl_y * (double)xp.x;
-  return cmk<R>((R)(ar * T.inv_x - ai * T.inv_y), (R)(ar * T.inv_y + ai * T.inv_x));
 }
 
 // Nodes per lane: c = ceil(p/32) rounded up to an odd number, so that the
@@ -303,15 +294,9 @@ __device__ __forceinline__ void solve1(const CTab<R> &T, int p, int periodic, C2
   B = cmk<R>(0, 0);
   CHUNK_BWD(t, i) B = csub(cmul(buf[i], ldt(T.ipv + i)), cmul(ldt(T.mu + i), B));
   CT x = scan_bwd(ldt(T.ab + lane), B, lane);
-  CT xl = cmk<R>(0, 0);
   CHUNK_BWD(t, i) {
     x = csub(cmul(buf[i], ldt(T.ipv + i)), cmul(ldt(T.mu + i), x));
     buf[i] = x;
-    if (i == p - 1) xl = x;
-  }
-  if (periodic) {
-    const CT sg = sm_sigma(T, shfl_c(x, 0), shfl_c(xl, (p - 1) / c));
-    CHUNK_FWD(t, i) buf[i] = csub(buf[i], cmul(sg, ldt(T.zed + i)));
   }
   __syncwarp();
 }
@@ -355,31 +340,11 @@ __device__ __forceinline__ void solve_pair(const CTab<R> &TA, const CTab<R> &TB,
   }
   CT xA = scan_bwd(ldt(TA.ab + lane), BA, lane);
   CT xB = scan_bwd(ldt(TB.ab + lane), BB, lane);
-  CT xlA = cmk<R>(0, 0), xlB = cmk<R>(0, 0);
   CHUNK_BWD(t, i) {
     const CT a = stA[i], b = stB[i];
     xA = csub(cmul(a, ldt(TA.ipv + i)), cmul(ldt(TA.mu + i), xA));
     xB = csub(cmul(b, ldt(TB.ipv + i)), cmul(ldt(TB.mu + i), xB));
-    if (periodic) {
-      stA[i] = xA;
-      stB[i] = xB;
-      if (i == p - 1) {
-        xlA = xA;
-        xlB = xB;
-      }
-    } else {
-      out[i] = cadd(cscale(ca, xA), cscale(cb, xB));
-    }
-  }
-  if (periodic) {
-    const int lp = (p - 1) / c;
-    const CT sA = sm_sigma(TA, shfl_c(xA, 0), shfl_c(xlA, lp));
-    const CT sB = sm_sigma(TB, shfl_c(xB, 0), shfl_c(xlB, lp));
-    CHUNK_FWD(t, i) {
-      const CT a = csub(stA[i], cmul(sA, ldt(TA.zed + i)));
-      const CT b = csub(stB[i], cmul(sB, ldt(TB.zed + i)));
-      out[i] = cadd(cscale(ca, a), cscale(cb, b));
-    }
+    out[i] = cadd(cscale(ca, xA), cscale(cb, xB));
   }
   __syncwarp();
 }
@@ -487,13 +452,10 @@ __global__ void __launch_bounds__(256) cplx_sweep_kernel(const CplxArgs<R> A) {
 
 using cd = std::complex<double>;
 
-// Complex Thomas tables of M = I + c B (h^2 B_p of Example 1), Section 7's
-// LU without pivoting.  Periodic lines: M = M0 + u v^T with g = -(1 + 2c),
-// u = (g, 0, ..., 0, -c), v = (1, 0, ..., 0, c / (1 + 2c)); M0 tridiagonal with
-// d0 - g on its first and d - c^2 / g on its last diagonal entry.
+// Complex Thomas tables of M = I + c B (h^2 B_p of Example 1) for a Dirichlet
+// or Neumann line, Section 7's LU without pivoting.
 struct HostCplxTab {
-  std::vector<cd> ell, ipv, mu, zed;
-  cd vl = 0, inv = 0;
+  std::vector<cd> ell, ipv, mu;
 };
 
 HostCplxTab cplx_tables(int p, int bc, cd c) {
@@ -503,11 +465,6 @@ HostCplxTab cplx_tables(int p, int bc, cd c) {
   if (bc == ETD_BC_NEUMANN) {
     sup[0] = -2.0 * c;
     sub[p - 1] = -2.0 * c;
-  }
-  const cd g = -(1.0 + 2.0 * c);
-  if (bc == ETD_BC_PERIODIC) {
-    dg[0] -= g;
-    dg[p - 1] -= (-c) * (-c) / g;
   }
   HostCplxTab T;
   T.ell.assign(p, 0);
@@ -521,18 +478,6 @@ HostCplxTab cplx_tables(int p, int bc, cd c) {
     }
     T.ipv[i] = 1.0 / piv;
     T.mu[i] = sup[i] / piv;
-  }
-  if (bc == ETD_BC_PERIODIC) {
-    std::vector<cd> u(p, 0.0), z(p);
-    u[0] = g;
-    u[p - 1] = -c;
-    cd y = 0;
-    for (int i = 0; i < p; ++i) z[i] = y = u[i] - T.ell[i] * y;
-    cd x = 0;
-    for (int i = p - 1; i >= 0; --i) z[i] = x = z[i] * T.ipv[i] - T.mu[i] * x;
-    T.zed = z;
-    T.vl = (-c) / g;
-    T.inv = 1.0 / (1.0 + z[0] + T.vl * z[p - 1]);
   }
   return T;
 }
@@ -556,23 +501,23 @@ etd_status build_cplx_axis(etd_ctx *ctx, Instance &I, int a) {
   cudaError_t err = cudaSuccess;
   for (int gi = 0; gi < 3; ++gi) {
     const cd c = (I.k / gammas[gi]) * cd(I.dcp, I.dcq) / (h * h);
-    const HostCplxTab T = cplx_tables(p, I.bc[a], c);
     CplxTabDev &D = X.tab[gi];
-    D.ell = upload_c<R>(I, T.ell, err);
-    D.ipv = upload_c<R>(I, T.ipv, err);
-    D.mu = upload_c<R>(I, T.mu, err);
-    if (I.bc[a] == ETD_BC_PERIODIC) D.zed = upload_c<R>(I, T.zed, err);
-    // chunk products of the warp scans (lane j: nodes [j c, (j+1) c))
-    const int cc = lane_chunk(p);
-    std::vector<cd> af(32, 1.0), ab(32, 1.0);
-    for (int j = 0; j < 32; ++j)
-      for (int i = j * cc; i < std::min(p, (j + 1) * cc); ++i) {
-        af[j] *= -T.ell[i];
-        ab[j] *= -T.mu[i];
-      }
-    D.af = upload_c<R>(I, af, err);
-    D.ab = upload_c<R>(I, ab, err);
-    if (I.bc[a] == ETD_BC_PERIODIC) {
+    const int cc = lane_chunk(p);  // nodes per lane (lane j: [j cc, (j+1) cc))
+    if (I.bc[a] != ETD_BC_PERIODIC) {
+      const HostCplxTab T = cplx_tables(p, I.bc[a], c);
+      D.ell = upload_c<R>(I, T.ell, err);
+      D.ipv = upload_c<R>(I, T.ipv, err);
+      D.mu = upload_c<R>(I, T.mu, err);
+      // chunk products of the warp scans
+      std::vector<cd> af(32, 1.0), ab(32, 1.0);
+      for (int j = 0; j < 32; ++j)
+        for (int i = j * cc; i < std::min(p, (j + 1) * cc); ++i) {
+          af[j] *= -T.ell[i];
+          ab[j] *= -T.mu[i];
+        }
+      D.af = upload_c<R>(I, af, err);
+      D.ab = upload_c<R>(I, ab, err);
+    } else {
       // circulant factorisation of the cyclic line matrix (1 + 2c) I - c (E + E^-1):
       // alpha (1 + lam^2) = 1 + 2c, alpha lam = c, i.e. lam + 1/lam = 2 + 1/c, |lam| < 1.
       // The two roots multiply to 1: take the larger one without cancellation
@@ -600,10 +545,6 @@ etd_status build_cplx_axis(etd_ctx *ctx, Instance &I, int a) {
       D.inv1m[0] = i1m.real();
       D.inv1m[1] = i1m.imag();
     }
-    D.vl[0] = T.vl.real();
-    D.vl[1] = T.vl.imag();
-    D.inv[0] = T.inv.real();
-    D.inv[1] = T.inv.imag();
   }
   if (I.rkind == ETD_REACTION_NLS && I.rp[2] != 0.0) {
     std::vector<R> c2(p);
@@ -731,8 +672,8 @@ cudaError_t cplx_step_t(const Instance &I, R *U, double t, cudaStream_t s, etd_c
     A.periodic = I.bc[a] == ETD_BC_PERIODIC;
     for (int g = 0; g < 3; ++g) {
       const CplxTabDev &D = X.tab[g];
-      A.tab[g] = CTab<R>{(const C2<R> *)D.ell, (const C2<R> *)D.ipv, (const C2<R> *)D.mu, (const C2<R> *)D.zed,
-                         (const C2<R> *)D.af, (const C2<R> *)D.ab, D.vl[0], D.vl[1], D.inv[0], D.inv[1],
+      A.tab[g] = CTab<R>{(const C2<R> *)D.ell, (const C2<R> *)D.ipv, (const C2<R> *)D.mu,
+                         (const C2<R> *)D.af, (const C2<R> *)D.ab,
                          (const C2<R> *)D.cpre, (const C2<R> *)D.csuf, (const C2<R> *)D.cchunk,
                          C2<R>{(R)D.lam[0], (R)D.lam[1]}, C2<R>{(R)D.ialpha[0], (R)D.ialpha[1]},
                          C2<R>{(R)D.inv1m[0], (R)D.inv1m[1]}};

@@ -8,25 +8,24 @@
 // The line systems of Section 7 then become complex tridiagonal systems
 // I + (k/gamma)(p + i q)/h^2 B_p, one per (axis, pole), factorised on the host
 // (Thomas LU without pivoting: every row is strictly diagonally dominant in
-// modulus for p >= 0, since |1 + 2c| > 2|c| when Re c >= 0) with periodic
-// lines closed by the rank-one Sherman-Morrison correction.
+// modulus for p >= 0, since |1 + 2c| > 2|c| when Re c >= 0); periodic lines
+// are factored exactly as alpha (I - lam E)(I - lam E^-1), E the cyclic shift,
+// |lam| < 1 (two cyclic first-order recurrences, no tables).
 #pragma once
 
 #include <cstddef>
 
 namespace etd {
 
-// device line tables of one axis and pole: complex (re, im) pairs in the
-// context's real type, p entries each
+// device line coefficients of one axis and pole: complex (re, im) pairs in the
+// context's real type (Dirichlet / Neumann: Thomas factors, p entries each;
+// periodic: the circulant factorisation)
 struct CplxTabDev {
   const void *ell = nullptr;  // l_i = a_i / piv_{i-1} (l_0 = 0)
   const void *ipv = nullptr;  // 1 / piv_i
   const void *mu = nullptr;   // e_i / piv_i (mu_{p-1} = 0)
-  const void *zed = nullptr;  // periodic: z = M0^{-1} u of the Sherman-Morrison split
-  const void *af = nullptr;   // [32] products of -l_i over each lane's chunk of ceil(p/32) nodes
+  const void *af = nullptr;   // [32] products of -l_i over each lane's chunk of nodes
   const void *ab = nullptr;   // [32] products of -mu_i over each lane's chunk
-  double vl[2] = {0, 0};      // periodic: v_{p-1} (v_0 = 1)
-  double inv[2] = {0, 0};     // periodic: 1 / (1 + v.z)
   // periodic lines on the circulant factorisation M = alpha (I - lam E)(I - lam E^-1)
   // (E the cyclic shift, |lam| < 1): per-lane powers of lam and the scalars
   const void *cpre = nullptr;   // [32] lam^(nodes before lane j)
