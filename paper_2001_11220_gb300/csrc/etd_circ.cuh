@@ -7,11 +7,11 @@
 // registers.  Every solve runs as (see etd_circ.h for the algebra):
 //   pass 1: zero-carry chunk summaries F_j, W_j (two FMAs per position, the
 //           weights lambda^t are kernel-parameter constants);
-//   round 1: an inclusive scan of F over the chunks of the line with the
+//   exchange 1: an inclusive scan of F over the chunks of the line with the
 //           constant multiplier Lambda (lane shuffles; lines of several warps
 //           add one shared-memory step over the warp totals), closed
 //           cyclically by the line total -> carry Yc_j of every chunk;
-//   round 2: the same suffix scan of G_j = W_j + kappa Yc_j -> carry Zc_j;
+//   exchange 2: the same suffix scan of G_j = W_j + kappa Yc_j -> carry Zc_j;
 //   pass 2: the recurrences y_i = b_i + lambda y_{i-1} and
 //           z_i = y_i + lambda z_{i+1} over the chunk from (Yc_j, Zc_j).
 // All 5 s solves of the sweep (T, S on U_n; T, S on F(U_n); P on
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
     }
   }
 
-  // ---- round 1: forward carries Yc_j (inclusive scan of F, cyclic closure)
+  // ---- exchange 1: forward carries Yc_j (inclusive scan of F, cyclic closure)
   R Yc[S][NQ];
   if (G == 32) {  // whole warps per line: every step of the scan runs (no per-step test)
 #pragma unroll
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) circ_first_kernel(const
       Yc[s][q] = fma(lp[j], y0, ex);
     }
 
-  // ---- round 2: backward carries Zc_j (suffix scan of G = W + kappa Yc)
+  // ---- exchange 2: backward carries Zc_j (suffix scan of G = W + kappa Yc)
   R Zc[S][NQ];
   if (G == 32) {
 #pragma unroll

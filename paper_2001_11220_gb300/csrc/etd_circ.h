@@ -128,7 +128,7 @@ template <typename R> inline void circ_to_args(const CircHost &H, CircMat<R> &M)
 }
 
 // Tensor maps of the strided sweep's three input fields (32 lines x rows per
-// box); false if the driver's encoder is unavailable or refuses the layout
+// box); false if the CUDA driver's tensor-map encoder is unavailable or refuses the layout
 bool circ_encode_maps(CircArgs<float> &a, int nspecies, int rows);
 bool circ_encode_maps(CircArgs<double> &a, int nspecies, int rows);
 // set to non-zero by a kernel whose wait for a TMA copy gave up (bounded
