@@ -7,6 +7,8 @@ profiling captures).
     python -m paper_2001_11220_gb300.run --workload cgl3d --p 200 --alpha 0.5 --steps 2
       (complex Ginzburg-Landau; --alpha != 0 couples Re u and Im u: complex line kernels)
     python -m paper_2001_11220_gb300.run --workload nls2d --p 79 --precision fp64 --steps 80
+    python -m paper_2001_11220_gb300.run --workload ensemble --p 512 --steps 3
+      (the batched ensemble of --p instances, one persistent launch per step)
 """
 from __future__ import annotations
 
@@ -51,7 +53,21 @@ def main():
     import torch
 
     from paper_2001_11220_gb300 import workloads as W
-    from paper_2001_11220_gb300.api import EtdRdpIf
+    from paper_2001_11220_gb300.api import EtdEnsemble, EtdRdpIf
+    if args.workload == "ensemble":
+        ws = W.ensemble(args.p, steps=args.steps)
+        ens = EtdEnsemble(ws, args.precision)
+        states = [torch.tensor(W.initial_state(x), device="cuda", dtype=ens.dtype) for x in ws]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ens.run(states, 0.0, args.steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        ok = all(bool(torch.isfinite(U).all()) for U in states)
+        print(f"ensemble of {args.p} instances {args.precision}: {args.steps} steps in {dt * 1e3:.2f} ms, "
+              f"info {ens.info()}, finite={ok}")
+        ens.close()
+        return
     w = workload(args.workload, args.p, args.alpha)
     ctx = EtdRdpIf.from_workload(w, args.precision)          # default stream: direct launches
     U = torch.tensor(W.initial_state(w), device="cuda", dtype=ctx.dtype)
