@@ -983,8 +983,17 @@ etd_status init_instance(etd_ctx *ctx, Instance &I, const etd_grid *grid, const 
     // short chunks on short lines (64^2 FP64: 35 us per step at L = 4, 53 at 8)
     if (small && I.n[a] >= 32 && I.n[a] <= 256) L = I.real_bytes == 4 ? 8 : 4;
     while (!plan_axis_ex(I, a, L, ETD_MAX_BLOCK_THREADS, nlb_small, small, 1) && L < 16) L *= 2;
-    if (!plan_axis_ex(I, a, L, ETD_MAX_BLOCK_THREADS, nlb_small, small, 1) && !plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS))
-      return fail(ctx, ETD_ERR_UNSUPPORTED, "axis %d with n = %lld does not fit one block", a, (long long)I.n[a]);
+    if (!plan_axis_ex(I, a, L, ETD_MAX_BLOCK_THREADS, nlb_small, small, 1) && !plan_axis(I, a, L, ETD_MAX_BLOCK_THREADS)) {
+      // lines longer than one block: segments of 32 chunks spread over several
+      // blocks, launched as one thread-block cluster where a line group's
+      // segments fit one, else the multi-launch segmented sweep
+      const int Ls = I.real_bytes == 4 ? 16 : 8;
+      const bool seg = (plan_axis_seg(I, a, Ls, 8, 32, true) && cluster_plan_fits(I, a)) ||
+                       plan_axis_seg(I, a, Ls, 8, 32, false);
+      if (!seg)
+        return fail(ctx, ETD_ERR_UNSUPPORTED, "axis %d with n = %lld fits neither one block nor a segmented plan", a,
+                    (long long)I.n[a]);
+    }
   }
   etd_status st = build_instance_tables(ctx, I);
   if (st != ETD_OK) return st;

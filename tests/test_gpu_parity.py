@@ -553,3 +553,21 @@ def test_staged_kernels_forced_fp64_matches_oracle(w, monkeypatch):
     assert any(k == 1 for k in staged), staged
     got = gpu_run(w, U0, 1, "fp64")
     assert rel_err(got, oracle_run(w, U0, 1)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("shape,bc", [((16384, 3), W.NEUMANN), ((16384, 3), W.PERIODIC),
+                                      ((3, 16384), W.DIRICHLET), ((3, 16384), W.PERIODIC)],
+                         ids=["x_neumann", "x_periodic", "y_dirichlet", "y_periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_longest_lines_the_api_accepts(shape, bc, prec):
+    """Lines of 16384 nodes (the largest n etd_create takes) along x and along y, on
+    the plans the library picks for them: one step against the oracle (FP64 1e-12,
+    FP32 the per-step bound)."""
+    w = case(f"maxline_{shape[0]}x{shape[1]}", shape, bc, (1e-6, 2e-6), "brusselator", (1.0, 3.4), k=0.01)
+    U0 = W.initial_state(w)
+    got = gpu_run(w, U0, 1, prec)
+    ref = oracle_run(w, U0, 1)
+    e = rel_err(got, ref)
+    tol = FP64_TOL if prec == "fp64" else fp32_step_bound(w)
+    print(f"{w.name} {W.BC_NAMES[bc]} {prec}: {e:.2e} (tol {tol:.2e})")
+    assert e <= tol
