@@ -186,7 +186,9 @@ etd_status etd_run_host(etd_ctx *ctx, void *U_host, double t0, int64_t nsteps);
  * U_n (device) at t_n and Ubar_next = dL/dU_{n+1} (device), writes
  * Ubar_n = dL/dU_n (device, may alias Ubar_next) and ADDS dL/dD_s into dD[s]
  * and dL/dparams_j into dparams[j] (host arrays of nspecies and 8 doubles;
- * either may be NULL).  Synchronises the stream. */
+ * either may be NULL).  Synchronises the stream.  The adjoint sweeps take
+ * lines of one block (at most 4096 nodes): longer axes, D_s = 0 and coupled
+ * contexts return ETD_ERR_UNSUPPORTED (so do etd_grad and etd_run_vjp). */
 etd_status etd_step_adjoint(etd_ctx *ctx, const void *Un, double t_n, const void *Ubar_next,
                             void *Ubar_n, double *dD, double *dparams);
 
