@@ -115,6 +115,7 @@ def test_null_arguments(lib):
     assert lib.etd_step(None, None, 0.0) == B.ETD_ERR_INVALID_ARG
     assert lib.etd_run(None, None, 0.0, 1) == B.ETD_ERR_INVALID_ARG
     assert lib.etd_get_info(None, None) == B.ETD_ERR_INVALID_ARG
+    assert lib.etd_check_finite(None, None, None) == B.ETD_ERR_INVALID_ARG
     lib.etd_destroy(None)
     assert lib.etd_last_error(None)
 
