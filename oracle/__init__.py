@@ -250,7 +250,8 @@ def run(P: Problem, U, t0: float, nsteps: int) -> np.ndarray:
 
 
 def step_adjoint(P: Problem, Un, t: float, Ubar_next):
-    """Reverse mode of one step: (Ubar_n, dD[:s], dparams[8])."""
+    """Reverse mode of one step: (Ubar_n, dD[:s], dparams[8]); coupled problems
+    return dD as the 4 entries d/dDc[s][t], row-major."""
     c = P.as_c()
     u = _arr(Un, P.shape).copy()
     ub = _arr(Ubar_next, P.shape).copy()
@@ -258,7 +259,7 @@ def step_adjoint(P: Problem, Un, t: float, Ubar_next):
     dD = np.zeros(4)
     dp = np.zeros(8)
     _check(_load().oracle_step_adjoint(ctypes.byref(c), _ptr(u), t, _ptr(ub), _ptr(out), _ptr(dD), _ptr(dp)), "step_adjoint")
-    return out, dD[: P.nspecies], dp
+    return out, (dD if P.Dc is not None else dD[: P.nspecies]), dp
 
 
 def grad(P: Problem, U0, t0: float, target, nsteps: int):
@@ -271,4 +272,4 @@ def grad(P: Problem, U0, t0: float, target, nsteps: int):
     dD = np.zeros(4)
     dp = np.zeros(8)
     _check(_load().oracle_grad(ctypes.byref(c), _ptr(u), t0, _ptr(tg), int(nsteps), _ptr(loss), _ptr(dU0), _ptr(dD), _ptr(dp)), "grad")
-    return float(loss[0]), dU0, dD[: P.nspecies], dp
+    return float(loss[0]), dU0, (dD if P.Dc is not None else dD[: P.nspecies]), dp

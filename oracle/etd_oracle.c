@@ -806,6 +806,17 @@ static void accumulate_dD(const oracle_problem *P, int a, double gamma, const do
                           const double *x, double *tmp, double *Dbar) {
   long N = npoints(P);
   axis_laplacian(P, a, x, tmp);
+  if (P->coupled) {
+    /* A_a = (B (x) Dc) / h^2: d/dDc[s][t] of the solve enters species s through B x_t,
+     * so dL/dDc[s][t] += -(k/gamma) <lam_s, B x_t> (Dbar row-major, 4 entries) */
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int t2 = 0; t2 < 2; ++t2) {
+        double acc = 0.0;
+        for (long i = 0; i < N; ++i) acc += lam[s2 * N + i] * tmp[t2 * N + i];
+        Dbar[2 * s2 + t2] += -(P->k / gamma) * acc;
+      }
+    return;
+  }
   for (int s = 0; s < P->nspecies; ++s) {
     double acc = 0.0;
     for (long i = 0; i < N; ++i) acc += lam[s * N + i] * tmp[s * N + i];
@@ -816,7 +827,7 @@ static void accumulate_dD(const oracle_problem *P, int a, double gamma, const do
 /* Reverse mode of step_forward, transposing each line of the frame in turn. */
 int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
                         const double *Ubar_next, double *Ubar_n, double *Dbar, double *pbar) {
-  if (check_problem(P) || P->coupled) return -1;
+  if (check_problem(P)) return -1;
   long M = npoints(P) * P->nspecies;
   int d = P->dim;
   double k = P->k;
@@ -873,7 +884,7 @@ int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
   oracle_reaction_vjp(P, Un, t, f0b, tmp, pbar);
   for (long i = 0; i < M; ++i) Ubar_n[i] = cUb[i] + wb[i] + tmp[i];
   if (Dbar)
-    for (int s = 0; s < P->nspecies; ++s) Dbar[s] += Dloc[s];
+    for (int s = 0; s < (P->coupled ? 4 : P->nspecies); ++s) Dbar[s] += Dloc[s];
 
   work_free(&W);
   free(Unext);
@@ -894,7 +905,7 @@ int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
 
 int oracle_grad(const oracle_problem *P, const double *U0, double t0, const double *target,
                 long nsteps, double *loss, double *dU0, double *dD, double *dparams) {
-  if (check_problem(P) || P->coupled || nsteps < 0) return -1;
+  if (check_problem(P) || nsteps < 0) return -1;
   long M = npoints(P) * P->nspecies;
   double *states = (double *)malloc(sizeof(double) * (size_t)M * (size_t)(nsteps + 1));
   if (!states) return -2;

@@ -104,7 +104,8 @@ int oracle_run(const oracle_problem *P, double *U, double t0, long nsteps);
 
 /* reverse mode of one step: given U_n (at time t) and Ubar_{n+1}, return
  * Ubar_n and accumulate Dbar[s] (d/dD_s) and pbar[j] (d/dparams_j).
- * Diagonal D only (returns -1 for coupled problems; so does oracle_grad). */
+ * Coupled problems: Dbar holds 4 entries, d/dDc[s][t] row-major (the
+ * transposed solves are those of B^T (x) Dc^T). */
 int oracle_step_adjoint(const oracle_problem *P, const double *Un, double t,
                         const double *Ubar_next, double *Ubar_n, double *Dbar, double *pbar);
 

@@ -76,11 +76,67 @@ def test_diagonal_coupling_is_two_uncoupled_species(bcs):
     assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
 
 
-def test_coupled_adjoint_is_refused():
-    P = oracle.Problem(n=(4, 4), bc=(2, 2), D=(1.0, 1.0), Dc=rot(1.0, 0.5), reaction=oracle.CGL, params=(1.3,), k=0.1)
-    U = RNG.standard_normal(P.shape)
-    with pytest.raises(ValueError):
-        oracle.step_adjoint(P, U, 0.0, U)
+@pytest.mark.parametrize("dims,bcs,kind,params,Dc", [
+    ((6, 5), (2, 2), oracle.CGL, (1.3,), rot(0.7, 0.5)),
+    ((7, 6), (1, 1), oracle.NLS, (0.2, -1.5, 0.8), rot(0.0, 0.3)),
+    ((5, 4, 4), (1, 0, 2), oracle.CGL, (0.9,), (0.4, -0.3, 0.2, 0.6)),   # a general (non-rotation) matrix
+])
+def test_coupled_step_adjoint_vs_finite_differences(dims, bcs, kind, params, Dc):
+    """Reverse mode of one coupled step: the state cotangent, the four entries of
+    dL/dDc and the reaction-parameter gradient against central differences of
+    <wbar, step(U)>."""
+    kw = dict(n=dims, bc=bcs, D=(1.0, 1.0), reaction=kind, params=params, k=0.05)
+    P = oracle.Problem(Dc=Dc, **kw)
+    U = 0.4 * RNG.standard_normal(P.shape)
+    wbar = RNG.standard_normal(P.shape)
+    Ubar, dD, dp = oracle.step_adjoint(P, U, 0.1, wbar)
+    assert dD.shape == (4,)
+    eps = 1e-6
+
+    def J(Pq, V):
+        return np.sum(wbar * oracle.step(Pq, V, 0.1))
+
+    v = RNG.standard_normal(P.shape)
+    fd = (J(P, U + eps * v) - J(P, U - eps * v)) / (2 * eps)
+    assert abs(fd - np.sum(Ubar * v)) < 1e-7 * max(1, abs(fd))
+    for j in range(4):
+        Dp, Dm = list(Dc), list(Dc)
+        Dp[j] += eps
+        Dm[j] -= eps
+        fdD = (J(oracle.Problem(Dc=Dp, **kw), U) - J(oracle.Problem(Dc=Dm, **kw), U)) / (2 * eps)
+        assert abs(fdD - dD[j]) < 1e-6 * max(1, abs(fdD)), (j, fdD, dD[j])
+    for j in range(len(params)):
+        pp, pm = list(params), list(params)
+        pp[j] += eps
+        pm[j] -= eps
+        kp, km = dict(kw, params=pp), dict(kw, params=pm)
+        fdp = (J(oracle.Problem(Dc=Dc, **kp), U) - J(oracle.Problem(Dc=Dc, **km), U)) / (2 * eps)
+        assert abs(fdp - dp[j]) < 1e-6 * max(1, abs(fdp)), (j, fdp, dp[j])
+
+
+def test_coupled_grad_multistep_vs_finite_differences():
+    """The checkpoint-free multi-step gradient of a coupled run (CGL, D = 1 + 0.6i,
+    periodic): dL/dU0 along a random direction and dL/dp, dL/dq of the complex
+    coefficient (p = Dc[0] = Dc[3], q = Dc[2] = -Dc[1]) against central differences."""
+    kw = dict(n=(6, 5), bc=(2, 1), D=(1.0, 1.0), reaction=oracle.CGL, params=(1.3,), k=0.05, length=(3.0, 2.5))
+    p0, q0 = 1.0, 0.6
+    P = oracle.Problem(Dc=rot(p0, q0), **kw)
+    U0 = 0.5 * RNG.standard_normal(P.shape)
+    target = 0.5 * RNG.standard_normal(P.shape)
+    loss, dU0, dD, _ = oracle.grad(P, U0, 0.0, target, 4)
+    eps = 1e-6
+
+    def L(Pq, V):
+        return 0.5 * np.sum((oracle.run(Pq, V, 0.0, 4) - target) ** 2)
+
+    assert abs(loss - L(P, U0)) < 1e-12 * max(1.0, loss)
+    v = RNG.standard_normal(P.shape)
+    fd = (L(P, U0 + eps * v) - L(P, U0 - eps * v)) / (2 * eps)
+    assert abs(fd - np.sum(dU0 * v)) < 1e-7 * max(1, abs(fd))
+    fdp = (L(oracle.Problem(Dc=rot(p0 + eps, q0), **kw), U0) - L(oracle.Problem(Dc=rot(p0 - eps, q0), **kw), U0)) / (2 * eps)
+    fdq = (L(oracle.Problem(Dc=rot(p0, q0 + eps), **kw), U0) - L(oracle.Problem(Dc=rot(p0, q0 - eps), **kw), U0)) / (2 * eps)
+    assert abs(fdp - (dD[0] + dD[3])) < 1e-6 * max(1, abs(fdp)), (fdp, dD)
+    assert abs(fdq - (dD[2] - dD[1])) < 1e-6 * max(1, abs(fdq)), (fdq, dD)
 
 
 # ------------------------------------------------------ eigenmode recurrence --
